@@ -1,0 +1,810 @@
+"""Plain CPU FP64 oracle: HHG refinement, P1 assembly, FMG (Alg. 4), estimator, marking, 2D red-green.
+
+TEST INFRASTRUCTURE ONLY -- imported by tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py``; never by the product path.
+
+Paper: B. Mann, U. Ruede, "kl-refinement: An adaptive mesh refinement scheme for
+hierarchical hybrid grids" (arXiv 2508.06049).
+
+What each part follows
+----------------------
+* Sec. 2 (HHG construction): every macro element of the coarse mesh T_0 is refined
+  uniformly L times, red refinement for triangles, Bey's rule for tetrahedra.
+  Here this is done literally, element by element, recursively.  A node is keyed
+  by its integer barycentric weights over the macro vertices (weights sum to 2^l),
+  which makes nodes on shared macro edges/faces/vertices coincide without any
+  structured indexing.
+* Sec. 4.4, Eq. (4.15): A_l u_l = b_l, P1 Lagrange elements for the Poisson /
+  piecewise-constant-coefficient diffusion problem of Eq. (5.1), assembled
+  element by element (stiffness k_T int grad phi_i . grad phi_j, mass int phi_i phi_j).
+  b_l = M_l f_l with f_l = f at the level-l nodes; Dirichlet nodes fixed to g.
+* Sec. 4.4, Alg. 4 (FMG): for l = 0..L, nu V-cycles on level l, then
+  u_{l+1} <- I u_l and w_l <- u_{l+1}.  The V-cycle (pre-smooth, residual,
+  restriction = I^T, coarse correction, prolongation, post-smooth) and the
+  smoother ordering are not spelled out in the paper; the readings taken are:
+    - Gauss-Seidel sweep = ordered stage list: macro vertices; macro-edge
+      interior nodes with even, then odd, edge-local index (counted from the
+      endpoint with the smaller global id); (3D) macro-face interior nodes by
+      colour (a + 2b) mod 3 in face-local coordinates (vertices sorted by global
+      id); macro-cell interior nodes by colour (alpha . p) mod m with alpha, m
+      chosen per macro from its interior stencil (red-black where the diagonal
+      couplings vanish).  Inside one stage all nodes are updated from the values
+      at the start of the stage.
+    - Coarse solve: exact dense Cholesky solve (the limit of the paper's CG).
+    - I = linear interpolation on the nested meshes, restriction = I^T.
+* Sec. 4.4, Alg. 4 (ErrorEstimate) and Eqs. (4.5), (4.6), (4.14): e~_l = u_L - I w_l,
+  theta~_l = ||e~_l|| / ||e~_{l-1}||, eta_j = theta~_l^j ||e~_l|| with l = L-j,
+  L2 norms through the mass matrix; local eta_T = ||e~_{L-1}||_{L2(T)} over the
+  micro elements inside macro T.
+* Theorem 4.1 / Corollaries 4.3-4.4: effectivity constants.
+* Sec. 3 and Sec. 5.1: marking of a top fraction of macro elements; 2D red-green
+  refinement with greens reverted before the next step.
+
+No kernel blocking, fusion or reordering beyond the definitions above.
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg
+import scipy.sparse as sp
+
+# Sentinel global id used to pad node keys (sorts after every real vertex id).
+_PAD = np.int64(1 << 40)
+
+
+# --------------------------------------------------------------------------------------
+# Refinement rules (Sec. 2): children given as index lists into [vertices..., midpoints...]
+# --------------------------------------------------------------------------------------
+
+def _red_children_2d():
+    # vertices 0,1,2 ; midpoints 3=(0,1) 4=(1,2) 5=(2,0)
+    edges = [(0, 1), (1, 2), (2, 0)]
+    children = [(0, 3, 5), (3, 1, 4), (5, 4, 2), (4, 5, 3)]
+    return edges, children
+
+
+def _bey_children_3d():
+    # vertices 0..3 ; midpoints 4=(0,1) 5=(0,2) 6=(0,3) 7=(1,2) 8=(1,3) 9=(2,3)
+    # Bey's rule: four corner tets and the interior octahedron cut along x02-x13.
+    edges = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
+    children = [
+        (0, 4, 5, 6), (4, 1, 7, 8), (5, 7, 2, 9), (6, 8, 9, 3),
+        (4, 5, 6, 8), (4, 5, 7, 8), (5, 6, 8, 9), (5, 7, 8, 9),
+    ]
+    return edges, children
+
+
+def _refine_weights(W, dim):
+    """One uniform refinement of micro elements given by integer weight vectors.
+
+    W has shape (nE, d+1, d+1): W[e, a] is the weight vector of vertex a of element e
+    over the d+1 vertices of its macro element (weights sum to 2^l).  Returns the
+    children's weights (sum 2^(l+1)) and the (vertex, midpoint) bookkeeping needed
+    for the interpolation operator.
+    """
+    edges, children = (_red_children_2d() if dim == 2 else _bey_children_3d())
+    nE = W.shape[0]
+    pts = [2 * W[:, a, :] for a in range(dim + 1)]
+    for (a, b) in edges:
+        pts.append(W[:, a, :] + W[:, b, :])
+    P = np.stack(pts, axis=1)  # (nE, d+1+n_edges, d+1)
+    C = np.stack([P[:, list(ch), :] for ch in children], axis=1)  # (nE, nchild, d+1, d+1)
+    return C.reshape(nE * len(children), dim + 1, dim + 1), edges
+
+
+# --------------------------------------------------------------------------------------
+# Node keys
+# --------------------------------------------------------------------------------------
+
+def _canonical_keys(wts, macro, cells):
+    """Canonical key rows for points with integer weights `wts` (N, d+1) over macro `macro`.
+
+    Key = (global vertex id, weight) pairs with nonzero weight, sorted by global id,
+    padded with (_PAD, 0).  Shape (N, 2(d+1)) int64.
+    """
+    gids = cells[macro].astype(np.int64)  # (N, d+1)
+    g = np.where(wts > 0, gids, _PAD)
+    w = np.where(wts > 0, wts, 0).astype(np.int64)
+    order = np.argsort(g, axis=1, kind="stable")
+    g = np.take_along_axis(g, order, axis=1)
+    w = np.take_along_axis(w, order, axis=1)
+    key = np.empty((wts.shape[0], 2 * wts.shape[1]), dtype=np.int64)
+    key[:, 0::2] = g
+    key[:, 1::2] = w
+    return key
+
+
+# --------------------------------------------------------------------------------------
+# Element matrices (P1)
+# --------------------------------------------------------------------------------------
+
+def _element_matrices(X):
+    """P1 stiffness (unit coefficient) and mass matrices for simplices X (nE, d+1, d).
+
+    Stiffness K_ab = |E| grad(phi_a) . grad(phi_b); mass M_ab = |E| (1 + delta_ab) / ((d+1)(d+2)).
+    """
+    nE, dp1, d = X.shape
+    J = np.transpose(X[:, 1:, :] - X[:, :1, :], (0, 2, 1))  # columns = edge vectors, (nE, d, d)
+    det = np.linalg.det(J)
+    vol = np.abs(det) / math.factorial(d)
+    Jinv = np.linalg.inv(J)  # rows = gradients of barycentric coords 1..d
+    G = np.empty((nE, dp1, d))
+    G[:, 1:, :] = Jinv
+    G[:, 0, :] = -Jinv.sum(axis=1)
+    K = vol[:, None, None] * np.einsum("eak,ebk->eab", G, G)
+    Mref = (np.ones((dp1, dp1)) + np.eye(dp1)) / ((d + 1) * (d + 2))
+    M = vol[:, None, None] * Mref[None, :, :]
+    return K, M, vol
+
+
+def _assemble(elems, Ke, n):
+    dp1 = elems.shape[1]
+    rows = np.repeat(elems, dp1, axis=1).ravel()
+    cols = np.tile(elems, (1, dp1)).ravel()
+    return sp.csr_matrix((Ke.ravel(), (rows, cols)), shape=(n, n))
+
+
+# --------------------------------------------------------------------------------------
+# Coarse topology
+# --------------------------------------------------------------------------------------
+
+def _faces_of(cells, dim):
+    """Facets (sorted vertex tuples) of each cell: edges in 2D, triangles in 3D."""
+    from itertools import combinations
+    out = []
+    for c in cells:
+        out.append([tuple(sorted(f)) for f in combinations([int(v) for v in c], dim)])
+    return out
+
+
+@dataclass
+class Level:
+    l: int
+    keys: np.ndarray          # (N, 2(d+1)) canonical node keys
+    x: np.ndarray             # (N, d) coordinates
+    elems: np.ndarray         # (nE, d+1) node ids
+    emacro: np.ndarray        # (nE,) macro id of each micro element
+    Ke: np.ndarray            # (nE, d+1, d+1) stiffness element matrices (with k_T)
+    Me: np.ndarray            # (nE, d+1, d+1) mass element matrices
+    A: sp.csr_matrix = None
+    M: sp.csr_matrix = None
+    dirichlet: np.ndarray = None
+    free: np.ndarray = None
+    stages: list = field(default_factory=list)
+    stage_rows: list = field(default_factory=list)
+    stage_diag: list = field(default_factory=list)
+    P: sp.csr_matrix = None   # interpolation from level l-1 to l (l >= 1)
+
+
+class Hierarchy:
+    """Nested P1 meshes T_0 ... T_L of an HHG (Sec. 2), assembled explicitly.
+
+    coords (nV, d), cells (nC, d+1) 0-based; dirichlet: per-vertex flags or None (= all
+    boundary vertices); k: per-cell coefficient or None (= 1).
+    """
+
+    def __init__(self, coords, cells, L, dirichlet=None, k=None):
+        coords = np.asarray(coords, dtype=np.float64)
+        cells = np.asarray(cells, dtype=np.int64)
+        self.dim = d = coords.shape[1]
+        if d not in (2, 3) or cells.shape[1] != d + 1:
+            raise ValueError("need triangles in 2D or tetrahedra in 3D")
+        self.coords, self.cells, self.L = coords, cells, int(L)
+        self.n_cells = len(cells)
+        self.k = np.ones(self.n_cells) if k is None else np.asarray(k, dtype=np.float64)
+        self._topology(dirichlet)
+        self.levels = []
+        W = np.repeat(np.eye(d + 1, dtype=np.int64)[None], self.n_cells, axis=0)
+        macro = np.arange(self.n_cells)
+        prev = None
+        for l in range(self.L + 1):
+            if l > 0:
+                Wc, macro_c = W, macro
+                W, edges = _refine_weights(W, d)
+                nchild = W.shape[0] // Wc.shape[0]
+                macro = np.repeat(macro_c, nchild)
+            lev = self._build_level(l, W, macro)
+            if l > 0:
+                lev.P = self._interpolation(lev, prev, Wc, macro_c, edges)
+            self.levels.append(lev)
+            prev = lev
+        self._colouring()
+        for lev in self.levels:
+            self._stages(lev)
+
+    # ---- topology and boundary (Sec. 2: macro primitives) ----
+    def _topology(self, dirichlet):
+        d = self.dim
+        facets = _faces_of(self.cells, d)
+        count = {}
+        for fl in facets:
+            for f in fl:
+                count[f] = count.get(f, 0) + 1
+        self.boundary_facets = {f for f, c in count.items() if c == 1}
+        bverts = set()
+        bedges = set()
+        for f in self.boundary_facets:
+            bverts.update(f)
+            if d == 2:
+                bedges.add(f)
+            else:
+                bedges.update({(f[0], f[1]), (f[0], f[2]), (f[1], f[2])})
+        self.boundary_edges = bedges
+        if dirichlet is None:
+            vflag = np.zeros(len(self.coords), dtype=bool)
+            vflag[list(bverts)] = True
+        else:
+            vflag = np.asarray(dirichlet).astype(bool).copy()
+        self.vflag = vflag
+        self.cell_of_vertex_set = {tuple(sorted(int(v) for v in c)): t for t, c in enumerate(self.cells)}
+
+    def _node_dirichlet(self, keys):
+        d = self.dim
+        g = keys[:, 0::2]
+        s = (g != _PAD).sum(axis=1)
+        out = np.zeros(len(keys), dtype=bool)
+        for i in np.nonzero(s <= d)[0]:
+            sup = tuple(int(v) for v in g[i, : s[i]])
+            if len(sup) == 1:
+                out[i] = self.vflag[sup[0]]
+            elif len(sup) == 2:
+                out[i] = sup in self.boundary_edges and all(self.vflag[v] for v in sup)
+            else:  # face interior (3D only: s <= d)
+                out[i] = sup in self.boundary_facets and all(self.vflag[v] for v in sup)
+        return out
+
+    def _build_level(self, l, W, macro):
+        d = self.dim
+        nE = W.shape[0]
+        flat_w = W.reshape(nE * (d + 1), d + 1)
+        flat_m = np.repeat(macro, d + 1)
+        keys_all = _canonical_keys(flat_w, flat_m, self.cells)
+        keys, inv = _unique_rows(keys_all)
+        elems = inv.reshape(nE, d + 1)
+        # coordinates from the canonical key: sum_a w_a X_{g_a} / 2^l
+        g = keys[:, 0::2]
+        w = keys[:, 1::2].astype(np.float64)
+        gsafe = np.where(g == _PAD, 0, g)
+        x = np.einsum("na,nak->nk", w, self.coords[gsafe]) / float(2 ** l)
+        X = x[elems]
+        K, Mm, _ = _element_matrices(X)
+        K = K * self.k[macro][:, None, None]
+        lev = Level(l=l, keys=keys, x=x, elems=elems, emacro=macro, Ke=K, Me=Mm)
+        n = len(keys)
+        lev.A = _assemble(elems, K, n)
+        lev.M = _assemble(elems, Mm, n)
+        lev.dirichlet = self._node_dirichlet(keys)
+        lev.free = ~lev.dirichlet
+        return lev
+
+    def _interpolation(self, fine, coarse, Wc, macro_c, edges):
+        """Linear interpolation I_{l-1}^{l}: old nodes copied, edge midpoints averaged (Sec. 4.4)."""
+        d = self.dim
+        nEc = Wc.shape[0]
+        rows, cols, vals = [], [], []
+        # coarse node ids of coarse element vertices
+        cvert = coarse.elems  # (nEc, d+1)
+        # fine keys of doubled coarse vertices
+        kv = _canonical_keys((2 * Wc).reshape(-1, d + 1), np.repeat(macro_c, d + 1), self.cells)
+        fid_v = _lookup(fine.keys, kv)
+        rows.append(fid_v)
+        cols.append(cvert.ravel())
+        vals.append(np.ones(len(fid_v)))
+        for (a, b) in edges:
+            km = _canonical_keys(Wc[:, a, :] + Wc[:, b, :], macro_c, self.cells)
+            fid = _lookup(fine.keys, km)
+            for c in (a, b):
+                rows.append(fid)
+                cols.append(cvert[:, c])
+                vals.append(np.full(nEc, 0.5))
+        rows = np.concatenate(rows)
+        cols = np.concatenate(cols)
+        vals = np.concatenate(vals)
+        # each (fine, coarse) pair is defined once, even if several coarse elements share it
+        pair, _ = _unique_rows(np.stack([rows, cols, (vals * 2).astype(np.int64)], axis=1))
+        P = sp.csr_matrix((pair[:, 2] / 2.0, (pair[:, 0], pair[:, 1])),
+                          shape=(len(fine.keys), len(coarse.keys)))
+        return P
+
+    # ---- smoother stage ordering (reading of "Gauss-Seidel", Sec. 5) ----
+    def _colouring(self):
+        """Per macro (alpha_T, m_T) for the macro-cell interior colours.
+
+        Decided from the interior couplings of macro T on level 2 (the interior stencil is
+        the same on every level): m=2 with the first alpha in a fixed candidate list for
+        which alpha . d is odd for every lattice direction d with a nonzero coupling;
+        otherwise m=3, alpha=(1,2) in 2D and m=4, alpha=(1,2,3) in 3D.
+        """
+        d = self.dim
+        self.alpha = np.zeros((self.n_cells, d), dtype=np.int64)
+        self.mcol = np.zeros(self.n_cells, dtype=np.int64)
+        cands = ([(1, 1), (1, 0), (0, 1)] if d == 2 else
+                 [(1, 1, 1), (1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 1, 1)])
+        fallback = ((1, 2), 3) if d == 2 else ((1, 2, 3), 4)
+        if self.L < 2:
+            for t in range(self.n_cells):
+                self.alpha[t], self.mcol[t] = fallback
+            return
+        lev = self.levels[2]
+        loc = self._local_coords(lev.keys)  # (N, macro, p) for interior nodes
+        A = lev.A
+        done = np.zeros(self.n_cells, dtype=bool)
+        for i in np.nonzero(loc[0] >= 0)[0]:
+            t = loc[0][i]
+            if done[t]:
+                continue
+            done[t] = True
+            row = A.getrow(i)
+            offs = [(j, v) for j, v in zip(row.indices, row.data) if j != i]
+            vmax = max(abs(v) for _, v in offs)
+            dirs = []
+            for j, v in offs:
+                if abs(v) > 1e-12 * vmax:
+                    dirs.append(self._local_p(lev.keys[j], t) - loc[1][i])
+            chosen = None
+            for a in cands:
+                if all((int(np.dot(a, dd)) % 2) != 0 for dd in dirs):
+                    chosen = (a, 2)
+                    break
+            if chosen is None:
+                chosen = fallback
+            self.alpha[t], self.mcol[t] = chosen
+
+    def _local_p(self, key, t):
+        """Lattice coordinates of a node (given by key) in macro t: weights on cells[t][1..d]."""
+        g = key[0::2]
+        w = key[1::2]
+        p = np.zeros(self.dim, dtype=np.int64)
+        for a in range(1, self.dim + 1):
+            hit = np.nonzero(g == self.cells[t][a])[0]
+            p[a - 1] = w[hit[0]] if len(hit) else 0
+        return p
+
+    def _local_coords(self, keys):
+        """For macro-cell interior nodes: (macro id, lattice coords); -1 elsewhere."""
+        d = self.dim
+        g = keys[:, 0::2]
+        w = keys[:, 1::2]
+        s = (g != _PAD).sum(axis=1)
+        macro = np.full(len(keys), -1, dtype=np.int64)
+        p = np.zeros((len(keys), d), dtype=np.int64)
+        inner = np.nonzero(s == d + 1)[0]
+        if len(inner) == 0:
+            return macro, p
+        sets, inv = _unique_rows(g[inner])
+        tmap = np.array([self.cell_of_vertex_set[tuple(int(v) for v in row)] for row in sets])
+        t = tmap[inv]
+        macro[inner] = t
+        for a in range(1, d + 1):
+            target = self.cells[t, a][:, None]
+            p[inner, a - 1] = (w[inner] * (g[inner] == target)).sum(axis=1)
+        return macro, p
+
+    def _stages(self, lev):
+        d = self.dim
+        keys = lev.keys
+        g = keys[:, 0::2]
+        w = keys[:, 1::2]
+        s = (g != _PAD).sum(axis=1)
+        free = lev.free
+        stage_of = np.full(len(keys), -1, dtype=np.int64)
+        # stage ids: 0 vertex, 1/2 edge even/odd, then faces (3D: 3 colours), then cells
+        stage_of[(s == 1)] = 0
+        e = s == 2
+        stage_of[e] = 1 + (w[e, 1] % 2)  # weight on the larger-id endpoint
+        base = 3
+        if d == 3:
+            f = s == 3
+            stage_of[f] = base + (w[f, 1] + 2 * w[f, 2]) % 3
+            base += 3
+        macro, p = self._local_coords(keys)
+        c = macro >= 0
+        if c.any():
+            col = (np.einsum("nk,nk->n", p[c], self.alpha[macro[c]])) % self.mcol[macro[c]]
+            stage_of[c] = base + col
+        n_stages = base + int(self.mcol.max())
+        lev.stages = []
+        diag = lev.A.diagonal()
+        for st in range(n_stages):
+            idx = np.nonzero((stage_of == st) & free)[0]
+            lev.stages.append(idx)
+            lev.stage_rows.append(lev.A[idx])
+            lev.stage_diag.append(diag[idx])
+
+
+def _row_hash(keys):
+    """64-bit hash of each key row (collisions are checked by the callers)."""
+    h = np.full(len(keys), np.uint64(1469598103934665603))
+    with np.errstate(over="ignore"):
+        for c in range(keys.shape[1]):
+            h = (h ^ keys[:, c].astype(np.uint64)) * np.uint64(1099511628211)
+            h ^= h >> np.uint64(29)
+    return h
+
+
+def _unique_rows(keys):
+    """Unique key rows (ordered by hash) and the inverse map; exact (hash collisions rejected)."""
+    h = _row_hash(keys)
+    uh, first, inv = np.unique(h, return_index=True, return_inverse=True)
+    uniq = keys[first]
+    if not np.array_equal(uniq[inv], keys):
+        raise AssertionError("node-key hash collision")
+    return uniq, inv.ravel()
+
+
+def _lookup(keys_unique, q):
+    """Row indices of the rows of q inside `keys_unique` (as produced by _unique_rows)."""
+    hk = _row_hash(keys_unique)
+    order = np.argsort(hk)
+    pos = np.searchsorted(hk[order], _row_hash(q))
+    pos = np.minimum(pos, len(order) - 1)
+    idx = order[pos]
+    if not np.array_equal(keys_unique[idx], q):
+        raise AssertionError("query keys not all present on the level")
+    return idx
+
+
+# --------------------------------------------------------------------------------------
+# Level data: right-hand sides and Dirichlet values (Sec. 4.4, Eq. (4.15); Eq. (5.1))
+# --------------------------------------------------------------------------------------
+
+def inject_from_finest(h: Hierarchy, vL: np.ndarray, l: int) -> np.ndarray:
+    """Values at level-l nodes taken from a level-L nodal vector (nested nodes: key * 2^(L-l))."""
+    if l == h.L:
+        return np.asarray(vL, dtype=np.float64).copy()
+    keys = h.levels[l].keys.copy()
+    keys[:, 1::2] *= 2 ** (h.L - l)
+    return np.asarray(vL)[_lookup(h.levels[h.L].keys, keys)]
+
+
+def nodal(h: Hierarchy, fn, l: int) -> np.ndarray:
+    """A nodal vector on level l from a callable of x (N, d) or a level-L nodal array."""
+    if callable(fn):
+        return np.asarray(fn(h.levels[l].x), dtype=np.float64)
+    return inject_from_finest(h, fn, l)
+
+
+class Problem:
+    """b_l = M_l f_l and Dirichlet values g_l for every level of a hierarchy."""
+
+    def __init__(self, h: Hierarchy, f, g):
+        self.h = h
+        self.b = [lev.M @ nodal(h, f, lev.l) for lev in h.levels]
+        self.g = [nodal(h, g, lev.l) for lev in h.levels]
+        lev0 = h.levels[0]
+        F = np.nonzero(lev0.free)[0]
+        self.coarse_free = F
+        A0 = lev0.A[F][:, F].toarray()
+        self.coarse_factor = scipy.linalg.cho_factor(A0, lower=True) if len(F) else None
+
+
+# --------------------------------------------------------------------------------------
+# Smoother, V-cycle, FMG (Alg. 4)
+# --------------------------------------------------------------------------------------
+
+def smooth(lev: Level, u: np.ndarray, rhs: np.ndarray, reverse: bool = False) -> None:
+    """One Gauss-Seidel sweep as the ordered stage list; Jacobi inside a stage (in place)."""
+    order = range(len(lev.stages))
+    if reverse:
+        order = reversed(order)
+    for s in order:
+        idx = lev.stages[s]
+        if len(idx) == 0:
+            continue
+        r = rhs[idx] - lev.stage_rows[s] @ u
+        u[idx] += r / lev.stage_diag[s]
+
+
+def residual(lev: Level, u: np.ndarray, rhs: np.ndarray) -> np.ndarray:
+    """r = rhs - A u on free nodes, zero on Dirichlet nodes."""
+    r = rhs - lev.A @ u
+    r[lev.dirichlet] = 0.0
+    return r
+
+
+def coarse_solve(prob: Problem, u: np.ndarray, rhs: np.ndarray) -> None:
+    """u <- u + A_ff^{-1} (rhs - A u)_f on level 0 (exact; the converged limit of CG)."""
+    lev0 = prob.h.levels[0]
+    F = prob.coarse_free
+    if len(F) == 0:
+        return
+    r = (rhs - lev0.A @ u)[F]
+    u[F] += scipy.linalg.cho_solve(prob.coarse_factor, r)
+
+
+def vcycle(prob: Problem, l: int, u: np.ndarray, rhs: np.ndarray, pre: int = 2, post: int = 1) -> None:
+    """One V(pre, post)-cycle on level l for A_l u = rhs (in place)."""
+    h = prob.h
+    if l == 0:
+        coarse_solve(prob, u, rhs)
+        return
+    lev = h.levels[l]
+    for _ in range(pre):
+        smooth(lev, u, rhs)
+    r = residual(lev, u, rhs)
+    rc = lev.P.T @ r                      # restriction = transpose of interpolation
+    uc = np.zeros(len(h.levels[l - 1].keys))
+    vcycle(prob, l - 1, uc, rc, pre, post)
+    corr = lev.P @ uc
+    u[lev.free] += corr[lev.free]
+    for _ in range(post):
+        smooth(lev, u, rhs)
+
+
+def fmg(prob: Problem, nu: int = 2, pre: int = 2, post: int = 1, n_extra: int = 0):
+    """Alg. 4 FMG: returns (u_L, [w_0 .. w_{L-1}], [u_0 .. u_L] after their V-cycles).
+
+    w_l is the prolongated level-l solution stored on level l+1 (before the level-(l+1)
+    V-cycles).  n_extra additional V-cycles on level L do not update w (Sec. 5).
+    """
+    h = prob.h
+    L = h.L
+    u = np.where(h.levels[0].dirichlet, prob.g[0], 0.0)
+    ws, us = [], []
+    for l in range(L + 1):
+        for _ in range(nu):
+            vcycle(prob, l, u, prob.b[l], pre, post)
+        us.append(u.copy())
+        if l < L:
+            fine = h.levels[l + 1]
+            u = fine.P @ u
+            u[fine.dirichlet] = prob.g[l + 1][fine.dirichlet]
+            ws.append(u.copy())
+    for _ in range(n_extra):
+        vcycle(prob, L, u, prob.b[L], pre, post)
+    return u, ws, us
+
+
+# --------------------------------------------------------------------------------------
+# Error estimator (Alg. 4 ErrorEstimate; Eqs. (4.5), (4.6), (4.10), (4.14))
+# --------------------------------------------------------------------------------------
+
+def local_mass_sq(lev: Level, e: np.ndarray, n_cells: int) -> np.ndarray:
+    """Per macro T: e^T M_{l,T} e, summing the element mass forms of micro elements inside T."""
+    ee = e[lev.elems]
+    per_elem = np.einsum("ea,eab,eb->e", ee, lev.Me, ee)
+    return np.bincount(lev.emacro, weights=per_elem, minlength=n_cells)
+
+
+def prolong_to_finest(h: Hierarchy, v: np.ndarray, l: int) -> np.ndarray:
+    """I_l^L v for a level-l nodal vector."""
+    for m in range(l + 1, h.L + 1):
+        v = h.levels[m].P @ v
+    return v
+
+
+def estimate(h: Hierarchy, u_L: np.ndarray, ws, j: int = 1):
+    """Alg. 4 ErrorEstimate with offset j (l = L - j), plus the local indicators.
+
+    Returns a dict with
+      err_l, err_lm1  : ||e~_l||, ||e~_{l-1}|| (L2 via the mass matrix)
+      theta           : theta~_l = ||e~_l|| / ||e~_{l-1}||          (Eq. 4.5b)
+      eta_j           : theta~_l^j ||e~_l||                          (Eq. 4.6)
+      eta_T           : ||e~_{L-1}||_{L2(T)} per macro (eta'_{1,T}, Eq. 4.14, Sec. 4.4)
+      eta_jT          : theta~_{l,T}^j ||e~_l||_T per macro          (Eq. 4.10)
+      sq_l_T, sq_lm1_T: per-macro squared local norms of e~_l and e~_{l-1}
+    """
+    L = h.L
+    l = L - j
+    if not (1 <= l <= L - 1):
+        raise ValueError("need 1 <= j <= L-1")
+    levL = h.levels[L]
+    e_l = u_L - prolong_to_finest(h, ws[l], l + 1)          # w_l lives on level l+1
+    e_lm1 = u_L - prolong_to_finest(h, ws[l - 1], l)         # w_{l-1} lives on level l
+    sq_l = local_mass_sq(levL, e_l, h.n_cells)
+    sq_lm1 = local_mass_sq(levL, e_lm1, h.n_cells)
+    e_L1 = u_L - ws[L - 1]
+    sq_T = local_mass_sq(levL, e_L1, h.n_cells)
+    err_l = math.sqrt(sq_l.sum())
+    err_lm1 = math.sqrt(sq_lm1.sum())
+    theta = err_l / err_lm1 if err_lm1 > 0 else 0.0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        theta_T = np.where(sq_lm1 > 0, np.sqrt(sq_l / sq_lm1), 0.0)
+    return dict(err_l=err_l, err_lm1=err_lm1, theta=theta, eta_j=theta ** j * err_l,
+                eta_T=np.sqrt(sq_T), eta_jT=theta_T ** j * np.sqrt(sq_l),
+                sq_l_T=sq_l, sq_lm1_T=sq_lm1, sq_T=sq_T)
+
+
+def l2_error_sq(h: Hierarchy, u_L: np.ndarray, u_exact) -> float:
+    """||I u - u_L||_M^2 on level L (nodal interpolant of the exact solution)."""
+    lev = h.levels[h.L]
+    e = u_exact(lev.x) - u_L
+    return float(e @ (lev.M @ e))
+
+
+# --------------------------------------------------------------------------------------
+# Theorem 4.1 and Corollaries 4.3 / 4.4 (effectivity constants)
+# --------------------------------------------------------------------------------------
+
+def theorem41_constants(theta: float, j: int, eps: float = 0.0):
+    """(C1, C2) of Theorem 4.1 with theta_eps = (1+eps) theta."""
+    te = (1.0 + eps) * theta
+    c1 = (1.0 + eps) ** (-j) * (1.0 - te ** j) ** (j + 1) / (1.0 + te ** (j + 1)) ** j
+    c2 = (1.0 + eps) ** j * (1.0 + te ** j) ** (j + 1) / (1.0 - te ** (j + 1)) ** j
+    return c1, c2
+
+
+def corollary_dgamma_bounds(theta_min: float, theta_max: float, j: int, eps: float = 0.0):
+    """Upper bounds on the local effectivity spread for eta_{j,T} (Cor. 4.3) and eta'_{j,T} (Cor. 4.4).
+
+    theta_max is the already (1+eps)-inflated worst local factor, as in the paper.
+    """
+    tx = theta_max
+    scaled = ((1.0 + eps) ** (2 * j) * ((1.0 + tx ** (j + 1)) / (1.0 - tx ** (j + 1))) ** j
+              * ((1.0 + tx ** j) / (1.0 - tx ** j)) ** (j + 1))
+    unscaled = (theta_min ** (-j) + 1.0) / (tx ** (-j) - 1.0)
+    return scaled, unscaled
+
+
+# --------------------------------------------------------------------------------------
+# Marking (Sec. 5.1: mark a fixed fraction of the macro elements with the largest indicator)
+# --------------------------------------------------------------------------------------
+
+def mark_top_fraction(eta: np.ndarray, fraction: float) -> np.ndarray:
+    """Boolean mask: n = max(1, ceil(fraction * N - 1e-9)); eta* = n-th largest value
+    (ties ordered by index); mark every T with eta_T >= (1 - 1e-8) eta*."""
+    eta = np.asarray(eta, dtype=np.float64)
+    N = len(eta)
+    if N == 0:
+        return np.zeros(0, dtype=bool)
+    n = max(1, int(math.ceil(fraction * N - 1e-9)))
+    n = min(n, N)
+    order = sorted(range(N), key=lambda i: (-eta[i], i))
+    star = eta[order[n - 1]]
+    return eta >= (1.0 - 1e-8) * star
+
+
+# --------------------------------------------------------------------------------------
+# 2D red-green refinement of the macro mesh (Sec. 3), greens reverted before each step
+# --------------------------------------------------------------------------------------
+
+class RG2D:
+    """Red-green refinement of a triangle mesh, written out from Sec. 3's description.
+
+    red   : split a triangle (v0,v1,v2) into 4 through its edge midpoints m01, m12, m20;
+            children (v0,m01,m20), (m01,v1,m12), (m20,m12,v2), (m12,m20,m01).
+    green : bisect a triangle with exactly one split edge from the opposite vertex a:
+            with (a,b,c) the rotation of (v0,v1,v2) that starts at a, children (a,b,m), (a,m,c).
+    One step (marked = flags on the current conforming mesh):
+      1. revert every green pair to its parent; a marked green child marks the parent;
+      2. red-refine the marked triangles, then repeat: red-refine every triangle that has
+         two or more split edges, or a split edge whose half is split again, until none;
+      3. green-bisect every triangle with exactly one split edge.
+    An edge (a,b) is split when its midpoint vertex exists.  New midpoints are numbered in
+    creation order: triangles in list order, edges (v0v1, v1v2, v2v0).  Refined triangles
+    are replaced in place by their children, so the cell order is deterministic.
+    """
+
+    def __init__(self, coords, cells):
+        self.coords = [tuple(float(c) for c in p) for p in np.asarray(coords, dtype=np.float64)]
+        # entries: (v0, v1, v2, green_parent or None, child index)
+        self.tris = [(int(a), int(b), int(c), None, -1) for a, b, c in np.asarray(cells)]
+        self.mid = {}
+
+    def mesh(self):
+        return (np.array(self.coords, dtype=np.float64),
+                np.array([t[:3] for t in self.tris], dtype=np.int32).reshape(-1, 3))
+
+    def _midpoint(self, a, b, create):
+        key = (min(a, b), max(a, b))
+        m = self.mid.get(key)
+        if m is None and create:
+            pa, pb = self.coords[a], self.coords[b]
+            self.coords.append(((pa[0] + pb[0]) * 0.5, (pa[1] + pb[1]) * 0.5))
+            m = len(self.coords) - 1
+            self.mid[key] = m
+        return m
+
+    def _red(self, t):
+        v0, v1, v2 = t
+        m01 = self._midpoint(v0, v1, True)
+        m12 = self._midpoint(v1, v2, True)
+        m20 = self._midpoint(v2, v0, True)
+        return [(v0, m01, m20), (m01, v1, m12), (m20, m12, v2), (m12, m20, m01)]
+
+    def _split_info(self, t):
+        v = t
+        split = []
+        over = False
+        for e in range(3):
+            a, b = v[e], v[(e + 1) % 3]
+            m = self._midpoint(a, b, False)
+            if m is not None:
+                split.append(e)
+                if self._midpoint(a, m, False) is not None or self._midpoint(m, b, False) is not None:
+                    over = True
+        return split, over
+
+    def refine(self, marked):
+        marked = np.asarray(marked).astype(bool)
+        if len(marked) != len(self.tris):
+            raise ValueError("one flag per current cell")
+        # 1. revert greens
+        R, flags = [], []
+        i = 0
+        while i < len(self.tris):
+            v0, v1, v2, parent, ci = self.tris[i]
+            if parent is not None:
+                nxt = self.tris[i + 1]
+                if ci != 0 or nxt[3] != parent or nxt[4] != 1:
+                    raise AssertionError("green pair not adjacent")
+                R.append(parent)
+                flags.append(bool(marked[i] or marked[i + 1]))
+                i += 2
+            else:
+                R.append((v0, v1, v2))
+                flags.append(bool(marked[i]))
+                i += 1
+        # 2. red refinement and closure
+        while any(flags):
+            newR = []
+            for t, fl in zip(R, flags):
+                newR.extend(self._red(t) if fl else [t])
+            R = newR
+            flags = []
+            for t in R:
+                split, over = self._split_info(t)
+                flags.append(len(split) >= 2 or over)
+        # 3. green closure
+        out = []
+        for t in R:
+            split, _ = self._split_info(t)
+            if len(split) == 1:
+                e = split[0]
+                a = t[(e + 2) % 3]
+                b = t[e]
+                c = t[(e + 1) % 3]
+                m = self._midpoint(b, c, False)
+                out.append((a, b, m, t, 0))
+                out.append((a, m, c, t, 1))
+            else:
+                out.append((t[0], t[1], t[2], None, -1))
+        self.tris = out
+
+
+# --------------------------------------------------------------------------------------
+# Adjoint of the discrete solve: gradients of J(u) = u^T M_S u (no counterpart in the paper)
+# --------------------------------------------------------------------------------------
+
+def exact_solve(prob: Problem) -> np.ndarray:
+    """Exact discrete solution u_L of A_L u = b_L with Dirichlet values g_L (sparse LU)."""
+    import scipy.sparse.linalg as spla
+    h = prob.h
+    lev = h.levels[h.L]
+    F = np.nonzero(lev.free)[0]
+    D = np.nonzero(lev.dirichlet)[0]
+    u = np.zeros(len(lev.keys))
+    u[D] = prob.g[h.L][D]
+    rhs = prob.b[h.L][F] - lev.A[F][:, D] @ u[D]
+    u[F] = spla.spsolve(lev.A[F][:, F].tocsc(), rhs)
+    return u
+
+
+def adjoint_gradients(h: Hierarchy, u_L: np.ndarray, in_S: np.ndarray):
+    """J = sum_{T in S} u^T M_{L,T} u and its gradients w.r.t. nodal f and per-macro k_T.
+
+    Solves A_ff lam_f = 2 (M_S u)_f (lam = 0 on Dirichlet nodes) exactly, then
+      dJ/df = M_L lam          (b_L = M_L f_L),
+      dJ/dk_T = -lam^T A_T^(1) u  (A_L = sum_T k_T A_T^(1)).
+    """
+    import scipy.sparse.linalg as spla
+    lev = h.levels[h.L]
+    in_S = np.asarray(in_S, dtype=bool)
+    J = float(local_mass_sq(lev, u_L, h.n_cells)[in_S].sum())
+    ee = u_L[lev.elems]
+    sel = in_S[lev.emacro]
+    g = np.zeros(len(lev.keys))
+    np.add.at(g, lev.elems[sel].ravel(), 2.0 * np.einsum("eab,eb->ea", lev.Me[sel], ee[sel]).ravel())
+    F = np.nonzero(lev.free)[0]
+    lam = np.zeros(len(lev.keys))
+    lam[F] = spla.spsolve(lev.A[F][:, F].tocsc(), g[F])
+    grad_f = lev.M @ lam
+    ll = lam[lev.elems]
+    unit = lev.Ke / h.k[lev.emacro][:, None, None]
+    per_elem = np.einsum("ea,eab,eb->e", ll, unit, ee)
+    grad_k = -np.bincount(lev.emacro, weights=per_elem, minlength=h.n_cells)
+    return J, grad_f, grad_k, lam
