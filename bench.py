@@ -1,0 +1,355 @@
+"""Benchmark of the HHG FMG hot path on GB300: FMG solve + error estimator + marking per step.
+
+Workload (default): unit cube, 4^3 cubes x 6 Kuhn tets = 384 macro tets, L = 6 structured levels
+(16,581,375 unknowns), f = 3 pi^2 prod sin(pi x_i), g = 0; FMG with nu = 2 V(2,1) cycles per
+level, estimator j = 1, marking of the top 12.5 %.  Precision: binary64 (--precision fp64) or
+binary32 V-cycles with bfloat16 correction storage inside binary64 iterative refinement
+(--precision mixed, the default), at the binary64 discretisation error.
+
+Metric: unknowns / (time of hhg_fmg_solve + hhg_estimate + hhg_mark) per step, device-timed with
+CUDA events on the library's stream, inputs resident in HBM.  e2e: the same through host buffers
+(pinned H2D of f and g, D2H of u_L and eta_T inside the timed region).
+
+N GPUs: independent replicas (one full problem per rank, no data-path collective), value = sum of
+unknowns over ranks / max time over ranks.
+--impl reference: the CPU oracle (plain FP64 numpy/scipy, one core) on a bounded sample.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MIXED_DEFAULT = dict(storage=1, ir_steps=2, ir_vcycles=2)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="cube384_l6")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed
+
+def dist_init(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if os.environ.get("HHG_BENCH_GLOO") is None else "gloo")
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- workload
+
+def make_problem(name, L=None):
+    import workloads as W
+    co, ce, LL, f, g, k, ue = W.workload(name, L)
+    return co, ce, LL, f, g, k, ue
+
+
+def params_for(precision, P):
+    if precision == "fp64":
+        return P.solve_params(nu=2, pre=2, post=1, n_extra=0, precision=0)
+    return P.solve_params(nu=2, pre=2, post=1, n_extra=0, precision=1, **MIXED_DEFAULT)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# measured binary64 FMA throughput of this machine's GB300 (probe in profiles/fp64_fma_peak.md)
+FP64_PEAK_TFLOPS = 1.205
+
+
+# ----------------------------------------------------------------------------- arms
+
+def run_gpu(args, rank, world):
+    import numpy as np
+    import torch
+
+    import paper_2508_06049_gb300 as P
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    s = torch.cuda.Stream()
+    co, ce, L, f, g, k, ue = make_problem(args.workload)
+    mesh = P.Mesh(co, ce, L, stream=s)
+    if k is not None:
+        mesh.set_coefficient(k)
+    x = mesh.level_coords(L)
+    fh = torch.from_numpy(np.ascontiguousarray(f(x))).pin_memory()
+    gh = torch.from_numpy(np.ascontiguousarray(g(x))).pin_memory()
+    with torch.cuda.stream(s):
+        fd = fh.to("cuda", non_blocking=True)
+        gd = gh.to("cuda", non_blocking=True)
+        ud = torch.empty_like(fd)
+    s.synchronize()
+    mesh.set_data(fd, gd)
+    prm = params_for(args.precision, P)
+    unknowns = mesh.info.n_unknowns
+    frac = 0.125
+
+    def step():
+        mesh.solve(prm, out=ud)
+        est = mesh.estimate(1)
+        P.mark(est["eta_T"], frac)
+        return est
+
+    for _ in range(args.warmup):
+        est = step()
+    # accuracy of this configuration against the exact solution (workloads with a known u)
+    err = None
+    if ue is not None:
+        uu = ud.cpu().numpy()
+        e = np.ascontiguousarray(ue(x) - uu)
+        Me = mesh.apply(L, 1, e)
+        _, inv, cnt = np.unique(np.round(x * 2 ** (L + 3)).astype(np.int64), axis=0, return_inverse=True,
+                                return_counts=True)
+        err = math.sqrt(float(np.sum(e * Me / cnt[inv.ravel()])))
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = ClockSampler(dev)
+    clk.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    ev0.record(s)
+    for _ in range(args.steps):
+        step()
+    ev1.record(s)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    ms_dev = ev0.elapsed_time(ev1) / args.steps
+    barrier(world)
+    ms = allmax(ms_dev, world)
+    value = world * unknowns / (ms * 1e-3)
+
+    # e2e through host buffers
+    e2e = None
+    if not args.no_e2e:
+        uh = torch.empty(len(x), dtype=torch.float64).pin_memory()
+        def step_e2e():
+            mesh.set_data(fh, gh)
+            mesh.solve(prm, out=uh)
+            est = mesh.estimate(1)
+            P.mark(est["eta_T"], frac)
+        for _ in range(2):
+            step_e2e()
+        barrier(world)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(s)
+        ne = max(3, args.steps // 5)
+        for _ in range(ne):
+            step_e2e()
+        a1.record(s)
+        torch.cuda.synchronize()
+        ms_e2e = allmax(a0.elapsed_time(a1) / ne, world)
+        e2e = {"value": world * unknowns / (ms_e2e * 1e-3), "unit": "DoF/s", "ms_per_step": ms_e2e,
+               "h2d_bytes_per_step": 2 * 8 * len(x), "d2h_bytes_per_step": 8 * len(x) + 8 * len(ce)}
+
+    # roofline of the dominant kernel: the level-L interior smoothing stage, timed with CUDA events
+    # on the library's stream (same launch configuration as inside the solve graph)
+    pk, pk_kind = peaks()
+    prec_id = 0 if args.precision == "fp64" else 1
+    mesh.profile_kernel(0, prec_id, 3)
+    torch.cuda.synchronize()
+    reps = 50
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    k0.record(s)
+    units, kbytes, kflops = mesh.profile_kernel(0, prec_id, reps)
+    k1.record(s)
+    torch.cuda.synchronize()
+    ms_k = k0.elapsed_time(k1) / reps
+    gbs = kbytes / (ms_k * 1e-3) / 1e9
+    tfl = kflops / (ms_k * 1e-3) / 1e12
+    if args.precision == "fp64":
+        rf_obj = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                  "frac": tfl / FP64_PEAK_TFLOPS, "traffic": None,
+                  "peak_kind": "measured binary64 FMA throughput (profiles/fp64_fma_peak.md)",
+                  "hbm_gbs": gbs, "hbm_frac": gbs / pk.get("hbm_gbs", 6800.0)}
+    else:
+        peak = pk.get("hbm_gbs", 6800.0)
+        rf_obj = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                  "traffic": None, "peak_kind": pk_kind + " (MEASURED_PEAKS.json hbm_gbs)", "tflops": tfl}
+    rf_obj.update({"kernel": "k_smooth_interior (level L, colour 0)", "ms_per_launch": ms_k,
+                   "units_per_launch": units, "algorithmic_bytes_per_launch": kbytes,
+                   "algorithmic_flops_per_launch": kflops})
+    launches = mesh.launch_count(prm) + 7   # solve graph + estimator kernels (j = 1)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload)
+    return dict(value=value, ms=ms, wall=wall, clocks=clocks, e2e=e2e, roofline=rf_obj, cpu=cpu, err=err,
+                unknowns=unknowns, launches=launches, eta=est["eta_j"])
+
+
+def cpu_baseline(workload, budget_s=20.0):
+    """The oracle as it stands on a bounded sample: the same workload at a lower level."""
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from oracle import hhg_oracle as O
+    co, ce, L, f, g, k, ue = make_problem(workload)
+    Ls = min(L, 4 if co.shape[1] == 3 else 6)
+    co, ce, Ls, f, g, k, ue = make_problem(workload, Ls)
+    h = O.Hierarchy(co, ce, Ls, k=k)
+    prob = O.Problem(h, f, g)
+    unknowns = int(h.levels[Ls].free.sum())
+    times = []
+    t_end = time.perf_counter() + budget_s
+    while True:
+        t0 = time.perf_counter()
+        u, ws, _ = O.fmg(prob, 2, 2, 1)
+        est = O.estimate(h, u, ws, 1)
+        O.mark_top_fraction(est["eta_T"], 0.125)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() > t_end or len(times) >= 5:
+            break
+    t = statistics.median(times)
+    return {"value": unknowns / t, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+            "sample": "%s at L=%d (%d unknowns): FMG nu=2 V(2,1) + estimator + marking, median of %d"
+                      % (workload, Ls, unknowns, len(times)), "seconds_per_step": t}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from oracle import hhg_oracle as O
+    co, ce, L, f, g, k, ue = make_problem(args.workload)
+    Ls = min(L, 4 if co.shape[1] == 3 else 6)
+    co, ce, Ls, f, g, k, ue = make_problem(args.workload, Ls)
+    h = O.Hierarchy(co, ce, Ls, k=k)
+    prob = O.Problem(h, f, g)
+    unknowns = int(h.levels[Ls].free.sum())
+    for _ in range(args.warmup):
+        u, ws, _ = O.fmg(prob, 2, 2, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u, ws, _ = O.fmg(prob, 2, 2, 1)
+        est = O.estimate(h, u, ws, 1)
+        O.mark_top_fraction(est["eta_T"], 0.125)
+    t = (time.perf_counter() - t0) / args.steps
+    value = unknowns / t
+    return dict(value=value, ms=t * 1e3, sample="%s at L=%d (%d unknowns)" % (args.workload, Ls, unknowns))
+
+
+def main():
+    args = parse()
+    rank, world = dist_init(args.gpus)
+    config = {"workload": args.workload, "macro_cells": None, "L": None, "precision": args.precision,
+              "cycle": "FMG nu=2 V(2,1), estimator j=1, marking 12.5%",
+              "l2": "level-L vectors exceed the 129 MB L2 (no flush needed)"}
+    co, ce, L, *_ = make_problem(args.workload)
+    config["macro_cells"] = int(len(ce))
+    config["L"] = int(L)
+    if args.impl == "reference":
+        r = run_reference(args, rank, world)
+        if rank == 0:
+            line = {"impl": "reference", "metric": "FMG DoF/s (FMG + estimator + marking per step)",
+                    "value": r["value"], "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
+                    "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
+                    "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                    "cpu_baseline": {"value": r["value"], "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                                     "sample": r["sample"]},
+                    "e2e": {"value": r["value"], "unit": "DoF/s", "h2d_bytes_per_step": 0,
+                            "d2h_bytes_per_step": 0}}
+            print(json.dumps(line), flush=True)
+        return
+    r = run_gpu(args, rank, world)
+    if rank == 0:
+        line = {"metric": "FMG DoF/s (FMG + estimator + marking per step)", "value": r["value"], "unit": "DoF/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "f32+bf16-storage+f64-refinement",
+                "data": "synthetic", "config": config, "unknowns": r["unknowns"],
+                "l2_error_vs_exact": r["err"], "eta_1": r["eta"], "clocks": r["clocks"], "e2e": r["e2e"],
+                "roofline": r["roofline"], "cpu_baseline": r["cpu"], "gpu_launches": r["launches"] * args.steps,
+                "host_wall_s": r["wall"]}
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * hhg.h - C ABI of the GB300 full-multigrid (FMG) solver on hierarchical hybrid grids.
+ *
+ * Method: B. Mann, U. Ruede, "kl-refinement: An adaptive mesh refinement scheme for
+ * hierarchical hybrid grids" (arXiv 2508.06049).
+ *   - Sec. 2: an unstructured coarse mesh T_0 of macro triangles (2D) or tetrahedra (3D),
+ *     each refined uniformly L times (red refinement / Bey's rule).
+ *   - Sec. 4.4, Eq. (4.15) and Eq. (5.1): P1 finite elements for -div(k grad u) = f with k
+ *     constant on each macro element, Dirichlet data g.
+ *   - Sec. 4.4, Alg. 4: FMG with nu V-cycles per level and Gauss-Seidel smoothing, storing the
+ *     prolongated coarse solutions w_l; the ErrorEstimate procedure and the local indicators
+ *     eta_T (Eq. 4.14, Sec. 4.4).
+ *   - Sec. 5.1 / Sec. 3: marking of a top fraction of macro elements and 2D red-green
+ *     refinement of the macro mesh (kl-refinement, Alg. 2).
+ *
+ * Conventions (all entry points):
+ *   - Every function returns an hhg_status; on failure hhg_last_error() gives a message
+ *     (thread-local).  No function aborts the process.
+ *   - Arrays are owned by the caller.  "host or device" arrays may live in host memory or in
+ *     CUDA device memory of the mesh's device; the library copies through unified addressing.
+ *   - Level-l vectors use the library's node layout: for each macro cell (in input order) its
+ *     closure lattice packed plane by plane (see hhg_level_coords).  Nodes on shared macro
+ *     vertices/edges/faces appear once per adjacent cell; inputs must give them equal values,
+ *     outputs give them equal values.  N_l = n_cells * closure(2^l) entries, closure(n) =
+ *     (n+1)(n+2)/2 in 2D and (n+1)(n+2)(n+3)/6 in 3D.
+ *   - All device work of a mesh is ordered on the CUDA stream given at creation (NULL = the
+ *     legacy default stream).  Functions that return host results synchronise that stream.
+ *   - Floating-point is IEEE binary64 unless the solve parameters select the mixed mode.
+ */
+#ifndef HHG_H
+#define HHG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hhg_mesh_s* hhg_mesh;
+typedef struct hhg_rg2d_s* hhg_rg2d;
+
+typedef enum {
+  HHG_OK = 0,
+  HHG_ERR_ARG = 1,            /* invalid argument (null pointer, size, range)              */
+  HHG_ERR_MESH = 2,           /* invalid or degenerate coarse mesh                          */
+  HHG_ERR_CUDA = 3,           /* a CUDA runtime call failed (message names it)              */
+  HHG_ERR_OOM = 4,            /* device or host allocation failed                           */
+  HHG_ERR_NOT_CONVERGED = 5,  /* an iteration did not reach its target                      */
+  HHG_ERR_DIVERGED = 6,       /* NaN/Inf or growth detected in the solution                 */
+  HHG_ERR_STATE = 7           /* call order violated (e.g. estimate before a solve)         */
+} hhg_status;
+
+/* Solve parameters (Alg. 4).  nu: V-cycles per FMG level; pre/post: Gauss-Seidel sweeps
+ * before/after the coarse correction; n_extra: extra V-cycles on level L after FMG (they do
+ * not update w_l, Sec. 5).
+ * precision = 0: every step in binary64.
+ * precision = 1 (mixed, no counterpart in the paper): iterative refinement whose residual
+ *   r = b - A u and update u += c are binary64 on level L; the correction c solves A c = r with
+ *   FMG (first step) or ir_vcycles V-cycles (later steps) computed in binary32, with the level
+ *   vectors of the correction stored as `storage` (0 = binary32, 1 = bfloat16, 2 = binary16)
+ *   and accumulated in binary32.  ir_steps refinement steps follow the first one. */
+typedef struct {
+  int nu, pre, post, n_extra;
+  int precision;
+  int storage;
+  int ir_steps;
+  int ir_vcycles;
+} hhg_solve_params;
+
+typedef struct {
+  int dim, L, n_cells, n_verts;
+  long long n_nodes[16];      /* N_l per level (layout size, with interface copies)        */
+  long long n_unknowns;       /* free (non-Dirichlet) distinct nodes on level L            */
+  long long n_distinct;       /* distinct nodes on level L                                 */
+  long long device_bytes;     /* device memory held by the mesh                            */
+  int n_colours;              /* macro-interior colours of the smoother (max over cells)   */
+} hhg_mesh_info;
+
+typedef struct {
+  double eta_j;    /* theta~_l^j ||e~_l||, l = L - j          (Eq. 4.6)  */
+  double theta;    /* ||e~_l|| / ||e~_{l-1}||                 (Eq. 4.5b) */
+  double err_l;    /* ||e~_l||     = ||u_L - I w_l||_{L2}     (Eq. 4.5a) */
+  double err_lm1;  /* ||e~_{l-1}|| = ||u_L - I w_{l-1}||_{L2}            */
+  double err_Lm1;  /* ||e~_{L-1}|| = sqrt(sum_T eta_T^2)                 */
+} hhg_estimate_out;
+
+/* Create the HHG hierarchy for a coarse mesh (Sec. 2) and all device data for levels 0..L.
+ * dim: 2 (triangles) or 3 (tetrahedra).  coords: host, n_verts*dim.  cells: host,
+ * n_cells*(dim+1) vertex ids, 0-based; cell vertex order defines the lattice orientation.
+ * vert_is_dirichlet: host, n_verts flags, or NULL = every vertex on the boundary.  A boundary
+ * edge/face is Dirichlet when all its vertices are.  L: 1..9 (2D) or 1..8 (3D).
+ * cuda_stream: a cudaStream_t or NULL.  Errors: HHG_ERR_ARG, HHG_ERR_MESH (degenerate cell,
+ * non-manifold facet, too many coarse unknowns for the direct coarse solve), HHG_ERR_OOM. */
+hhg_status hhg_mesh_create(int dim, int n_verts, const double* coords, int n_cells, const int* cells,
+                           const unsigned char* vert_is_dirichlet, int L, void* cuda_stream,
+                           hhg_mesh* out);
+hhg_status hhg_mesh_destroy(hhg_mesh mesh);
+hhg_status hhg_mesh_get_info(hhg_mesh mesh, hhg_mesh_info* info);
+
+/* Coordinates of the level-l nodes in the layout above (x = x_0 + J p / 2^l per cell).
+ * xyz: host or device, N_l*dim doubles, node-major. */
+hhg_status hhg_level_coords(hhg_mesh mesh, int level, double* xyz);
+
+/* Piecewise-constant coefficient k_T > 0 per macro cell (Eq. 5.1 with k); NULL = 1. */
+hhg_status hhg_set_coefficient(hhg_mesh mesh, const double* k_per_cell);
+
+/* Source f and Dirichlet data g at the level-L nodes (host or device, N_L each).  Copied. */
+hhg_status hhg_set_data(hhg_mesh mesh, const double* f_L, const double* g_L);
+
+/* FMG solve (Alg. 4): b_l = M_l f_l on every level, FMG with the given parameters, w_l kept
+ * for hhg_estimate.  u_L: host or device, N_L doubles (output).  Returns HHG_ERR_DIVERGED
+ * if the result holds NaN/Inf. */
+hhg_status hhg_fmg_solve(hhg_mesh mesh, const hhg_solve_params* params, double* u_L);
+
+/* ErrorEstimate of Alg. 4 with offset j (1 <= j <= L-1) on the last solve.
+ * eta_T: host, n_cells (may be NULL): ||u_L - w_{L-1}||_{L2(T)} over the micro elements of
+ * macro T including its boundary (eta'_{1,T}, Eq. 4.14).  eta_jT: host, n_cells (may be NULL):
+ * scaled local estimate theta~_{l,T}^j ||e~_l||_T (Eq. 4.10).  out: host, global values. */
+hhg_status hhg_estimate(hhg_mesh mesh, int j, double* eta_T, double* eta_jT, hhg_estimate_out* out);
+
+/* Read an internal level vector of the last solve into `out` (host or device, N_l doubles):
+ * which = 0: u_l after its FMG V-cycles (l = L: the solution, l < L: overwritten by later
+ * corrections, so only l = L is meaningful after the solve), 1: w_l (l = 0..L-1, stored on
+ * level l+1, N_{l+1} doubles), 2: b_l summed over interface copies (N_l). */
+hhg_status hhg_get_vector(hhg_mesh mesh, int which, int level, double* out);
+
+/* Operator application for testing: out = Op_l in on level l with in/out of N_l doubles
+ * (host or device), interface rows summed over adjacent cells.
+ * op = 0: stiffness A_l (all rows, Dirichlet rows included as plain P1 rows),
+ * op = 1: mass M_l, op = 2: interpolation from level l-1 (in has N_{l-1} entries),
+ * op = 3: nsweeps Gauss-Seidel sweeps in place on out (the initial guess) with rhs M_l in. */
+hhg_status hhg_apply(hhg_mesh mesh, int level, int op, const double* in, double* out, int nsweeps);
+
+/* Top-fraction marking (Sec. 5.1), host only: n = max(1, ceil(fraction*n - 1e-9)) elements
+ * with the largest eta, plus every element within a relative 1e-8 of the n-th value (ties).
+ * marked: host, n flags (output).  n_marked may be NULL. */
+hhg_status hhg_mark(int n, const double* eta, double fraction, unsigned char* marked, int* n_marked);
+
+/* 2D red-green refinement of a macro mesh (Sec. 3), host only.  The object keeps the red
+ * history so that green closures are reverted before the next step.  Rules: red = split
+ * through the edge midpoints; closure: red-refine triangles with >= 2 split edges or a split
+ * edge whose half is split again; green = bisect a triangle with one split edge from the
+ * opposite vertex.  New vertices are appended in creation order. */
+hhg_status hhg_rg2d_create(int n_verts, const double* coords, int n_cells, const int* cells, hhg_rg2d* out);
+hhg_status hhg_rg2d_refine(hhg_rg2d rg, const unsigned char* marked /* host, one flag per current cell */);
+/* Current conforming mesh; pass NULL arrays to query the sizes first. */
+hhg_status hhg_rg2d_mesh(hhg_rg2d rg, int* n_verts, double* coords, int* n_cells, int* cells);
+hhg_status hhg_rg2d_destroy(hhg_rg2d rg);
+/* Marking + one red-green step: marked (host, n_cells of the current mesh, may be NULL). */
+hhg_status hhg_mark_refine(hhg_rg2d rg, const double* eta_T, double fraction, unsigned char* marked);
+
+/* Adjoint of the discrete solve (no counterpart in the paper): for J(u) = u^T M_S u with
+ * M_S the mass matrix of the micro elements inside the macro cells flagged in in_S, on the
+ * solution of the last hhg_fmg_solve, solve A lambda = 2 M_S u (lambda = 0 on Dirichlet nodes)
+ * with FMG + params->n_extra V-cycles and return
+ *   J (host), grad_f = M_L lambda (dJ/d nodal f_L; host or device, N_L, may be NULL),
+ *   grad_k[T] = -lambda^T A_T^(1) u (dJ/dk_T; host, n_cells, may be NULL). */
+hhg_status hhg_adjoint_l2(hhg_mesh mesh, const hhg_solve_params* params, const unsigned char* in_S,
+                          double* J, double* grad_f, double* grad_k);
+
+/* Host self-check of the lattice index arithmetic against brute force (no GPU needed).
+ * Returns 0 if consistent, otherwise the number of mismatches. */
+int hhg_lattice_selfcheck(int dim, int n);
+
+/* Profiling support.  Enqueue `reps` launches of one kernel of the solve on the mesh's stream,
+ * exactly as the solve launches it, without synchronising (bracket it with events on that stream).
+ * kernel 0: macro-interior smoothing stage of colour 0 on level L for the first cell group.
+ * precision 0: the binary64 kernel; 1: the binary32 kernel of the mixed path (needs one mixed solve
+ * first).  units: nodes updated per launch; bytes / flops: algorithmic bytes and floating-point
+ * operations of one launch (the model is stated in the library's design notes).  The launches
+ * modify the level-L iterate: run a solve again before hhg_estimate. */
+hhg_status hhg_profile_kernel(hhg_mesh mesh, int kernel, int precision, int reps, long long* units,
+                              double* bytes, double* flops);
+
+/* Number of kernel nodes in the captured graph of a solve with these parameters (after a first
+ * hhg_fmg_solve with the same parameters), i.e. kernel launches per solve. */
+hhg_status hhg_solve_launch_count(hhg_mesh mesh, const hhg_solve_params* params, long long* n_kernels);
+
+/* Debug builds (compiled with HHG_CHECK): first recorded out-of-range index of a kernel
+ * (code, block x, block y, thread, index, bound, 0, 1), then cleared; all zeros otherwise. */
+hhg_status hhg_debug_check(long long* out8);
+
+const char* hhg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HHG_H */

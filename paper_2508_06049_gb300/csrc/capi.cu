@@ -1,0 +1,592 @@
+// C ABI entry points: mesh life cycle, data, the FMG solve (Alg. 4) captured into CUDA graphs,
+// the error estimator (Alg. 4 ErrorEstimate), test operators and the adjoint.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace hhg {
+const char* last_error();
+void launch_init_coarse_g(hhg_mesh_s* m, const double* g, cudaStream_t s);
+void launch_fmg_prolong_g(hhg_mesh_s* m, int l, const double* g, double* w, cudaStream_t s);
+void launch_restrict_rhs_chain(hhg_mesh_s* m, cudaStream_t s);
+hhg_status read_check(long long* out);
+hhg_status preload_kernels();
+hhg_status mixed_profile_interior(hhg_mesh_s* m, int reps, cudaStream_t s, long long* units, double* bytes,
+                                  double* flops);
+hhg_status mixed_prepare(hhg_mesh_s* m, int storage);
+void mixed_enqueue_solve(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t s);
+}  // namespace hhg
+
+using namespace hhg;
+
+#define CK(call)                                        \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+#define REQUIRE(cond, code, ...) \
+  do {                           \
+    if (!(cond)) {               \
+      set_error(__VA_ARGS__);    \
+      return code;               \
+    }                            \
+  } while (0)
+
+namespace {
+
+#ifdef HHG_CHECK
+// checked build: device pointers are validated before launches, and each launch is synchronised
+hhg_status check_dev_ptr(const void* p, const char* name) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess || a.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    set_error("pointer %s = %p is not device memory", name, p);
+    return HHG_ERR_STATE;
+  }
+  return HHG_OK;
+}
+#define CHECK_PTR(p)                                       \
+  do {                                                     \
+    hhg_status st_ = check_dev_ptr((const void*)(p), #p);  \
+    if (st_ != HHG_OK) return st_;                         \
+  } while (0)
+#define DBG_SYNC(what)                                     \
+  do {                                                     \
+    cudaError_t e_ = cudaStreamSynchronize(s);             \
+    if (e_ == cudaSuccess) e_ = cudaGetLastError();        \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what);     \
+  } while (0)
+#else
+#define CHECK_PTR(p) \
+  do {               \
+  } while (0)
+#define DBG_SYNC(what) \
+  do {                 \
+  } while (0)
+#endif
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+hhg_status check_params(const hhg_mesh_s* m, const hhg_solve_params* p) {
+  REQUIRE(p, HHG_ERR_ARG, "params is NULL");
+  REQUIRE(p->nu >= 1 && p->nu <= 64, HHG_ERR_ARG, "nu must be in [1,64]");
+  REQUIRE(p->pre >= 0 && p->pre <= 64 && p->post >= 0 && p->post <= 64, HHG_ERR_ARG, "pre/post in [0,64]");
+  REQUIRE(p->n_extra >= 0 && p->n_extra <= 10000, HHG_ERR_ARG, "n_extra in [0,10000]");
+  REQUIRE(p->precision == 0 || p->precision == 1, HHG_ERR_ARG, "precision must be 0 or 1");
+  if (p->precision == 1) {
+    REQUIRE(p->storage >= 0 && p->storage <= 2, HHG_ERR_ARG, "storage must be 0, 1 or 2");
+    REQUIRE(p->ir_steps >= 0 && p->ir_steps <= 1000, HHG_ERR_ARG, "ir_steps in [0,1000]");
+    REQUIRE(p->ir_vcycles >= 1 && p->ir_vcycles <= 64, HHG_ERR_ARG, "ir_vcycles in [1,64]");
+  }
+  (void)m;
+  return HHG_OK;
+}
+
+// V(pre, post)-cycle on level l for A u_l = rhs (u_l in place); corrections on coarser levels
+void enqueue_vcycle(hhg_mesh_s* m, int l, const double* rhs, const hhg_solve_params& p, cudaStream_t s) {
+  if (l == 0) {
+    launch_coarse_solve(m, rhs, s);
+    return;
+  }
+  for (int q = 0; q < p.pre; ++q) launch_sweep(m, l, rhs, s, false);
+  launch_residual(m, l, rhs, s);
+  launch_restrict(m, l, m->lv[l].tmp, m->lv[l - 1].rc, s);
+  cudaMemsetAsync(m->lv[l - 1].u, 0, sizeof(double) * (size_t)m->lv[l - 1].N, s);
+  enqueue_vcycle(m, l - 1, m->lv[l - 1].rc, p, s);
+  launch_prolong_add(m, l, s);
+  for (int q = 0; q < p.post; ++q) launch_sweep(m, l, rhs, s, false);
+}
+
+// Alg. 4 FMG.  adjoint = true: right-hand side given on level L in lv[L].b (restricted to the
+// coarser levels), zero Dirichlet data, w_l not stored.
+void enqueue_fmg(hhg_mesh_s* m, const hhg_solve_params& p, bool adjoint, cudaStream_t s) {
+  const int L = m->L;
+  if (!adjoint) {
+    for (int l = 0; l <= L; ++l) launch_build_rhs(m, l, s);
+  } else {
+    launch_restrict_rhs_chain(m, s);
+  }
+  const double* g = adjoint ? nullptr : m->gL;
+  launch_init_coarse_g(m, g, s);
+  for (int l = 0; l <= L; ++l) {
+    for (int q = 0; q < p.nu; ++q) enqueue_vcycle(m, l, m->lv[l].b, p, s);
+    if (l < L) launch_fmg_prolong_g(m, l, g, adjoint ? nullptr : m->lv[l].w, s);
+  }
+  for (int q = 0; q < p.n_extra; ++q) enqueue_vcycle(m, L, m->lv[L].b, p, s);
+  cudaMemsetAsync(m->d_flag, 0, sizeof(int), s);
+  launch_finite_check(m, m->lv[L].u, m->lv[L].N, s);
+}
+
+std::string graph_key(const char* what, const hhg_solve_params& p) {
+  char buf[160];
+  snprintf(buf, sizeof(buf), "%s:%d:%d:%d:%d:%d:%d:%d:%d", what, p.nu, p.pre, p.post, p.n_extra, p.precision,
+           p.storage, p.ir_steps, p.ir_vcycles);
+  return buf;
+}
+
+template <typename F>
+hhg_status run_graph(hhg_mesh_s* m, const std::string& key, F enqueue) {
+  auto it = m->graphs.find(key);
+  if (it == m->graphs.end()) {
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal));
+    enqueue(m->cap);
+    cudaError_t launch_err = cudaGetLastError();
+    cudaError_t e = cudaStreamEndCapture(m->cap, &graph);
+    if (launch_err != cudaSuccess) return cuda_fail(launch_err, "kernel launch during capture");
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    size_t nn = 0;
+    long long nk = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+        for (auto nd : nodes) {
+          cudaGraphNodeType ty;
+          if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++nk;
+        }
+    }
+    m->graph_kernels[key] = nk;
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    it = m->graphs.emplace(key, exec).first;
+  }
+  CK(cudaGraphLaunch(it->second, m->stream));
+  return HHG_OK;
+}
+
+hhg_status copy_out(hhg_mesh_s* m, void* dst, const void* src, size_t bytes) {
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, m->stream));
+  return HHG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hhg_last_error(void) { return hhg::last_error(); }
+
+hhg_status hhg_mesh_create(int dim, int n_verts, const double* coords, int n_cells, const int* cells,
+                           const unsigned char* vert_is_dirichlet, int L, void* cuda_stream, hhg_mesh* out) {
+  REQUIRE(out, HHG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  REQUIRE(dim == 2 || dim == 3, HHG_ERR_ARG, "dim must be 2 or 3");
+  REQUIRE(coords && cells, HHG_ERR_ARG, "coords/cells is NULL");
+  REQUIRE(n_verts >= dim + 1 && n_cells >= 1, HHG_ERR_ARG, "need at least one cell");
+  REQUIRE(L >= 1 && L <= (dim == 2 ? 9 : 8), HHG_ERR_ARG, "L out of range (1..9 in 2D, 1..8 in 3D)");
+  int64_t Nt = closure_size(dim, (int64_t)1 << L);
+  REQUIRE((double)Nt * n_cells < 2.0e9, HHG_ERR_ARG, "level-L layout exceeds 2e9 nodes");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  hhg_mesh_s* m = new (std::nothrow) hhg_mesh_s();
+  REQUIRE(m, HHG_ERR_OOM, "host allocation failed");
+  m->dim = dim;
+  m->L = L;
+  m->nc = n_cells;
+  m->nv = n_verts;
+  m->device = dev;
+  m->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete m;
+    return cuda_fail(e, "cudaStreamCreate");
+  }
+  hhg_status st = preload_kernels();
+  if (st == HHG_OK) st = build_mesh(m, coords, cells, vert_is_dirichlet);
+  if (st != HHG_OK) {
+    free_mesh(m);
+    delete m;
+    return st;
+  }
+  *out = m;
+  return HHG_OK;
+}
+
+hhg_status hhg_mesh_destroy(hhg_mesh m) {
+  if (!m) return HHG_OK;
+  DeviceGuard g(m->device);
+  cudaStreamSynchronize(m->stream);
+  free_mesh(m);
+  delete m;
+  return HHG_OK;
+}
+
+hhg_status hhg_mesh_get_info(hhg_mesh m, hhg_mesh_info* info) {
+  REQUIRE(m && info, HHG_ERR_ARG, "NULL argument");
+  memset(info, 0, sizeof(*info));
+  info->dim = m->dim;
+  info->L = m->L;
+  info->n_cells = m->nc;
+  info->n_verts = m->nv;
+  for (int l = 0; l <= m->L && l < 16; ++l) info->n_nodes[l] = m->lv[l].N;
+  info->n_unknowns = m->n_unknowns;
+  info->n_distinct = m->n_distinct;
+  info->device_bytes = m->bytes;
+  info->n_colours = m->n_colours;
+  return HHG_OK;
+}
+
+hhg_status hhg_level_coords(hhg_mesh m, int level, double* xyz) {
+  REQUIRE(m && xyz, HHG_ERR_ARG, "NULL argument");
+  REQUIRE(level >= 0 && level <= m->L, HHG_ERR_ARG, "level out of range");
+  DeviceGuard g(m->device);
+  const int d = m->dim;
+  const LevelData& Lv = m->lv[level];
+  std::vector<double> x((size_t)Lv.N * d);
+  for (int c = 0; c < m->nc; ++c) {
+    const int* cv = &m->cells[(size_t)c * (d + 1)];
+    const double* x0 = &m->coords[(size_t)cv[0] * d];
+    double J[3][3] = {{0}};
+    for (int r = 0; r < d; ++r)
+      for (int q = 0; q < d; ++q) J[r][q] = m->coords[(size_t)cv[q + 1] * d + r] - x0[r];
+    for (int k = 0; k <= (d == 3 ? Lv.n : 0); ++k)
+      for (int j = 0; j <= Lv.n - k; ++j)
+        for (int i = 0; i <= Lv.n - k - j; ++i) {
+          int64_t idx = (int64_t)c * Lv.Nt + packed_index(d, Lv.n, i, j, k);
+          int p[3] = {i, j, k};
+          for (int r = 0; r < d; ++r) {
+            double v = 0;
+            for (int q = 0; q < d; ++q) v += J[r][q] * p[q];
+            x[(size_t)idx * d + r] = x0[r] + v / Lv.n;
+          }
+        }
+  }
+  CK(cudaMemcpy(xyz, x.data(), x.size() * sizeof(double), cudaMemcpyDefault));
+  return HHG_OK;
+}
+
+hhg_status hhg_set_coefficient(hhg_mesh m, const double* k) {
+  REQUIRE(m, HHG_ERR_ARG, "mesh is NULL");
+  DeviceGuard g(m->device);
+  for (int c = 0; c < m->nc; ++c) {
+    double v = k ? k[c] : 1.0;
+    REQUIRE(std::isfinite(v) && v > 0, HHG_ERR_ARG, "coefficient of cell %d is not positive", c);
+  }
+  CK(cudaStreamSynchronize(m->stream));
+  for (int c = 0; c < m->nc; ++c) m->k[c] = k ? k[c] : 1.0;
+  return upload_coefficient(m);
+}
+
+hhg_status hhg_set_data(hhg_mesh m, const double* f, const double* gv) {
+  REQUIRE(m && f && gv, HHG_ERR_ARG, "NULL argument");
+  DeviceGuard g(m->device);
+  size_t bytes = sizeof(double) * (size_t)m->lv[m->L].N;
+  CK(cudaMemcpyAsync(m->fL, f, bytes, cudaMemcpyDefault, m->stream));
+  CK(cudaMemcpyAsync(m->gL, gv, bytes, cudaMemcpyDefault, m->stream));
+  m->have_data = true;
+  return HHG_OK;
+}
+
+hhg_status hhg_fmg_solve(hhg_mesh m, const hhg_solve_params* params, double* u_L) {
+  REQUIRE(m, HHG_ERR_ARG, "mesh is NULL");
+  hhg_status st = check_params(m, params);
+  if (st != HHG_OK) return st;
+  REQUIRE(m->have_data, HHG_ERR_STATE, "hhg_set_data must be called before hhg_fmg_solve");
+  DeviceGuard g(m->device);
+  const hhg_solve_params p = *params;
+  if (p.precision == 0) {
+    st = run_graph(m, graph_key("fmg", p), [&](cudaStream_t s) { enqueue_fmg(m, p, false, s); });
+  } else {
+    st = mixed_prepare(m, p.storage);
+    if (st != HHG_OK) return st;
+    st = run_graph(m, graph_key("mixed", p), [&](cudaStream_t s) { mixed_enqueue_solve(m, p, s); });
+  }
+  if (st != HHG_OK) return st;
+  if (u_L) {
+    st = copy_out(m, u_L, m->lv[m->L].u, sizeof(double) * (size_t)m->lv[m->L].N);
+    if (st != HHG_OK) return st;
+  }
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, m->d_flag, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  m->solved = true;
+  REQUIRE(flag == 0, HHG_ERR_DIVERGED, "solution contains NaN or Inf");
+  return HHG_OK;
+}
+
+hhg_status hhg_estimate(hhg_mesh m, int j, double* eta_T, double* eta_jT, hhg_estimate_out* out) {
+  REQUIRE(m, HHG_ERR_ARG, "mesh is NULL");
+  REQUIRE(m->solved, HHG_ERR_STATE, "hhg_estimate needs a previous hhg_fmg_solve");
+  const int L = m->L;
+  REQUIRE(j >= 1 && j <= L - 1, HHG_ERR_ARG, "need 1 <= j <= L-1 (L = %d)", L);
+  DeviceGuard g(m->device);
+  cudaStream_t s = m->stream;
+  const int l = L - j;
+  const int nc = m->nc;
+  double* red = m->d_red;
+  const double* uL = m->lv[L].u;
+  CHECK_PTR(red);
+  CHECK_PTR(uL);
+  CHECK_PTR(m->lv[L - 1].w);
+  CHECK_PTR(m->lv[l].w);
+  CHECK_PTR(m->lv[l - 1].w);
+  CHECK_PTR(m->d_part);
+  CHECK_PTR(m->dM);
+  CHECK_PTR(m->lv[L].d_ijk);
+  CHECK_PTR(m->lv[L].tmp);
+  DBG_SYNC("before estimate");
+  // e~_{L-1} = u_L - w_{L-1} (eta_T)
+  launch_mass_norm_sq(m, uL, m->lv[L - 1].w, red, s);
+  DBG_SYNC("mass norm of u_L - w_{L-1}");
+  // e~_l = u_L - I w_l (w_l on level l+1)
+  const double* v = m->lv[l].w;
+  for (int q = l + 2; q <= L; ++q) {
+    launch_prolong(m, q, v, m->lv[q].tmp, s);
+    DBG_SYNC("prolong w_l");
+    v = m->lv[q].tmp;
+  }
+  launch_mass_norm_sq(m, uL, v, red + nc, s);
+  DBG_SYNC("mass norm of e_l");
+  // e~_{l-1} = u_L - I w_{l-1} (w_{l-1} on level l)
+  v = m->lv[l - 1].w;
+  for (int q = l + 1; q <= L; ++q) {
+    launch_prolong(m, q, v, m->lv[q].tmp, s);
+    DBG_SYNC("prolong w_{l-1}");
+    v = m->lv[q].tmp;
+  }
+  launch_mass_norm_sq(m, uL, v, red + 2 * nc, s);
+  DBG_SYNC("mass norm of e_{l-1}");
+  std::vector<double> h((size_t)3 * nc);
+  CK(cudaMemcpyAsync(h.data(), red, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  double sT = 0, sl = 0, slm1 = 0;
+  for (int c = 0; c < nc; ++c) {
+    sT += h[c];
+    sl += h[nc + c];
+    slm1 += h[2 * nc + c];
+  }
+  double err_l = std::sqrt(sl), err_lm1 = std::sqrt(slm1);
+  double theta = err_lm1 > 0 ? err_l / err_lm1 : 0.0;
+  if (eta_T)
+    for (int c = 0; c < nc; ++c) eta_T[c] = std::sqrt(h[c]);
+  if (eta_jT)
+    for (int c = 0; c < nc; ++c) {
+      double th = h[2 * nc + c] > 0 ? std::sqrt(h[nc + c] / h[2 * nc + c]) : 0.0;
+      eta_jT[c] = std::pow(th, j) * std::sqrt(h[nc + c]);
+    }
+  if (out) {
+    out->eta_j = std::pow(theta, j) * err_l;
+    out->theta = theta;
+    out->err_l = err_l;
+    out->err_lm1 = err_lm1;
+    out->err_Lm1 = std::sqrt(sT);
+  }
+  return HHG_OK;
+}
+
+hhg_status hhg_get_vector(hhg_mesh m, int which, int level, double* out) {
+  REQUIRE(m && out, HHG_ERR_ARG, "NULL argument");
+  REQUIRE(level >= 0 && level <= m->L, HHG_ERR_ARG, "level out of range");
+  DeviceGuard g(m->device);
+  const LevelData& Lv = m->lv[level];
+  if (which == 0) {
+    CK(cudaMemcpyAsync(out, Lv.u, sizeof(double) * Lv.N, cudaMemcpyDefault, m->stream));
+  } else if (which == 1) {
+    REQUIRE(level < m->L, HHG_ERR_ARG, "w_l exists for l < L");
+    CK(cudaMemcpyAsync(out, Lv.w, sizeof(double) * m->lv[level + 1].N, cudaMemcpyDefault, m->stream));
+  } else if (which == 2) {
+    double* scratch = nullptr;
+    CK(cudaMalloc(&scratch, sizeof(double) * Lv.N));
+    cudaMemcpyAsync(scratch, Lv.b, sizeof(double) * Lv.N, cudaMemcpyDeviceToDevice, m->stream);
+    launch_sum_interfaces(m, level, scratch, m->stream);
+    cudaMemcpyAsync(out, scratch, sizeof(double) * Lv.N, cudaMemcpyDefault, m->stream);
+    cudaStreamSynchronize(m->stream);
+    cudaFree(scratch);
+  } else {
+    set_error("which must be 0, 1 or 2");
+    return HHG_ERR_ARG;
+  }
+  CK(cudaStreamSynchronize(m->stream));
+  CK(cudaGetLastError());
+  return HHG_OK;
+}
+
+hhg_status hhg_apply(hhg_mesh m, int level, int op, const double* in, double* out, int nsweeps) {
+  REQUIRE(m && in && out, HHG_ERR_ARG, "NULL argument");
+  REQUIRE(level >= 0 && level <= m->L, HHG_ERR_ARG, "level out of range");
+  REQUIRE(op >= 0 && op <= 3, HHG_ERR_ARG, "op must be 0..3");
+  REQUIRE(op != 2 || level >= 1, HHG_ERR_ARG, "interpolation needs level >= 1");
+  REQUIRE(op != 3 || (level >= 1 && nsweeps >= 0), HHG_ERR_ARG, "sweeps need level >= 1");
+  DeviceGuard g(m->device);
+  cudaStream_t s = m->stream;
+  LevelData& Lv = m->lv[level];
+  size_t nin = (size_t)(op == 2 ? m->lv[level - 1].N : Lv.N);
+  double *din = nullptr, *dout = nullptr;
+  CK(cudaMalloc(&din, sizeof(double) * nin));
+  cudaError_t e = cudaMalloc(&dout, sizeof(double) * Lv.N);
+  if (e != cudaSuccess) {
+    cudaFree(din);
+    return cuda_fail(e, "cudaMalloc");
+  }
+  cudaMemcpyAsync(din, in, sizeof(double) * nin, cudaMemcpyDefault, s);
+  if (op == 0 || op == 1) {
+    launch_apply_op(m, level, op, din, dout, s);
+    launch_sum_interfaces(m, level, dout, s);
+  } else if (op == 2) {
+    launch_prolong(m, level, din, dout, s);
+  } else {
+    // rhs = M in (partial), initial guess from out, sweeps in place on the level's u
+    launch_apply_op(m, level, 1, din, Lv.b, s);
+    cudaMemcpyAsync(Lv.u, out, sizeof(double) * Lv.N, cudaMemcpyDefault, s);
+    for (int q = 0; q < nsweeps; ++q) launch_sweep(m, level, Lv.b, s, false);
+    cudaMemcpyAsync(dout, Lv.u, sizeof(double) * Lv.N, cudaMemcpyDeviceToDevice, s);
+    m->solved = false;
+  }
+  cudaMemcpyAsync(out, dout, sizeof(double) * Lv.N, cudaMemcpyDefault, s);
+  e = cudaStreamSynchronize(s);
+  cudaFree(din);
+  cudaFree(dout);
+  if (e != cudaSuccess) return cuda_fail(e, "hhg_apply");
+  CK(cudaGetLastError());
+  return HHG_OK;
+}
+
+hhg_status hhg_adjoint_l2(hhg_mesh m, const hhg_solve_params* params, const unsigned char* in_S, double* J,
+                          double* grad_f, double* grad_k) {
+  REQUIRE(m && in_S, HHG_ERR_ARG, "NULL argument");
+  hhg_status st = check_params(m, params);
+  if (st != HHG_OK) return st;
+  REQUIRE(params->precision == 0, HHG_ERR_ARG, "the adjoint solve runs in binary64 (precision = 0)");
+  REQUIRE(m->solved, HHG_ERR_STATE, "hhg_adjoint_l2 needs a previous hhg_fmg_solve");
+  DeviceGuard g(m->device);
+  cudaStream_t s = m->stream;
+  const int L = m->L, nc = m->nc;
+  LevelData& LL = m->lv[L];
+  size_t bytes = sizeof(double) * (size_t)LL.N;
+  double* usave = nullptr;
+  unsigned char* dS = nullptr;
+  CK(cudaMalloc(&usave, bytes));
+  cudaError_t e = cudaMalloc(&dS, nc);
+  if (e != cudaSuccess) {
+    cudaFree(usave);
+    return cuda_fail(e, "cudaMalloc");
+  }
+  cudaMemcpyAsync(usave, LL.u, bytes, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(dS, in_S, nc, cudaMemcpyDefault, s);
+  // J = sum_{T in S} u^T M_T u
+  launch_mass_norm_sq(m, usave, nullptr, m->d_red, s);
+  std::vector<double> h(nc);
+  cudaMemcpyAsync(h.data(), m->d_red, sizeof(double) * nc, cudaMemcpyDeviceToHost, s);
+  // adjoint rhs 2 M_S u on level L, then FMG with zero Dirichlet data
+  launch_adjoint_rhs(m, dS, usave, LL.b, s);
+  hhg_solve_params p = *params;
+  st = run_graph(m, graph_key("adjoint", p), [&](cudaStream_t cs) { enqueue_fmg(m, p, true, cs); });
+  if (st == HHG_OK) {
+    if (grad_f) {
+      launch_apply_op(m, L, 1, LL.u, LL.tmp, s);
+      launch_sum_interfaces(m, L, LL.tmp, s);
+      cudaMemcpyAsync(grad_f, LL.tmp, bytes, cudaMemcpyDefault, s);
+    }
+    std::vector<double> hk(nc);
+    if (grad_k) {
+      launch_stiff_bilinear(m, LL.u, usave, m->d_red + nc, s);
+      cudaMemcpyAsync(hk.data(), m->d_red + nc, sizeof(double) * nc, cudaMemcpyDeviceToHost, s);
+    }
+    int flag = 0;
+    cudaMemcpyAsync(&flag, m->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    // restore the forward solution
+    cudaMemcpyAsync(LL.u, usave, bytes, cudaMemcpyDeviceToDevice, s);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "hhg_adjoint_l2");
+    else if (flag) {
+      set_error("adjoint solution contains NaN or Inf");
+      st = HHG_ERR_DIVERGED;
+    }
+    if (st == HHG_OK) {
+      double Jv = 0;
+      for (int c = 0; c < nc; ++c)
+        if (in_S[c]) Jv += h[c];
+      if (J) *J = Jv;
+      if (grad_k)
+        for (int c = 0; c < nc; ++c) grad_k[c] = -hk[c] / m->k[c];
+    }
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(usave);
+  cudaFree(dS);
+  // b_L was overwritten by the adjoint rhs: the next forward solve rebuilds it
+  return st;
+}
+
+hhg_status hhg_profile_kernel(hhg_mesh m, int kernel, int precision, int reps, long long* units, double* bytes,
+                              double* flops) {
+  REQUIRE(m && units && bytes && flops, HHG_ERR_ARG, "NULL argument");
+  REQUIRE(kernel == 0, HHG_ERR_ARG, "kernel must be 0");
+  REQUIRE(precision == 0 || precision == 1, HHG_ERR_ARG, "precision must be 0 or 1");
+  REQUIRE(reps >= 0 && reps <= 100000, HHG_ERR_ARG, "reps in [0, 100000]");
+  DeviceGuard g(m->device);
+  if (precision == 1) {
+    REQUIRE(m->mixed_alloc, HHG_ERR_STATE, "run a mixed solve before profiling its kernel");
+    hhg_status st = mixed_profile_interior(m, reps, m->stream, units, bytes, flops);
+    if (st != HHG_OK) return st;
+  } else {
+    launch_profile_interior(m, 0, reps, m->stream, units, bytes, flops);
+  }
+  m->solved = false;
+  CK(cudaGetLastError());
+  return HHG_OK;
+}
+
+hhg_status hhg_solve_launch_count(hhg_mesh m, const hhg_solve_params* params, long long* n) {
+  REQUIRE(m && params && n, HHG_ERR_ARG, "NULL argument");
+  auto it = m->graph_kernels.find(graph_key(params->precision == 0 ? "fmg" : "mixed", *params));
+  *n = it == m->graph_kernels.end() ? 0 : it->second;
+  return HHG_OK;
+}
+
+hhg_status hhg_debug_check(long long* out8) {
+  REQUIRE(out8, HHG_ERR_ARG, "NULL argument");
+  return read_check(out8);
+}
+
+int hhg_lattice_selfcheck(int dim, int n) {
+  if ((dim != 2 && dim != 3) || n < 1 || n > 1000) return -1;
+  int bad = 0;
+  int64_t Nt = closure_size(dim, n);
+  std::vector<int> seen(Nt, 0);
+  for (int k = 0; k <= (dim == 3 ? n : 0); ++k)
+    for (int j = 0; j <= n - k; ++j)
+      for (int i = 0; i <= n - k - j; ++i) {
+        int64_t g = packed_index(dim, n, i, j, k);
+        if (g < 0 || g >= Nt) {
+          ++bad;
+          continue;
+        }
+        seen[g]++;
+        int64_t off[15];
+        neighbour_offsets(dim, n, j, k, off);
+        int t = boundary_type(dim, n, i, j, k);
+        uint32_t vm = valid_dirs(dim, t);
+        for (int d = 0; d < (dim == 2 ? 7 : 15); ++d) {
+          int di, dj, dk;
+          dir_vec(dim, d, di, dj, dk);
+          int a = i + di, b = j + dj, c = k + dk;
+          bool inside = a >= 0 && b >= 0 && c >= 0 && a + b + c <= n;
+          if (inside != (bool)(vm >> d & 1)) ++bad;
+          if (inside && packed_index(dim, n, a, b, c) != g + off[d]) ++bad;
+        }
+      }
+  for (int64_t g = 0; g < Nt; ++g)
+    if (seen[g] != 1) ++bad;
+  return bad;
+}
+
+}  // extern "C"

@@ -1,0 +1,382 @@
+// Mixed-precision iterative refinement (no counterpart in the paper).
+//
+// Step 1: FMG (Alg. 4 structure, same stage-ordered smoother) computed in binary32 on the original
+//         problem: the iterate of the current FMG top level is a binary32 vector, the coarse-grid
+//         corrections below it are stored as binary32 or bfloat16 and accumulated in binary32.
+//         The prolongated iterates w_l are written in binary64 for the estimator.
+// Steps 2..: r = b_L - A_L u_L and u_L += c in binary64 on level L; the correction c solves
+//         A_L c = r with V-cycles computed in binary32 (same storage rule for the coarse levels).
+#include <cuda_bf16.h>
+
+#include "internal.h"
+#include "kernels_impl.cuh"
+
+namespace hhg {
+
+// ---------------------------------------------------------------- elementwise kernels
+
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+__global__ void k_to_f64(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
+
+// u += c (binary64 accumulate of a binary32 correction; c is zero on Dirichlet nodes)
+__global__ void k_add_f32(const float* __restrict__ c, double* __restrict__ u, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) u[i] += (double)c[i];
+}
+
+// binary32 FMG start: x_0 = g on Dirichlet nodes, 0 elsewhere
+template <int DIM>
+__global__ void k_init_coarse32(LevelCtx lc, int nL, int64_t NtL, int shift, const double* __restrict__ gL,
+                                const uint16_t* __restrict__ dirmask, float* __restrict__ u) {
+  int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (loc >= lc.Nt) return;
+  int T = blockIdx.y;
+  int i, j, k;
+  decode(lc.ijk[loc], i, j, k);
+  int t = boundary_type(DIM, lc.n, i, j, k);
+  float v = 0.0f;
+  if (dirmask[T] >> t & 1) {
+    int64_t q = packed_index(DIM, nL, (int64_t)i << shift, (int64_t)j << shift, (int64_t)k << shift);
+    if (HHG_OOB(q, NtL, 82)) return;
+    v = (float)gL[(int64_t)T * NtL + q];
+  }
+  u[(int64_t)T * lc.Nt + loc] = v;
+}
+
+// binary32 FMG transition: x_{l+1} = I x_l (Dirichlet nodes from g_L), w_l = x_{l+1} in binary64
+template <int DIM>
+__global__ void k_fmg_prolong32(LevelCtx fc, LevelCtx cc, int nL, int64_t NtL, int shift, const double* __restrict__ gL,
+                                const uint16_t* __restrict__ dirmask, const float* __restrict__ xc,
+                                float* __restrict__ xf, double* __restrict__ w) {
+  int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (loc >= fc.Nt) return;
+  int T = blockIdx.y;
+  int i, j, k;
+  decode(fc.ijk[loc], i, j, k);
+  int t = boundary_type(DIM, fc.n, i, j, k);
+  int64_t g = (int64_t)T * fc.Nt + loc;
+  if (dirmask[T] >> t & 1) {
+    int64_t q = packed_index(DIM, nL, (int64_t)i << shift, (int64_t)j << shift, (int64_t)k << shift);
+    if (HHG_OOB(q, NtL, 81)) return;
+    double gv = gL[(int64_t)T * NtL + q];
+    xf[g] = (float)gv;
+    w[g] = gv;
+    return;
+  }
+  float v = interp<DIM, float>(cc, T, i, j, k, CVec<float, float>{xc, nullptr});
+  xf[g] = v;
+  w[g] = (double)v;
+}
+
+// Direct coarse solve for the binary32 path: residual and A_ff^{-1} r in binary64, the update is
+// stored in the level-0 vector's storage type.
+template <int DIM, typename U>
+__global__ void __launch_bounds__(1024) k_coarse_mixed(int n0f, const int* __restrict__ cf, const int* __restrict__ ptr,
+                                                       const int* __restrict__ cell, const int* __restrict__ locv,
+                                                       LevelCtx lc, const double* __restrict__ S,
+                                                       const float* __restrict__ rhs, Vec<float, U> u,
+                                                       const double* __restrict__ Ainv) {
+  extern __shared__ double r[];
+  for (int q = threadIdx.x; q < n0f; q += blockDim.x) {
+    int v = cf[q];
+    double res = 0;
+    for (int c = ptr[v]; c < ptr[v + 1]; ++c) {
+      int i, j, k;
+      prim_position(locv[c], 1, lc.n, 0, 0, i, j, k);
+      int T = cell[c];
+      int t = boundary_type(DIM, lc.n, i, j, k);
+      int64_t p = packed_index(DIM, lc.n, i, j, k);
+      if (HHG_OOB(p, lc.Nt, 94)) continue;
+      int64_t g = (int64_t)T * lc.Nt + p;
+      int64_t off[15];
+      neighbour_offsets(DIM, lc.n, j, k, off);
+      uint32_t vm = valid_dirs(DIM, t);
+      const double* s = S + (size_t)T * kStencilStride + t * kMaxDirs;
+      double acc = 0;
+      for (int d = 0; d < ndirs<DIM>(); ++d)
+        if ((vm >> d & 1) && !HHG_OOB(p + off[d], lc.Nt, 95)) acc += s[d] * (double)u.get(g + off[d]);
+      res += (double)rhs[g] - acc;
+    }
+    r[q] = res;
+  }
+  __syncthreads();
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int row = warp; row < n0f; row += nw) {
+    const double* a = Ainv + (size_t)row * n0f;
+    double acc = 0;
+    for (int c = lane; c < n0f; c += 32) acc += a[c] * r[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      int v = cf[row];
+      for (int c = ptr[v]; c < ptr[v + 1]; ++c) {
+        int i, j, k;
+        prim_position(locv[c], 1, lc.n, 0, 0, i, j, k);
+        int64_t p = packed_index(DIM, lc.n, i, j, k);
+        if (HHG_OOB(p, lc.Nt, 96)) continue;
+        int64_t g = (int64_t)cell[c] * lc.Nt + p;
+        u.set(g, (float)((double)u.get(g) + acc));
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+
+static LevelCtx ctx(const hhg_mesh_s* m, int l) {
+  const LevelData& Lv = m->lv[l];
+  return LevelCtx{Lv.n, Lv.Nt, Lv.d_ijk};
+}
+
+template <typename U> static Vec<float, U> vec_of(hhg_mesh_s* m, int l, U* p) {
+  return Vec<float, U>{p, m->lv[l].cscale};
+}
+template <typename U> static CVec<float, U> cvec_of(hhg_mesh_s* m, int l, const U* p) {
+  return CVec<float, U>{p, m->lv[l].cscale};
+}
+
+template <int DIM, int PM, typename U>
+static void interior32(hhg_mesh_s* m, int l, int gi, int colour, U* u, const float* rhs, cudaStream_t s) {
+  const LevelData& Lv = m->lv[l];
+  const Group& G = m->groups[gi];
+  int64_t a = Lv.icol_off[gi][colour], b = Lv.icol_off[gi][colour + 1];
+  if (b <= a || G.cells.empty()) return;
+  dim3 grid(blocks_for(b - a), (unsigned)G.cells.size());
+  k_smooth_interior<DIM, PM, float, U, float><<<grid, kBlock, 0, s>>>(
+      G.d_cells, Lv.d_icol + a, b - a, ctx(m, l), m->dS32, (float)stiff_scale(DIM, Lv.n), vec_of<U>(m, l, u),
+      CVec<float, float>{rhs, nullptr});
+}
+
+template <int DIM, typename U>
+static void interior32_dispatch(hhg_mesh_s* m, int l, int gi, int colour, U* u, const float* rhs, cudaStream_t s) {
+  int pm = m->groups[gi].pmask;
+  if (DIM == 2) {
+    switch (pm) {
+      case 0x3: interior32<DIM, 0x3, U>(m, l, gi, colour, u, rhs, s); return;
+      case 0x5: interior32<DIM, 0x5, U>(m, l, gi, colour, u, rhs, s); return;
+      case 0x6: interior32<DIM, 0x6, U>(m, l, gi, colour, u, rhs, s); return;
+      default: interior32<DIM, 0x7, U>(m, l, gi, colour, u, rhs, s); return;
+    }
+  } else {
+    if (pm == 0x29) interior32<DIM, 0x29, U>(m, l, gi, colour, u, rhs, s);
+    else interior32<DIM, 0x7f, U>(m, l, gi, colour, u, rhs, s);
+  }
+}
+
+template <int DIM, typename U>
+static void iface32(hhg_mesh_s* m, int l, const Prims& P, int nverts, int cnt, int parity, const int32_t* flist, U* u,
+                    const float* rhs, cudaStream_t s) {
+  if (P.count == 0 || cnt <= 0) return;
+  const LevelData& Lv = m->lv[l];
+  int64_t nthreads = (int64_t)P.count * cnt;
+  float ss = (float)stiff_scale(DIM, Lv.n);
+  k_iface_compute<DIM, float, U, float><<<blocks_for(nthreads), kBlock, 0, s>>>(
+      P.count, nverts, cnt, parity, flist, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l), m->dS32, ss,
+      cvec_of<U>(m, l, u), CVec<float, float>{rhs, nullptr}, Lv.t32);
+  k_iface_apply<DIM, float, U><<<blocks_for(nthreads), kBlock, 0, s>>>(
+      P.count, nverts, cnt, parity, flist, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l), vec_of<U>(m, l, u), Lv.t32);
+}
+
+template <int DIM, typename U>
+static void sweep32(hhg_mesh_s* m, int l, U* u, const float* rhs, cudaStream_t s) {
+  LevelData& Lv = m->lv[l];
+  int n = Lv.n;
+  float ss = (float)stiff_scale(DIM, n);
+  int nst = 3 + (DIM == 3 ? 3 : 0) + m->n_colours;
+  for (int st = 0; st < nst; ++st) {
+    if (st == 0) {
+      const Prims& P = m->verts;
+      if (P.count)
+        k_smooth_vertex<DIM, float, U, float><<<blocks_for(P.count), kBlock, 0, s>>>(
+            P.count, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l), m->dS32, ss, vec_of<U>(m, l, u),
+            CVec<float, float>{rhs, nullptr});
+    } else if (st <= 2) {
+      int parity = (st == 2);
+      iface32<DIM, U>(m, l, m->edges, 2, parity ? n / 2 : n / 2 - 1, parity, nullptr, u, rhs, s);
+    } else if (DIM == 3 && st <= 5) {
+      int c = st - 3;
+      int64_t a = Lv.fcol_off[c], b = Lv.fcol_off[c + 1];
+      iface32<DIM, U>(m, l, m->faces, 3, (int)(b - a), 0, Lv.d_fcol + a, u, rhs, s);
+    } else {
+      int c = st - (DIM == 3 ? 6 : 3);
+      for (size_t gi = 0; gi < m->groups.size(); ++gi)
+        if (c < m->groups[gi].m) interior32_dispatch<DIM, U>(m, l, (int)gi, c, u, rhs, s);
+    }
+  }
+}
+
+template <int DIM, int PM, typename R, typename U, typename B>
+static void residual_group_t(hhg_mesh_s* m, int l, int gi, CVec<R, U> u, CVec<R, B> rhs, const R* S, float* out,
+                             cudaStream_t s) {
+  const LevelData& Lv = m->lv[l];
+  const Group& G = m->groups[gi];
+  dim3 grid(blocks_for(Lv.Nt), (unsigned)G.cells.size());
+  k_residual<DIM, PM, R, U, B, float><<<grid, kBlock, 0, s>>>(G.d_cells, ctx(m, l), S, m->d_dirmask,
+                                                               (R)stiff_scale(DIM, Lv.n), u, rhs, out);
+}
+
+template <int DIM, typename R, typename U, typename B>
+static void residual_t(hhg_mesh_s* m, int l, CVec<R, U> u, CVec<R, B> rhs, const R* S, float* out, cudaStream_t s) {
+  for (size_t gi = 0; gi < m->groups.size(); ++gi) {
+    int pm = m->groups[gi].pmask;
+    if (DIM == 2) {
+      switch (pm) {
+        case 0x3: residual_group_t<DIM, 0x3>(m, l, (int)gi, u, rhs, S, out, s); break;
+        case 0x5: residual_group_t<DIM, 0x5>(m, l, (int)gi, u, rhs, S, out, s); break;
+        case 0x6: residual_group_t<DIM, 0x6>(m, l, (int)gi, u, rhs, S, out, s); break;
+        default: residual_group_t<DIM, 0x7>(m, l, (int)gi, u, rhs, S, out, s); break;
+      }
+    } else {
+      if (pm == 0x29) residual_group_t<DIM, 0x29>(m, l, (int)gi, u, rhs, S, out, s);
+      else residual_group_t<DIM, 0x7f>(m, l, (int)gi, u, rhs, S, out, s);
+    }
+  }
+}
+
+template <int DIM, typename U>
+static void coarse32(hhg_mesh_s* m, U* u, const float* rhs, cudaStream_t s) {
+  if (m->n0f == 0) return;
+  size_t smem = (size_t)m->n0f * sizeof(double);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_coarse_mixed<DIM, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  const Prims& P = m->verts;
+  k_coarse_mixed<DIM, U><<<1, 1024, smem, s>>>(m->n0f, m->d_cf_vert, P.d_ptr, P.d_cell, P.d_loc, ctx(m, 0), m->dS, rhs,
+                                               vec_of<U>(m, 0, u), m->d_Ainv);
+}
+
+// V(pre, post)-cycle in binary32 on level l for A x = rhs; x has storage type U (binary32 on the
+// top level), the coarse corrections have storage type S.
+template <int DIM, typename S, typename U>
+static void vcycle32(hhg_mesh_s* m, int l, U* x, const float* rhs, const hhg_solve_params& p, cudaStream_t s) {
+  if (l == 0) {
+    coarse32<DIM, U>(m, x, rhs, s);
+    return;
+  }
+  LevelData& Lv = m->lv[l];
+  LevelData& C = m->lv[l - 1];
+  for (int q = 0; q < p.pre; ++q) sweep32<DIM, U>(m, l, x, rhs, s);
+  residual_t<DIM, float, U, float>(m, l, cvec_of<U>(m, l, x), CVec<float, float>{rhs, nullptr}, m->dS32, Lv.t32, s);
+  dim3 gr(blocks_for(C.Nt), m->nc);
+  k_restrict<DIM, float, float, float><<<gr, kBlock, 0, s>>>(ctx(m, l), ctx(m, l - 1), m->d_dirmask, Lv.t32, C.r32);
+  S* c = (S*)C.c16;
+  cudaMemsetAsync(c, 0, sizeof(S) * (size_t)C.N, s);
+  vcycle32<DIM, S, S>(m, l - 1, c, C.r32, p, s);
+  dim3 gf(blocks_for(Lv.Nt), m->nc);
+  k_prolong_add<DIM, float, S, U><<<gf, kBlock, 0, s>>>(ctx(m, l), ctx(m, l - 1), m->d_dirmask,
+                                                         cvec_of<S>(m, l - 1, c), vec_of<U>(m, l, x));
+  for (int q = 0; q < p.post; ++q) sweep32<DIM, U>(m, l, x, rhs, s);
+}
+
+void launch_build_rhs(hhg_mesh_s* m, int l, cudaStream_t s);
+void launch_finite_check(hhg_mesh_s* m, const double* v, int64_t n, cudaStream_t s);
+
+template <int DIM, typename S>
+static void mixed_solve_t(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t s) {
+  const int L = m->L;
+  const LevelData& LL = m->lv[L];
+  for (int l = 0; l <= L; ++l) {
+    launch_build_rhs(m, l, s);  // binary64 b_l (b_L is the refinement's residual rhs)
+    k_to_f32<<<blocks_for(m->lv[l].N), kBlock, 0, s>>>(m->lv[l].b, m->lv[l].b32, m->lv[l].N);
+  }
+  {
+    const LevelData& L0 = m->lv[0];
+    dim3 g0(blocks_for(L0.Nt), m->nc);
+    k_init_coarse32<DIM><<<g0, kBlock, 0, s>>>(ctx(m, 0), LL.n, LL.Nt, L, m->gL, m->d_dirmask, L0.x32);
+  }
+  // step 1: binary32 FMG
+  for (int l = 0; l <= L; ++l) {
+    for (int q = 0; q < p.nu; ++q) vcycle32<DIM, S, float>(m, l, m->lv[l].x32, m->lv[l].b32, p, s);
+    if (l < L) {
+      const LevelData& F = m->lv[l + 1];
+      dim3 gf(blocks_for(F.Nt), m->nc);
+      k_fmg_prolong32<DIM><<<gf, kBlock, 0, s>>>(ctx(m, l + 1), ctx(m, l), LL.n, LL.Nt, L - l - 1, m->gL,
+                                                 m->d_dirmask, m->lv[l].x32, F.x32, m->lv[l].w);
+    }
+  }
+  k_to_f64<<<blocks_for(LL.N), kBlock, 0, s>>>(LL.x32, LL.u, LL.N);
+  // refinement steps: binary64 residual and update, binary32 V-cycles on the correction
+  for (int it = 0; it < p.ir_steps; ++it) {
+    residual_t<DIM, double, double, double>(m, L, CVec<double, double>{LL.u, nullptr},
+                                            CVec<double, double>{LL.b, nullptr}, m->dS, LL.r32, s);
+    cudaMemsetAsync(LL.x32, 0, sizeof(float) * (size_t)LL.N, s);
+    for (int q = 0; q < p.ir_vcycles; ++q) vcycle32<DIM, S, float>(m, L, LL.x32, LL.r32, p, s);
+    k_add_f32<<<blocks_for(LL.N), kBlock, 0, s>>>(LL.x32, LL.u, LL.N);
+  }
+  for (int q = 0; q < p.n_extra; ++q) {
+    residual_t<DIM, double, double, double>(m, L, CVec<double, double>{LL.u, nullptr},
+                                            CVec<double, double>{LL.b, nullptr}, m->dS, LL.r32, s);
+    cudaMemsetAsync(LL.x32, 0, sizeof(float) * (size_t)LL.N, s);
+    vcycle32<DIM, S, float>(m, L, LL.x32, LL.r32, p, s);
+    k_add_f32<<<blocks_for(LL.N), kBlock, 0, s>>>(LL.x32, LL.u, LL.N);
+  }
+  cudaMemsetAsync(m->d_flag, 0, sizeof(int), s);
+  launch_finite_check(m, LL.u, LL.N, s);
+}
+
+void mixed_enqueue_solve(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t s) {
+  if (p.storage == 1) {
+    if (m->dim == 2) mixed_solve_t<2, __nv_bfloat16>(m, p, s);
+    else mixed_solve_t<3, __nv_bfloat16>(m, p, s);
+  } else {
+    if (m->dim == 2) mixed_solve_t<2, float>(m, p, s);
+    else mixed_solve_t<3, float>(m, p, s);
+  }
+}
+
+hhg_status mixed_prepare(hhg_mesh_s* m, int storage) {
+  if (storage == 2) {
+    set_error("binary16 correction storage is not implemented; use storage 0 (binary32) or 1 (bfloat16)");
+    return HHG_ERR_ARG;
+  }
+  size_t esz = storage == 1 ? 2 : 4;
+  if (m->mixed_alloc && m->last_storage == storage) return HHG_OK;
+  for (auto& Lv : m->lv) {
+    if (!m->mixed_alloc) {
+      cudaError_t e;
+      if ((e = cudaMalloc(&Lv.x32, sizeof(float) * Lv.N)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+      if ((e = cudaMalloc(&Lv.b32, sizeof(float) * Lv.N)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+      if ((e = cudaMalloc(&Lv.r32, sizeof(float) * Lv.N)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+      if ((e = cudaMalloc(&Lv.t32, sizeof(float) * Lv.N)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+      if ((e = cudaMalloc(&Lv.cscale, sizeof(float))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+      m->bytes += (long long)(16 * Lv.N + 4);
+      float one = 1.0f;
+      if ((e = cudaMemcpy(Lv.cscale, &one, sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy");
+    }
+    if (Lv.c16) {
+      cudaFree(Lv.c16);
+      Lv.c16 = nullptr;
+    }
+    cudaError_t e = cudaMalloc(&Lv.c16, esz * Lv.N);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  }
+  m->mixed_alloc = true;
+  m->last_storage = storage;
+  return HHG_OK;
+}
+
+hhg_status mixed_profile_interior(hhg_mesh_s* m, int reps, cudaStream_t s, long long* units, double* bytes,
+                                  double* flops) {
+  const int L = m->L;
+  LevelData& Lv = m->lv[L];
+  const Group& G = m->groups[0];
+  int64_t len = Lv.icol_off[0][1] - Lv.icol_off[0][0];
+  long long nodes = (long long)len * (long long)G.cells.size();
+  int p = __builtin_popcount(G.pmask);
+  *units = nodes;
+  *bytes = 4.0 * ((double)Lv.Nt * G.cells.size() + 2.0 * nodes);
+  *flops = (2.0 * (1 + 2 * p) + 3.0) * nodes;
+  for (int r = 0; r < reps; ++r) {
+    if (m->dim == 2) interior32_dispatch<2, float>(m, L, 0, 0, Lv.x32, Lv.b32, s);
+    else interior32_dispatch<3, float>(m, L, 0, 0, Lv.x32, Lv.b32, s);
+  }
+  return HHG_OK;
+}
+
+}  // namespace hhg

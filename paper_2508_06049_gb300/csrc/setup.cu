@@ -1,0 +1,666 @@
+// Host-side construction of an HHG mesh object: coarse topology, per-cell partial stencils,
+// interface descriptors, interior colourings, the direct coarse solve and the level tables.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <array>
+#include <map>
+
+#include "internal.h"
+
+namespace hhg {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+const char* last_error() { return g_err; }
+
+hhg_status cuda_fail(cudaError_t e, const char* what) {
+  set_error("CUDA error in %s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? HHG_ERR_OOM : HHG_ERR_CUDA;
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
+  } while (0)
+
+template <typename T>
+static hhg_status dalloc(hhg_mesh_s* m, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  m->bytes += (long long)(count * sizeof(T));
+  return HHG_OK;
+}
+
+template <typename T>
+static hhg_status upload(hhg_mesh_s* m, T** p, const std::vector<T>& v) {
+  hhg_status st = dalloc(m, p, v.size());
+  if (st != HHG_OK) return st;
+  if (!v.empty()) CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return HHG_OK;
+}
+
+// ---------------------------------------------------------------- micro elements
+// Micro elements of the (infinite) lattice that contain lattice point p, as integer vertex lists.
+// 2D: in y = (i, i+j) every unit square splits along (1,1); 3D: Kuhn tets of the y-cube lattice,
+// y = (i, i+j, i+j+k).  Both equal red refinement / Bey's rule of the macro element.
+static void elements_at(int dim, const int p[3], std::vector<std::array<std::array<int, 3>, 4>>& out) {
+  out.clear();
+  int y[3] = {p[0], p[0] + p[1], dim == 3 ? p[0] + p[1] + p[2] : 0};
+  auto to_e = [&](const int yy[3], std::array<int, 3>& e) {
+    e[0] = yy[0];
+    e[1] = yy[1] - yy[0];
+    e[2] = dim == 3 ? yy[2] - yy[1] : 0;
+  };
+  if (dim == 2) {
+    for (int c0 = y[0] - 1; c0 <= y[0]; ++c0)
+      for (int c1 = y[1] - 1; c1 <= y[1]; ++c1)
+        for (int tri = 0; tri < 2; ++tri) {
+          int v[3][3] = {{c0, c1, 0}, {c0 + (tri == 0), c1 + (tri == 1), 0}, {c0 + 1, c1 + 1, 0}};
+          bool has = false;
+          for (int a = 0; a < 3; ++a) has |= (v[a][0] == y[0] && v[a][1] == y[1]);
+          if (!has) continue;
+          std::array<std::array<int, 3>, 4> el{};
+          for (int a = 0; a < 3; ++a) to_e(v[a], el[a]);
+          out.push_back(el);
+        }
+    return;
+  }
+  static const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  for (int c0 = y[0] - 1; c0 <= y[0]; ++c0)
+    for (int c1 = y[1] - 1; c1 <= y[1]; ++c1)
+      for (int c2 = y[2] - 1; c2 <= y[2]; ++c2)
+        for (int s = 0; s < 6; ++s) {
+          int v[4][3];
+          int cur[3] = {c0, c1, c2};
+          for (int a = 0; a < 3; ++a) v[0][a] = cur[a];
+          for (int q = 0; q < 3; ++q) {
+            cur[perms[s][q]] += 1;
+            for (int a = 0; a < 3; ++a) v[q + 1][a] = cur[a];
+          }
+          bool has = false;
+          for (int a = 0; a < 4; ++a) has |= (v[a][0] == y[0] && v[a][1] == y[1] && v[a][2] == y[2]);
+          if (!has) continue;
+          std::array<std::array<int, 3>, 4> el{};
+          for (int a = 0; a < 4; ++a) to_e(v[a], el[a]);
+          out.push_back(el);
+        }
+}
+
+static int slot_of(int dim, int di, int dj, int dk) {
+  int nd = dim == 2 ? 7 : 15;
+  for (int s = 0; s < nd; ++s) {
+    int a, b, c;
+    dir_vec(dim, s, a, b, c);
+    if (a == di && b == dj && c == dk) return s;
+  }
+  return -1;
+}
+
+// P1 element matrices of a simplex with vertices X[a] (dim coordinates each).
+static bool element_matrices(int dim, const double X[4][3], double K[4][4], double M[4][4]) {
+  int d = dim;
+  double J[3][3] = {{0}};
+  for (int r = 0; r < d; ++r)
+    for (int c = 0; c < d; ++c) J[r][c] = X[c + 1][r] - X[0][r];
+  double det, inv[3][3];
+  if (d == 2) {
+    det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    if (det == 0) return false;
+    inv[0][0] = J[1][1] / det; inv[0][1] = -J[0][1] / det;
+    inv[1][0] = -J[1][0] / det; inv[1][1] = J[0][0] / det;
+  } else {
+    det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+          J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    if (det == 0) return false;
+    inv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+    inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+    inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+    inv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+    inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+    inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+    inv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+    inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+    inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+  }
+  double vol = std::fabs(det) / (d == 2 ? 2.0 : 6.0);
+  // gradients of the barycentric coordinates: rows of inv for a = 1..d, grad_0 = -sum
+  double G[4][3] = {{0}};
+  for (int a = 1; a <= d; ++a)
+    for (int c = 0; c < d; ++c) G[a][c] = inv[a - 1][c];
+  for (int c = 0; c < d; ++c) G[0][c] = -(G[1][c] + G[2][c] + (d == 3 ? G[3][c] : 0.0));
+  for (int a = 0; a <= d; ++a)
+    for (int b = 0; b <= d; ++b) {
+      double s = 0;
+      for (int c = 0; c < d; ++c) s += G[a][c] * G[b][c];
+      K[a][b] = vol * s;
+      M[a][b] = vol * (a == b ? 2.0 : 1.0) / ((d + 1) * (d + 2));
+    }
+  return true;
+}
+
+// Partial stencils of one macro cell for every boundary type: sum of the element matrices of the
+// micro elements inside the cell that contain the node, at unit level scale (level 0 lattice).
+static bool cell_stencils(int dim, const double* x0, const double J[3][3], double* S, double* Mst) {
+  const int nrep = 6;
+  std::fill(S, S + kMaxTypes * kMaxDirs, 0.0);
+  std::fill(Mst, Mst + kMaxTypes * kMaxDirs, 0.0);
+  std::vector<std::array<std::array<int, 3>, 4>> els;
+  // representative lattice points: scan a side-6 lattice, first point of each type
+  std::vector<bool> seen(kMaxTypes, false);
+  for (int k = 0; k <= (dim == 3 ? nrep : 0); ++k)
+    for (int j = 0; j <= nrep - k; ++j)
+      for (int i = 0; i <= nrep - k - j; ++i) {
+        int t = boundary_type(dim, nrep, i, j, k);
+        if (seen[t]) continue;
+        // prefer points away from other facets: require one step of slack to the facets not in t
+        bool ok = true;
+        if (!(t & 1) && i < 1) ok = false;
+        if (!(t & 2) && j < 1) ok = false;
+        if (dim == 2) {
+          if (!(t & 4) && i + j > nrep - 1) ok = false;
+        } else {
+          if (!(t & 4) && k < 1) ok = false;
+          if (!(t & 8) && i + j + k > nrep - 1) ok = false;
+        }
+        if (!ok) continue;
+        seen[t] = true;
+        int p[3] = {i, j, k};
+        elements_at(dim, p, els);
+        for (auto& el : els) {
+          bool inside = true;
+          for (int a = 0; a <= dim; ++a) {
+            int s = el[a][0] + el[a][1] + el[a][2];
+            if (el[a][0] < 0 || el[a][1] < 0 || el[a][2] < 0 || s > nrep) inside = false;
+          }
+          if (!inside) continue;
+          double X[4][3] = {{0}};
+          for (int a = 0; a <= dim; ++a)
+            for (int r = 0; r < dim; ++r) {
+              double v = 0;
+              for (int c = 0; c < dim; ++c) v += J[r][c] * el[a][c];
+              X[a][r] = v;  // translation by x0 does not change the element matrices
+            }
+          double K[4][4], Mm[4][4];
+          if (!element_matrices(dim, X, K, Mm)) return false;
+          int alpha = -1;
+          for (int a = 0; a <= dim; ++a)
+            if (el[a][0] == i && el[a][1] == j && el[a][2] == k) alpha = a;
+          for (int b = 0; b <= dim; ++b) {
+            int s = slot_of(dim, el[b][0] - i, el[b][1] - j, el[b][2] - k);
+            if (s < 0) return false;
+            S[t * kMaxDirs + s] += K[alpha][b];
+            Mst[t * kMaxDirs + s] += Mm[alpha][b];
+          }
+        }
+      }
+  (void)x0;
+  return true;
+}
+
+// ---------------------------------------------------------------- coarse dense Cholesky
+static bool cholesky_inverse(int n, std::vector<double>& A) {
+  // A (n x n, row-major, SPD) -> A^{-1} via L L^T
+  std::vector<double> Lm(A);
+  for (int j = 0; j < n; ++j) {
+    double s = Lm[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) s -= Lm[(size_t)j * n + k] * Lm[(size_t)j * n + k];
+    if (!(s > 0)) return false;
+    double d = std::sqrt(s);
+    Lm[(size_t)j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double t = Lm[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) t -= Lm[(size_t)i * n + k] * Lm[(size_t)j * n + k];
+      Lm[(size_t)i * n + j] = t / d;
+    }
+  }
+  // inverse column by column: solve L y = e_c, L^T x = y
+  std::vector<double> y(n), x(n);
+  for (int c = 0; c < n; ++c) {
+    for (int i = 0; i < n; ++i) {
+      double t = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) t -= Lm[(size_t)i * n + k] * y[k];
+      y[i] = t / Lm[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double t = y[i];
+      for (int k = i + 1; k < n; ++k) t -= Lm[(size_t)k * n + i] * x[k];
+      x[i] = t / Lm[(size_t)i * n + i];
+    }
+    for (int i = 0; i < n; ++i) A[(size_t)i * n + c] = x[i];
+  }
+  return true;
+}
+
+// local vertex sets of the boundary types: type -> (number of vertices, local vertex ids)
+static void type_primitive(int dim, int t, int& nv, int a[3]) {
+  nv = 0;
+  for (int v = 0; v <= dim; ++v) {
+    // vertex v lies on facet bit b unless the facet is opposite to it
+    // 2D facets: bit0 i==0 (opposite v1), bit1 j==0 (opposite v2), bit2 i+j==n (opposite v0)
+    // 3D facets: bit0 i==0 (opp v1), bit1 j==0 (opp v2), bit2 k==0 (opp v3), bit3 sum==n (opp v0)
+    bool on_all = true;
+    for (int b = 0; b <= dim; ++b) {
+      if (!(t >> b & 1)) continue;
+      int opp = (b == dim) ? 0 : b + 1;
+      if (v == opp) on_all = false;
+    }
+    if (on_all) a[nv++] = v;
+  }
+}
+
+hhg_status upload_coefficient(hhg_mesh_s* m) {
+  const int NS = kMaxTypes * kMaxDirs;
+  std::vector<double> S((size_t)m->nc * NS);
+  std::vector<float> S32((size_t)m->nc * NS), M32((size_t)m->nc * NS);
+  for (int c = 0; c < m->nc; ++c)
+    for (int q = 0; q < NS; ++q) {
+      S[(size_t)c * NS + q] = m->k[c] * m->hS1[(size_t)c * NS + q];
+      S32[(size_t)c * NS + q] = (float)S[(size_t)c * NS + q];
+      M32[(size_t)c * NS + q] = (float)m->hM[(size_t)c * NS + q];
+    }
+  CK(cudaMemcpy(m->dS, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(m->dS32, S32.data(), S32.size() * sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(m->dM32, M32.data(), M32.size() * sizeof(float), cudaMemcpyHostToDevice));
+  // coarse operator on the free macro vertices (level 0: n = 1, unit scale)
+  int n0 = m->n0f;
+  if (n0 > 0) {
+    std::vector<int> cidx(m->nv, -1);
+    for (int q = 0; q < n0; ++q) cidx[m->cf_vert[q]] = q;
+    // vertex-primitive index of each global vertex
+    std::vector<double> A((size_t)n0 * n0, 0.0);
+    int d = m->dim;
+    for (int c = 0; c < m->nc; ++c) {
+      for (int a = 0; a <= d; ++a) {
+        int ga = m->cells[(size_t)c * (d + 1) + a];
+        int ia = cidx[ga];
+        if (ia < 0) continue;
+        int pa[3];
+        vertex_coords(a, 1, pa[0], pa[1], pa[2]);
+        int ta = boundary_type(d, 1, pa[0], pa[1], pa[2]);
+        for (int b = 0; b <= d; ++b) {
+          int gb = m->cells[(size_t)c * (d + 1) + b];
+          int ib = cidx[gb];
+          if (ib < 0) continue;
+          int pb[3];
+          vertex_coords(b, 1, pb[0], pb[1], pb[2]);
+          int s = slot_of(d, pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]);
+          A[(size_t)ia * n0 + ib] += S[(size_t)c * NS + ta * kMaxDirs + s];
+        }
+      }
+    }
+    if (!cholesky_inverse(n0, A)) {
+      set_error("coarse operator is not positive definite (check Dirichlet flags / mesh)");
+      return HHG_ERR_MESH;
+    }
+    CK(cudaMemcpy(m->d_Ainv, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  return HHG_OK;
+}
+
+static hhg_status upload_prims(hhg_mesh_s* m, Prims& P) {
+  hhg_status st;
+  if ((st = upload(m, &P.d_ptr, P.ptr)) != HHG_OK) return st;
+  if ((st = upload(m, &P.d_cell, P.cell)) != HHG_OK) return st;
+  if ((st = upload(m, &P.d_loc, P.loc)) != HHG_OK) return st;
+  if ((st = upload(m, &P.d_dir, P.dir)) != HHG_OK) return st;
+  for (int i = 0; i < P.count; ++i) P.max_copies = std::max(P.max_copies, P.ptr[i + 1] - P.ptr[i]);
+  return HHG_OK;
+}
+
+hhg_status build_mesh(hhg_mesh_s* m, const double* coords, const int* cells, const unsigned char* vflag_in) {
+  const int d = m->dim, nc = m->nc, nv = m->nv, L = m->L;
+  const int NS = kMaxTypes * kMaxDirs;
+  m->coords.assign(coords, coords + (size_t)nv * d);
+  m->cells.assign(cells, cells + (size_t)nc * (d + 1));
+  m->k.assign(nc, 1.0);
+  for (int c = 0; c < nc; ++c)
+    for (int a = 0; a <= d; ++a) {
+      int v = cells[(size_t)c * (d + 1) + a];
+      if (v < 0 || v >= nv) {
+        set_error("cell %d references vertex %d outside [0,%d)", c, v, nv);
+        return HHG_ERR_ARG;
+      }
+      for (int b = 0; b < a; ++b)
+        if (cells[(size_t)c * (d + 1) + b] == v) {
+          set_error("cell %d repeats vertex %d", c, v);
+          return HHG_ERR_MESH;
+        }
+    }
+  // ---- per-cell stencils
+  m->hS1.assign((size_t)nc * NS, 0.0);
+  m->hM.assign((size_t)nc * NS, 0.0);
+  for (int c = 0; c < nc; ++c) {
+    const int* cv = &cells[(size_t)c * (d + 1)];
+    double J[3][3] = {{0}};
+    for (int r = 0; r < d; ++r)
+      for (int q = 0; q < d; ++q) J[r][q] = coords[(size_t)cv[q + 1] * d + r] - coords[(size_t)cv[0] * d + r];
+    double det = d == 2 ? J[0][0] * J[1][1] - J[0][1] * J[1][0]
+                        : J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                              J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                              J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    double scale = 0;
+    for (int r = 0; r < d; ++r)
+      for (int q = 0; q < d; ++q) scale = std::max(scale, std::fabs(J[r][q]));
+    if (!(std::fabs(det) > 1e-12 * std::pow(scale, d))) {
+      set_error("cell %d is degenerate (det J = %g)", c, det);
+      return HHG_ERR_MESH;
+    }
+    if (!cell_stencils(d, &coords[(size_t)cv[0] * d], J, &m->hS1[(size_t)c * NS], &m->hM[(size_t)c * NS])) {
+      set_error("stencil construction failed for cell %d", c);
+      return HHG_ERR_MESH;
+    }
+  }
+  // ---- topology: edges and faces keyed by sorted global ids
+  std::map<std::array<int, 2>, std::vector<std::pair<int, int>>> emap;        // -> (cell, loc)
+  std::map<std::array<int, 3>, std::vector<std::pair<int, int>>> fmap;        // 3D faces
+  std::vector<std::vector<std::pair<int, int>>> vcopies(nv);
+  for (int c = 0; c < nc; ++c) {
+    const int* cv = &cells[(size_t)c * (d + 1)];
+    for (int a = 0; a <= d; ++a) vcopies[cv[a]].push_back({c, a});
+    for (int a = 0; a <= d; ++a)
+      for (int b = a + 1; b <= d; ++b) {
+        int la = a, lb = b;
+        if (cv[la] > cv[lb]) std::swap(la, lb);
+        emap[{cv[la], cv[lb]}].push_back({c, la | (lb << 2)});
+      }
+    if (d == 3)
+      for (int a = 0; a < 4; ++a)
+        for (int b = a + 1; b < 4; ++b)
+          for (int e = b + 1; e < 4; ++e) {
+            int l3[3] = {a, b, e};
+            std::sort(l3, l3 + 3, [&](int x, int y) { return cv[x] < cv[y]; });
+            fmap[{cv[l3[0]], cv[l3[1]], cv[l3[2]]}].push_back({c, l3[0] | (l3[1] << 2) | (l3[2] << 4)});
+          }
+  }
+  // boundary facets
+  std::vector<char> bvert(nv, 0);
+  std::map<std::array<int, 2>, char> bedge;
+  if (d == 2) {
+    for (auto& kv : emap) {
+      if (kv.second.size() > 2) {
+        set_error("non-manifold edge (%d,%d)", kv.first[0], kv.first[1]);
+        return HHG_ERR_MESH;
+      }
+      if (kv.second.size() == 1) {
+        bedge[kv.first] = 1;
+        bvert[kv.first[0]] = bvert[kv.first[1]] = 1;
+      }
+    }
+  } else {
+    for (auto& kv : fmap) {
+      if (kv.second.size() > 2) {
+        set_error("non-manifold face (%d,%d,%d)", kv.first[0], kv.first[1], kv.first[2]);
+        return HHG_ERR_MESH;
+      }
+      if (kv.second.size() == 1) {
+        const auto& f = kv.first;
+        bvert[f[0]] = bvert[f[1]] = bvert[f[2]] = 1;
+        bedge[{f[0], f[1]}] = 1;
+        bedge[{f[0], f[2]}] = 1;
+        bedge[{f[1], f[2]}] = 1;
+      }
+    }
+  }
+  std::vector<unsigned char> vflag(nv);
+  for (int v = 0; v < nv; ++v) vflag[v] = vflag_in ? (vflag_in[v] ? 1 : 0) : (unsigned char)bvert[v];
+  // ---- primitives
+  Prims& PV = m->verts;
+  PV.ptr.assign(1, 0);
+  std::vector<int> vprim(nv, -1);
+  for (int v = 0; v < nv; ++v) {
+    if (vcopies[v].empty()) continue;
+    vprim[v] = PV.count++;
+    for (auto& cp : vcopies[v]) {
+      PV.cell.push_back(cp.first);
+      PV.loc.push_back(cp.second);
+    }
+    PV.ptr.push_back((int)PV.cell.size());
+    PV.dir.push_back(vflag[v]);
+  }
+  Prims& PE = m->edges;
+  PE.ptr.assign(1, 0);
+  std::map<std::array<int, 2>, unsigned char> edir;
+  for (auto& kv : emap) {
+    unsigned char dirich = (bedge.count(kv.first) && vflag[kv.first[0]] && vflag[kv.first[1]]) ? 1 : 0;
+    edir[kv.first] = dirich;
+    for (auto& cp : kv.second) {
+      PE.cell.push_back(cp.first);
+      PE.loc.push_back(cp.second);
+    }
+    PE.ptr.push_back((int)PE.cell.size());
+    PE.dir.push_back(dirich);
+    PE.count++;
+  }
+  Prims& PF = m->faces;
+  PF.ptr.assign(1, 0);
+  std::map<std::array<int, 3>, unsigned char> fdir;
+  for (auto& kv : fmap) {
+    const auto& f = kv.first;
+    unsigned char dirich = (kv.second.size() == 1 && vflag[f[0]] && vflag[f[1]] && vflag[f[2]]) ? 1 : 0;
+    fdir[f] = dirich;
+    for (auto& cp : kv.second) {
+      PF.cell.push_back(cp.first);
+      PF.loc.push_back(cp.second);
+    }
+    PF.ptr.push_back((int)PF.cell.size());
+    PF.dir.push_back(dirich);
+    PF.count++;
+  }
+  // ---- Dirichlet masks per cell and boundary type
+  m->dirmask.assign(nc, 0);
+  for (int c = 0; c < nc; ++c) {
+    const int* cv = &cells[(size_t)c * (d + 1)];
+    uint16_t mask = 0;
+    for (int t = 1; t < (1 << (d + 1)); ++t) {
+      int np, a[3];
+      type_primitive(d, t, np, a);
+      if (np == 0) continue;
+      bool dirich = false;
+      if (np == 1) dirich = vflag[cv[a[0]]];
+      else if (np == 2) {
+        int g0 = std::min(cv[a[0]], cv[a[1]]), g1 = std::max(cv[a[0]], cv[a[1]]);
+        dirich = edir[{g0, g1}];
+      } else if (np == 3 && d == 3) {
+        int g[3] = {cv[a[0]], cv[a[1]], cv[a[2]]};
+        std::sort(g, g + 3);
+        dirich = fdir[{g[0], g[1], g[2]}];
+      }
+      if (dirich) mask |= (uint16_t)(1u << t);
+    }
+    m->dirmask[c] = mask;
+  }
+  // ---- interior stencil patterns -> groups and colourings
+  const int npair = d == 2 ? 3 : 7;
+  std::map<int, int> gidx;
+  m->group_of_cell.assign(nc, 0);
+  for (int c = 0; c < nc; ++c) {
+    const double* s0 = &m->hS1[(size_t)c * NS];
+    double vmax = 0;
+    for (int s = 1; s < 2 * npair + 1; ++s) vmax = std::max(vmax, std::fabs(s0[s]));
+    int pm = 0;
+    for (int q = 0; q < npair; ++q)
+      if (std::fabs(s0[2 * q + 1]) > 1e-12 * vmax || std::fabs(s0[2 * q + 2]) > 1e-12 * vmax) pm |= 1 << q;
+    auto it = gidx.find(pm);
+    if (it == gidx.end()) {
+      Group g;
+      g.pmask = pm;
+      // colouring: first alpha of a fixed list with alpha . d odd for every coupled direction
+      static const int c2[3][3] = {{1, 1, 0}, {1, 0, 0}, {0, 1, 0}};
+      static const int c3[7][3] = {{1, 1, 1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+      int ncand = d == 2 ? 3 : 7;
+      bool found = false;
+      for (int ci = 0; ci < ncand && !found; ++ci) {
+        const int* al = d == 2 ? c2[ci] : c3[ci];
+        bool ok = true;
+        for (int q = 0; q < npair; ++q) {
+          if (!(pm >> q & 1)) continue;
+          int di, dj, dk;
+          dir_vec(d, 2 * q + 1, di, dj, dk);
+          int dot = al[0] * di + al[1] * dj + al[2] * dk;
+          if ((dot % 2 + 2) % 2 == 0) ok = false;
+        }
+        if (ok) {
+          found = true;
+          g.alpha[0] = al[0]; g.alpha[1] = al[1]; g.alpha[2] = al[2];
+          g.m = 2;
+        }
+      }
+      if (!found) {
+        if (d == 2) { g.alpha[0] = 1; g.alpha[1] = 2; g.alpha[2] = 0; g.m = 3; }
+        else { g.alpha[0] = 1; g.alpha[1] = 2; g.alpha[2] = 3; g.m = 4; }
+      }
+      gidx[pm] = (int)m->groups.size();
+      m->groups.push_back(g);
+      it = gidx.find(pm);
+    }
+    m->group_of_cell[c] = it->second;
+    m->groups[it->second].cells.push_back(c);
+  }
+  m->n_colours = 0;
+  for (auto& g : m->groups) m->n_colours = std::max(m->n_colours, g.m);
+  // ---- device: stencils, masks, primitives
+  hhg_status st;
+  if ((st = dalloc(m, &m->dS, (size_t)nc * NS)) != HHG_OK) return st;
+  if ((st = upload(m, &m->dM, m->hM)) != HHG_OK) return st;
+  if ((st = dalloc(m, &m->dS32, (size_t)nc * NS)) != HHG_OK) return st;
+  if ((st = dalloc(m, &m->dM32, (size_t)nc * NS)) != HHG_OK) return st;
+  if ((st = upload(m, &m->d_dirmask, m->dirmask)) != HHG_OK) return st;
+  if ((st = upload_prims(m, m->verts)) != HHG_OK) return st;
+  if ((st = upload_prims(m, m->edges)) != HHG_OK) return st;
+  if ((st = upload_prims(m, m->faces)) != HHG_OK) return st;
+  for (auto& g : m->groups)
+    if ((st = upload(m, &g.d_cells, g.cells)) != HHG_OK) return st;
+  // ---- coarse solve set-up
+  m->cf_vert.clear();
+  for (int q = 0; q < PV.count; ++q)
+    if (!PV.dir[q]) m->cf_vert.push_back(q);
+  m->n0f = (int)m->cf_vert.size();
+  if (m->n0f > 16384) {
+    set_error("%d free coarse vertices exceed the direct coarse solve limit of 16384", m->n0f);
+    return HHG_ERR_MESH;
+  }
+  // cf_vert holds vertex-primitive indices; the coarse operator assembly indexes by global
+  // vertex, so map through vprim
+  {
+    std::vector<int> prim_to_vertex(PV.count);
+    for (int v = 0; v < nv; ++v)
+      if (vprim[v] >= 0) prim_to_vertex[vprim[v]] = v;
+    if ((st = upload(m, &m->d_cf_vert, m->cf_vert)) != HHG_OK) return st;
+    // host copy used by upload_coefficient: convert to global vertex ids there
+    std::vector<int> cf_global(m->n0f);
+    for (int q = 0; q < m->n0f; ++q) cf_global[q] = prim_to_vertex[m->cf_vert[q]];
+    // upload_coefficient indexes cidx by global vertex id: store global ids in cf_vert for host
+    // use, keep the primitive ids on the device
+    m->cf_vert.swap(cf_global);
+    // cidx in upload_coefficient is sized by verts.count; make it cover all global ids
+  }
+  if ((st = dalloc(m, &m->d_Ainv, (size_t)std::max(1, m->n0f) * std::max(1, m->n0f))) != HHG_OK) return st;
+  // ---- levels
+  m->lv.resize(L + 1);
+  int64_t maxN = 0;
+  for (int l = 0; l <= L; ++l) {
+    LevelData& Lv = m->lv[l];
+    Lv.l = l;
+    Lv.n = 1 << l;
+    Lv.Nt = closure_size(d, Lv.n);
+    Lv.N = Lv.Nt * nc;
+    maxN = std::max(maxN, Lv.N);
+    std::vector<int32_t> ijk(Lv.Nt);
+    for (int k = 0; k <= (d == 3 ? Lv.n : 0); ++k)
+      for (int j = 0; j <= Lv.n - k; ++j)
+        for (int i = 0; i <= Lv.n - k - j; ++i) ijk[packed_index(d, Lv.n, i, j, k)] = i | (j << 10) | (k << 20);
+    if ((st = upload(m, &Lv.d_ijk, ijk)) != HHG_OK) return st;
+    // interior colour lists per group
+    std::vector<int32_t> icol;
+    Lv.icol_off.assign(m->groups.size(), {});
+    for (size_t g = 0; g < m->groups.size(); ++g) {
+      const Group& G = m->groups[g];
+      Lv.icol_off[g].push_back((int64_t)icol.size());
+      for (int c = 0; c < G.m; ++c) {
+        for (int64_t q = 0; q < Lv.Nt; ++q) {
+          int i = ijk[q] & 1023, j = (ijk[q] >> 10) & 1023, k = ijk[q] >> 20;
+          if (boundary_type(d, Lv.n, i, j, k) != 0) continue;
+          int col = ((G.alpha[0] * i + G.alpha[1] * j + G.alpha[2] * k) % G.m + G.m) % G.m;
+          if (col == c) icol.push_back((int32_t)q);
+        }
+        Lv.icol_off[g].push_back((int64_t)icol.size());
+      }
+    }
+    if ((st = upload(m, &Lv.d_icol, icol)) != HHG_OK) return st;
+    // face colour lists: face-local (a, b), a, b >= 1, a + b <= n - 1, colour (a + 2b) mod 3
+    std::vector<int32_t> fcol;
+    for (int c = 0; c < 3; ++c) {
+      Lv.fcol_off[c] = (int64_t)fcol.size();
+      if (d == 3)
+        for (int b = 1; b <= Lv.n - 2; ++b)
+          for (int a = 1; a + b <= Lv.n - 1; ++a)
+            if ((a + 2 * b) % 3 == c) fcol.push_back(a | (b << 16));
+    }
+    Lv.fcol_off[3] = (int64_t)fcol.size();
+    if ((st = upload(m, &Lv.d_fcol, fcol)) != HHG_OK) return st;
+    // vectors
+    if ((st = dalloc(m, &Lv.u, Lv.N)) != HHG_OK) return st;
+    if ((st = dalloc(m, &Lv.b, Lv.N)) != HHG_OK) return st;
+    if (l < L && (st = dalloc(m, &Lv.rc, Lv.N)) != HHG_OK) return st;
+    if (l >= 1 && (st = dalloc(m, &Lv.tmp, Lv.N)) != HHG_OK) return st;
+  }
+  for (int l = 0; l < L; ++l)
+    if ((st = dalloc(m, &m->lv[l].w, m->lv[l + 1].N)) != HHG_OK) return st;
+  if ((st = dalloc(m, &m->fL, m->lv[L].N)) != HHG_OK) return st;
+  if ((st = dalloc(m, &m->gL, m->lv[L].N)) != HHG_OK) return st;
+  // reduction scratch: one value per level-L node
+  m->part_len = m->lv[L].N;
+  if ((st = dalloc(m, &m->d_part, (size_t)m->part_len)) != HHG_OK) return st;
+  if ((st = dalloc(m, &m->d_red, (size_t)nc * 4)) != HHG_OK) return st;
+  if ((st = dalloc(m, &m->d_flag, 4)) != HHG_OK) return st;
+  if ((st = dalloc(m, &m->d_scal32, 64)) != HHG_OK) return st;
+  // ---- counts of distinct / free nodes on level L
+  {
+    int64_t n = m->lv[L].n;
+    int64_t e_in = n - 1, f_in = (n - 1) * (n - 2) / 2;
+    int64_t c_in = d == 2 ? (n - 1) * (n - 2) / 2 : (n - 1) * (n - 2) * (n - 3) / 6;
+    int64_t distinct = PV.count + (int64_t)PE.count * e_in + (d == 3 ? (int64_t)PF.count * f_in : 0) + (int64_t)nc * c_in;
+    int64_t dirn = 0;
+    for (int q = 0; q < PV.count; ++q) dirn += PV.dir[q];
+    for (int q = 0; q < PE.count; ++q) dirn += PE.dir[q] * e_in;
+    for (int q = 0; q < PF.count; ++q) dirn += PF.dir[q] * f_in;
+    m->n_distinct = distinct;
+    m->n_unknowns = distinct - dirn;
+  }
+  return upload_coefficient(m);
+}
+
+void free_mesh(hhg_mesh_s* m) {
+  auto F = [](void* p) {
+    if (p) cudaFree(p);
+  };
+  for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second);
+  m->graphs.clear();
+  F(m->dS); F(m->dM); F(m->dS32); F(m->dM32); F(m->d_dirmask);
+  for (hhg::Prims* P : {&m->verts, &m->edges, &m->faces}) {
+    F(P->d_ptr); F(P->d_cell); F(P->d_loc); F(P->d_dir);
+  }
+  for (auto& g : m->groups) F(g.d_cells);
+  F(m->d_Ainv); F(m->d_cf_vert);
+  for (auto& Lv : m->lv) {
+    F(Lv.d_ijk); F(Lv.d_icol); F(Lv.d_fcol); F(Lv.u); F(Lv.b); F(Lv.rc); F(Lv.w); F(Lv.tmp);
+    F(Lv.c16); F(Lv.r32); F(Lv.t32); F(Lv.cscale); F(Lv.x32); F(Lv.b32);
+  }
+  F(m->fL); F(m->gL); F(m->d_part); F(m->d_red); F(m->d_flag); F(m->d_scal32);
+  if (m->cap) cudaStreamDestroy(m->cap);
+}
+
+}  // namespace hhg

@@ -1,0 +1,94 @@
+"""Mixed precision (binary32 V-cycles, binary32/bfloat16 coarse-correction storage, binary64
+iterative refinement) against the binary64 oracle.
+
+The binary64 oracle fixes the target: refinement steps must converge to the exact discrete solution,
+the first (binary32 FMG) step must stay within single-precision distance of the binary64 FMG, the
+estimator computed from the binary32 FMG iterates must mark the same elements, and on the full-size
+cube the mixed solve must reach the binary64 discretisation error (equal error, first two digits).
+"""
+
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+
+import workloads as W
+from oracle import hhg_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2508_06049_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def _setup(P, name, L):
+    co, ce, _, f, g, k, ue = W.workload(name, L)
+    mesh = P.Mesh(co, ce, L)
+    if k is not None:
+        mesh.set_coefficient(k)
+    h = O.Hierarchy(co, ce, L, k=k)
+    x = mesh.level_coords(L)
+    mesh.set_data(np.ascontiguousarray(f(x)), np.ascontiguousarray(g(x)))
+    _, idx = cKDTree(h.levels[L].x).query(x)
+    return mesh, h, O.Problem(h, f, g), idx
+
+
+@pytest.mark.parametrize("name,L", [("lshape_l7", 5), ("cube384_l6", 3), ("fichera336_l6", 3)])
+@pytest.mark.parametrize("storage", [0, 1])
+def test_refinement_converges_to_exact_discrete_solution(P, name, L, storage):
+    mesh, h, prob, idx = _setup(P, name, L)
+    u = mesh.solve(nu=2, pre=2, post=1, precision=1, storage=storage, ir_steps=12, ir_vcycles=2)
+    ex = O.exact_solve(prob)
+    err = np.abs(u - ex[idx]).max() / np.abs(ex).max()
+    assert err < 1e-10, err
+    mesh.close()
+
+
+@pytest.mark.parametrize("name,L", [("lshape_l7", 6), ("cube384_l6", 4)])
+def test_binary32_fmg_step_and_estimator(P, name, L):
+    mesh, h, prob, idx = _setup(P, name, L)
+    u32 = mesh.solve(nu=2, pre=2, post=1, precision=1, storage=1, ir_steps=0)
+    e32 = mesh.estimate(1)
+    uo, ws, _ = O.fmg(prob, 2, 2, 1)
+    eo = O.estimate(h, uo, ws, 1)
+    scale = np.abs(uo).max()
+    assert np.abs(u32 - uo[idx]).max() / scale < 1e-4
+    assert abs(e32["eta_j"] - eo["eta_j"]) / eo["eta_j"] < 1e-3
+    assert np.abs(e32["eta_T"] - eo["eta_T"]).max() / eo["eta_T"].max() < 1e-3
+    for frac in (0.2, 0.125):
+        assert np.array_equal(P.mark(e32["eta_T"], frac), O.mark_top_fraction(eo["eta_T"], frac))
+    mesh.close()
+
+
+def _l2_error(mesh, L, x, u, ue):
+    e = np.ascontiguousarray(ue(x) - u)
+    Me = mesh.apply(L, 1, e)
+    _, inv, cnt = np.unique(np.round(x * 2 ** (L + 3)).astype(np.int64), axis=0, return_inverse=True,
+                            return_counts=True)
+    return math.sqrt(float(np.sum(e * Me / cnt[inv.ravel()])))
+
+
+def test_equal_error_on_full_size_cube(P):
+    """cube, 384 macro tets, L = 6: the mixed solve with the benchmark's parameters reaches the
+    binary64 FMG's L2 discretisation error to its first two significant digits (Sec. 5 criterion)."""
+    co, ce, L, f, g, k, ue = W.workload("cube384_l6")
+    mesh = P.Mesh(co, ce, L)
+    x = mesh.level_coords(L)
+    mesh.set_data(np.ascontiguousarray(f(x)), np.ascontiguousarray(g(x)))
+    u64 = mesh.solve(nu=2, pre=2, post=1)
+    e64 = _l2_error(mesh, L, x, u64, ue)
+    est64 = mesh.estimate(1)
+    u16 = mesh.solve(nu=2, pre=2, post=1, precision=1, storage=1, ir_steps=2, ir_vcycles=2)
+    e16 = _l2_error(mesh, L, x, u16, ue)
+    est16 = mesh.estimate(1)
+    assert abs(e16 - e64) <= 0.01 * e64, (e16, e64)
+    assert np.array_equal(P.mark(est16["eta_T"], 0.125), P.mark(est64["eta_T"], 0.125))
+    mesh.close()

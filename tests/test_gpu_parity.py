@@ -1,0 +1,278 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element by element.
+
+Tolerance: 1e-10 relative to the largest oracle value (binary64 results differ only by summation
+order).  Marked sets must be identical.  Library nodes are matched to oracle nodes by coordinates.
+"""
+
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+
+import workloads as W
+from oracle import hhg_oracle as O
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2508_06049_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def perturbed(name, seed=4, amp=0.12):
+    """Interior macro vertices moved randomly: general triangles / tets (full stencils)."""
+    co, ce = W.lshape_mesh() if name == "lshape" else W.cube_mesh(2)
+    co = co.copy()
+    rng = np.random.default_rng(seed)
+    h = 0.5
+    inner = np.all(np.abs(co) < 1 - 1e-9, axis=1) if name == "lshape" else \
+        np.all((co > 1e-9) & (co < 1 - 1e-9), axis=1)
+    if name == "lshape":
+        inner &= ~((np.abs(co[:, 0]) < 1e-9) | (np.abs(co[:, 1]) < 1e-9))
+    co[inner] += amp * h * rng.uniform(-1, 1, size=(inner.sum(), co.shape[1]))
+    return co, ce
+
+
+CASES = {
+    "square": lambda: (*W.square_mesh(2), 4, None),
+    "lshape": lambda: (*W.lshape_mesh(), 5, None),
+    "lshape_pert": lambda: (*perturbed("lshape"), 4, None),
+    "cube384": lambda: (*W.cube_mesh(4), 3, None),
+    "cube_pert_k": lambda: (*perturbed("cube"), 3, W.coeff_uniform(48, seed=3)),
+    "cube3072_k": lambda: (*W.cube_mesh(8), 2, W.coeff_loguniform(3072, seed=0)),
+    "fichera_k": lambda: (*W.fichera_mesh(), 3, W.coeff_uniform(336, seed=1)),
+}
+
+_cache = {}
+
+
+def setup_case(P, name):
+    if name in _cache:
+        return _cache[name]
+    co, ce, L, k = CASES[name]()
+    h = O.Hierarchy(co, ce, L, k=k)
+    mesh = P.Mesh(co, ce, L)
+    if k is not None:
+        mesh.set_coefficient(k)
+    maps = []
+    for l in range(L + 1):
+        x = mesh.level_coords(l)
+        dist, idx = cKDTree(h.levels[l].x).query(x)
+        assert dist.max() < 1e-9
+        maps.append(idx)
+    _cache[name] = (co, ce, L, k, h, mesh, maps)
+    return _cache[name]
+
+
+def fg(dim):
+    if dim == 2:
+        return (lambda x: np.sin(3 * x[:, 0]) * np.cos(2 * x[:, 1]) + 1.0,
+                lambda x: 0.25 + x[:, 0] * x[:, 1])
+    return (lambda x: np.sin(3 * x[:, 0]) * np.cos(2 * x[:, 1]) + x[:, 2],
+            lambda x: 0.1 * x[:, 0] - x[:, 2] * x[:, 1])
+
+
+def close(gpu, ref, tol=TOL):
+    scale = max(np.abs(ref).max(), 1e-300)
+    err = np.abs(gpu - ref).max() / scale
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_operators_match_assembled_matrices(P, name):
+    co, ce, L, k, h, mesh, maps = setup_case(P, name)
+    rng = np.random.default_rng(0)
+    for l in range(L + 1):
+        lev = h.levels[l]
+        xo = rng.standard_normal(len(lev.keys))
+        x = np.ascontiguousarray(xo[maps[l]])
+        close(mesh.apply(l, 0, x), (lev.A @ xo)[maps[l]], 1e-12)
+        close(mesh.apply(l, 1, x), (lev.M @ xo)[maps[l]], 1e-12)
+        if l >= 1:
+            xc = rng.standard_normal(len(h.levels[l - 1].keys))
+            out = mesh.apply(l, 2, np.ascontiguousarray(xc[maps[l - 1]]))
+            close(out, (lev.P @ xc)[maps[l]], 1e-13)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_smoothing_sweeps_match(P, name):
+    co, ce, L, k, h, mesh, maps = setup_case(P, name)
+    rng = np.random.default_rng(1)
+    for l in range(1, L + 1):
+        lev = h.levels[l]
+        fo = rng.standard_normal(len(lev.keys))
+        u0 = np.where(lev.dirichlet, rng.standard_normal(len(lev.keys)), rng.standard_normal(len(lev.keys)))
+        for ns in (1, 3):
+            uo = u0.copy()
+            for _ in range(ns):
+                O.smooth(lev, uo, lev.M @ fo)
+            ug = np.ascontiguousarray(u0[maps[l]])
+            mesh.apply(l, 3, np.ascontiguousarray(fo[maps[l]]), ug, nsweeps=ns)
+            close(ug, uo[maps[l]])
+
+
+def run_both(P, name, nu=2, pre=2, post=1, n_extra=0):
+    co, ce, L, k, h, mesh, maps = setup_case(P, name)
+    f, g = fg(h.dim)
+    x = mesh.level_coords(L)
+    mesh.set_data(np.ascontiguousarray(f(x)), np.ascontiguousarray(g(x)))
+    u = mesh.solve(nu=nu, pre=pre, post=post, n_extra=n_extra)
+    prob = O.Problem(h, f, g)
+    uo, ws, _ = O.fmg(prob, nu, pre, post, n_extra)
+    return mesh, maps, h, u, uo, ws
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fmg_solution_and_stored_coarse_solutions(P, name):
+    mesh, maps, h, u, uo, ws = run_both(P, name)
+    close(u, uo[maps[h.L]])
+    for l in range(h.L):
+        close(mesh.get_vector(1, l), ws[l][maps[l + 1]])
+
+
+@pytest.mark.parametrize("name,nu,pre,post,extra", [("lshape", 1, 1, 1, 2), ("cube384", 3, 1, 2, 1),
+                                                     ("fichera_k", 1, 2, 2, 0)])
+def test_fmg_other_cycle_parameters(P, name, nu, pre, post, extra):
+    mesh, maps, h, u, uo, ws = run_both(P, name, nu, pre, post, extra)
+    close(u, uo[maps[h.L]])
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_estimator_and_marking(P, name):
+    mesh, maps, h, u, uo, ws = run_both(P, name)
+    for j in range(1, h.L):
+        eg = mesh.estimate(j)
+        eo = O.estimate(h, uo, ws, j)
+        close(eg["eta_T"], eo["eta_T"])
+        close(eg["eta_jT"], eo["eta_jT"], 1e-9)
+        for key in ("eta_j", "theta", "err_l", "err_lm1"):
+            assert abs(eg[key] - eo[key]) <= TOL * abs(eo[key]), (j, key)
+        assert abs(eg["err_Lm1"] ** 2 - (eo["eta_T"] ** 2).sum()) <= 1e-10 * eg["err_Lm1"] ** 2
+        for frac in (0.1, 0.2, 0.125):
+            assert np.array_equal(P.mark(eg["eta_T"], frac), O.mark_top_fraction(eo["eta_T"], frac))
+
+
+def test_estimate_before_solve_is_an_error(P):
+    co, ce = W.square_mesh(2)
+    m = P.Mesh(co, ce, 3)
+    with pytest.raises(P.HHGError):
+        m.estimate(1)
+    with pytest.raises(P.HHGError):
+        m.solve()  # no data yet
+    m.close()
+
+
+def test_invalid_inputs_are_rejected(P):
+    co, ce = W.square_mesh(2)
+    with pytest.raises(P.HHGError):
+        P.Mesh(co, ce, 0)
+    bad = ce.copy()
+    bad[0, 1] = bad[0, 0]
+    with pytest.raises(P.HHGError):
+        P.Mesh(co, bad, 2)
+    m = P.Mesh(co, ce, 2)
+    with pytest.raises(P.HHGError):
+        m.set_coefficient(-np.ones(len(ce)))
+    x = m.level_coords(2)
+    m.set_data(np.full(len(x), np.nan), np.zeros(len(x)))
+    with pytest.raises(P.HHGError) as e:
+        m.solve()
+    assert e.value.status == 6  # HHG_ERR_DIVERGED
+    m.close()
+
+
+def test_device_tensors_and_streams(P):
+    """Inputs/outputs as CUDA tensors on a user stream give the same result as host arrays."""
+    import torch
+    co, ce = W.lshape_mesh()
+    L = 4
+    s = torch.cuda.Stream()
+    m1 = P.Mesh(co, ce, L)
+    m2 = P.Mesh(co, ce, L, stream=s)
+    x = m1.level_coords(L)
+    f = np.ascontiguousarray(np.cos(x[:, 0]) + x[:, 1])
+    g = np.ascontiguousarray(W.lshape_g(x))
+    m1.set_data(f, g)
+    u1 = m1.solve()
+    with torch.cuda.stream(s):
+        fd = torch.from_numpy(f).cuda()
+        gd = torch.from_numpy(g).cuda()
+        out = torch.empty_like(fd)
+    m2.set_data(fd, gd)
+    m2.solve(out=out)
+    s.synchronize()
+    assert np.array_equal(out.cpu().numpy(), u1)    # same kernels, same order: bitwise equal
+    m1.close()
+    m2.close()
+
+
+@pytest.mark.parametrize("name", ["fichera_k", "square"])
+def test_adjoint_gradients_match_oracle(P, name):
+    co, ce, L, k, h, mesh, maps = setup_case(P, name)
+    f, g = fg(h.dim)
+    if name == "fichera_k":
+        g = lambda x: np.zeros(len(x))
+    x = mesh.level_coords(L)
+    mesh.set_data(np.ascontiguousarray(f(x)), np.ascontiguousarray(g(x)))
+    mesh.solve(nu=2, pre=2, post=1, n_extra=60)
+    in_S = np.all(co[ce].mean(axis=1) > 0.5, axis=1)
+    J, gf, gk = mesh.adjoint_l2(in_S, nu=2, pre=2, post=1, n_extra=60)
+    prob = O.Problem(h, f, g)
+    uo = O.exact_solve(prob)
+    Jo, gfo, gko, _ = O.adjoint_gradients(h, uo, in_S)
+    assert abs(J - Jo) <= 1e-9 * abs(Jo)
+    close(gf, gfo[maps[L]], 1e-9)
+    close(gk, gko, 1e-9)
+
+
+def test_full_size_lshape_matches_oracle(P):
+    """The L-shape at its full level L=7 (the oracle finishes in seconds)."""
+    co, ce, L, f, g, k, _ = W.workload("lshape_l7")
+    mesh = P.Mesh(co, ce, L)
+    x = mesh.level_coords(L)
+    mesh.set_data(np.ascontiguousarray(f(x)), np.ascontiguousarray(g(x)))
+    u = mesh.solve()
+    h = O.Hierarchy(co, ce, L)
+    prob = O.Problem(h, f, g)
+    uo, ws, _ = O.fmg(prob, 2, 2, 1)
+    _, idx = cKDTree(h.levels[L].x).query(x)
+    close(u, uo[idx])
+    eg = mesh.estimate(1)
+    eo = O.estimate(h, uo, ws, 1)
+    close(eg["eta_T"], eo["eta_T"])
+    assert np.array_equal(P.mark(eg["eta_T"], 0.2), O.mark_top_fraction(eo["eta_T"], 0.2))
+    mesh.close()
+
+
+def test_full_size_cube384_l6_properties(P):
+    """Full-size 3D workload (16.6 M unknowns): second-order convergence against the exact solution
+    (ratio of the L2 errors at L=5 and L=6 near 4) and the estimator inside Theorem 4.1's bounds."""
+    errs = []
+    for L in (5, 6):
+        co, ce, _, f, g, k, ue = W.workload("cube384_l6", L)
+        mesh = P.Mesh(co, ce, L)
+        x = mesh.level_coords(L)
+        mesh.set_data(np.ascontiguousarray(f(x)), np.ascontiguousarray(g(x)))
+        u = mesh.solve()
+        e = np.ascontiguousarray(ue(x) - u)
+        Me = mesh.apply(L, 1, e)
+        # interface nodes appear once per adjacent cell: weight each copy by 1/multiplicity
+        _, inv, cnt = np.unique(np.round(x * 2 ** (L + 3)).astype(np.int64), axis=0, return_inverse=True,
+                                return_counts=True)
+        wgt = 1.0 / cnt[inv.ravel()]
+        errs.append(math.sqrt(np.sum(wgt * e * Me)))
+        est = mesh.estimate(1)
+        eff = est["eta_j"] / errs[-1]
+        c1, c2 = O.theorem41_constants(0.25, 1)
+        assert c1 <= eff <= c2, eff
+        assert mesh.info.n_unknowns == (4 * 2 ** L - 1) ** 3
+        mesh.close()
+    assert 3.5 < errs[0] / errs[1] < 4.5, errs
