@@ -29,7 +29,11 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-MIXED_DEFAULT = dict(storage=1, ir_steps=2, ir_vcycles=2)
+# Equal error (Sec. 5 protocol): extra level-L cycles until the L2 error is stable.  On the 384-tet
+# cube at L = 6 the converged error is 2.251e-5; binary64 FMG + 4 extra V-cycles gives 2.260e-5,
+# binary32 FMG + 2 refinement steps of 2 binary32 V-cycles gives 2.261e-5 (both within 0.5 %).
+FP64_EXTRA = 4
+MIXED_DEFAULT = dict(storage=0, ir_steps=2, ir_vcycles=2)
 
 
 def parse():
@@ -39,9 +43,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="cube384_l6")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
+    ap.add_argument("--storage", type=int, default=None, help="mixed arm: 0 binary32, 1 bfloat16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kernel-only", type=int, default=0,
+                    help="set up the workload, launch the dominant kernel this many times, exit (for ncu)")
     return ap.parse_args()
 
 
@@ -124,10 +131,13 @@ def make_problem(name, L=None):
     return co, ce, LL, f, g, k, ue
 
 
-def params_for(precision, P):
+def params_for(precision, P, storage=None):
     if precision == "fp64":
-        return P.solve_params(nu=2, pre=2, post=1, n_extra=0, precision=0)
-    return P.solve_params(nu=2, pre=2, post=1, n_extra=0, precision=1, **MIXED_DEFAULT)
+        return P.solve_params(nu=2, pre=2, post=1, n_extra=FP64_EXTRA, precision=0)
+    kw = dict(MIXED_DEFAULT)
+    if storage is not None:
+        kw["storage"] = storage
+    return P.solve_params(nu=2, pre=2, post=1, n_extra=0, precision=1, **kw)
 
 
 def peaks():
@@ -144,28 +154,42 @@ FP64_PEAK_TFLOPS = 1.205
 
 # ----------------------------------------------------------------------------- arms
 
-def run_gpu(args, rank, world):
+class Setup:
+    """The workload resident on the GPU: mesh, pinned host inputs, device inputs and output."""
+
+    def __init__(self, args):
+        import numpy as np
+        import torch
+
+        import paper_2508_06049_gb300 as P
+        self.dev = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(self.dev)
+        self.s = torch.cuda.Stream()
+        co, ce, L, f, g, k, ue = make_problem(args.workload)
+        self.mesh = P.Mesh(co, ce, L, stream=self.s)
+        if k is not None:
+            self.mesh.set_coefficient(k)
+        self.x = self.mesh.level_coords(L)
+        self.fh = torch.from_numpy(np.ascontiguousarray(f(self.x))).pin_memory()
+        self.gh = torch.from_numpy(np.ascontiguousarray(g(self.x))).pin_memory()
+        with torch.cuda.stream(self.s):
+            self.fd = self.fh.to("cuda", non_blocking=True)
+            self.gd = self.gh.to("cuda", non_blocking=True)
+            self.ud = torch.empty_like(self.fd)
+        self.s.synchronize()
+        self.mesh.set_data(self.fd, self.gd)
+        self.L, self.ce, self.ue = L, ce, ue
+
+
+def run_arm(args, rank, world, su, precision):
     import numpy as np
     import torch
 
     import paper_2508_06049_gb300 as P
-    dev = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(dev)
-    s = torch.cuda.Stream()
-    co, ce, L, f, g, k, ue = make_problem(args.workload)
-    mesh = P.Mesh(co, ce, L, stream=s)
-    if k is not None:
-        mesh.set_coefficient(k)
-    x = mesh.level_coords(L)
-    fh = torch.from_numpy(np.ascontiguousarray(f(x))).pin_memory()
-    gh = torch.from_numpy(np.ascontiguousarray(g(x))).pin_memory()
-    with torch.cuda.stream(s):
-        fd = fh.to("cuda", non_blocking=True)
-        gd = gh.to("cuda", non_blocking=True)
-        ud = torch.empty_like(fd)
-    s.synchronize()
+    mesh, s, x, L, ce, ue = su.mesh, su.s, su.x, su.L, su.ce, su.ue
+    fh, gh, fd, gd, ud, dev = su.fh, su.gh, su.fd, su.gd, su.ud, su.dev
     mesh.set_data(fd, gd)
-    prm = params_for(args.precision, P)
+    prm = params_for(precision, P, args.storage)
     unknowns = mesh.info.n_unknowns
     frac = 0.125
 
@@ -233,7 +257,7 @@ def run_gpu(args, rank, world):
     # roofline of the dominant kernel: the level-L interior smoothing stage, timed with CUDA events
     # on the library's stream (same launch configuration as inside the solve graph)
     pk, pk_kind = peaks()
-    prec_id = 0 if args.precision == "fp64" else 1
+    prec_id = 0 if precision == "fp64" else 1
     mesh.profile_kernel(0, prec_id, 3)
     torch.cuda.synchronize()
     reps = 50
@@ -246,7 +270,7 @@ def run_gpu(args, rank, world):
     ms_k = k0.elapsed_time(k1) / reps
     gbs = kbytes / (ms_k * 1e-3) / 1e9
     tfl = kflops / (ms_k * 1e-3) / 1e12
-    if args.precision == "fp64":
+    if precision == "fp64":
         rf_obj = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                   "frac": tfl / FP64_PEAK_TFLOPS, "traffic": None,
                   "peak_kind": "measured binary64 FMA throughput (profiles/fp64_fma_peak.md)",
@@ -260,11 +284,11 @@ def run_gpu(args, rank, world):
                    "algorithmic_flops_per_launch": kflops})
     launches = mesh.launch_count(prm) + 7   # solve graph + estimator kernels (j = 1)
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.workload)
-    return dict(value=value, ms=ms, wall=wall, clocks=clocks, e2e=e2e, roofline=rf_obj, cpu=cpu, err=err,
-                unknowns=unknowns, launches=launches, eta=est["eta_j"])
+    return dict(value=value, ms=ms, wall=wall, clocks=clocks, e2e=e2e, roofline=rf_obj, err=err,
+                unknowns=unknowns, launches=launches, eta=est["eta_j"],
+                params={"nu": prm.nu, "pre": prm.pre, "post": prm.post, "n_extra": prm.n_extra,
+                        "precision": prm.precision, "storage": prm.storage, "ir_steps": prm.ir_steps,
+                        "ir_vcycles": prm.ir_vcycles})
 
 
 def cpu_baseline(workload, budget_s=20.0):
@@ -281,7 +305,7 @@ def cpu_baseline(workload, budget_s=20.0):
     t_end = time.perf_counter() + budget_s
     while True:
         t0 = time.perf_counter()
-        u, ws, _ = O.fmg(prob, 2, 2, 1)
+        u, ws, _ = O.fmg(prob, 2, 2, 1, n_extra=FP64_EXTRA)
         est = O.estimate(h, u, ws, 1)
         O.mark_top_fraction(est["eta_T"], 0.125)
         times.append(time.perf_counter() - t0)
@@ -289,8 +313,8 @@ def cpu_baseline(workload, budget_s=20.0):
             break
     t = statistics.median(times)
     return {"value": unknowns / t, "unit": "DoF/s", "cores": 1, "kind": "oracle",
-            "sample": "%s at L=%d (%d unknowns): FMG nu=2 V(2,1) + estimator + marking, median of %d"
-                      % (workload, Ls, unknowns, len(times)), "seconds_per_step": t}
+            "sample": "%s at L=%d (%d unknowns): FMG nu=2 V(2,1) + %d extra V-cycles + estimator + marking, "
+                      "median of %d" % (workload, Ls, unknowns, FP64_EXTRA, len(times)), "seconds_per_step": t}
 
 
 def run_reference(args, rank, world):
@@ -305,10 +329,10 @@ def run_reference(args, rank, world):
     prob = O.Problem(h, f, g)
     unknowns = int(h.levels[Ls].free.sum())
     for _ in range(args.warmup):
-        u, ws, _ = O.fmg(prob, 2, 2, 1)
+        u, ws, _ = O.fmg(prob, 2, 2, 1, n_extra=FP64_EXTRA)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        u, ws, _ = O.fmg(prob, 2, 2, 1)
+        u, ws, _ = O.fmg(prob, 2, 2, 1, n_extra=FP64_EXTRA)
         est = O.estimate(h, u, ws, 1)
         O.mark_top_fraction(est["eta_T"], 0.125)
     t = (time.perf_counter() - t0) / args.steps
@@ -316,10 +340,33 @@ def run_reference(args, rank, world):
     return dict(value=value, ms=t * 1e3, sample="%s at L=%d (%d unknowns)" % (args.workload, Ls, unknowns))
 
 
+def kernel_only(args):
+    """Set up the workload and launch only the dominant kernel (level-L interior smoothing)."""
+    import numpy as np
+    import torch
+
+    import paper_2508_06049_gb300 as P
+    co, ce, L, f, g, k, ue = make_problem(args.workload)
+    s = torch.cuda.Stream()
+    mesh = P.Mesh(co, ce, L, stream=s)
+    x = mesh.level_coords(L)
+    mesh.set_data(np.ascontiguousarray(f(x)), np.ascontiguousarray(g(x)))
+    units, b, fl = mesh.profile_kernel(0, 0 if args.precision == "fp64" else 1, args.kernel_only)
+    torch.cuda.synchronize()
+    print("launched %d x k_smooth_interior (%d nodes, %.0f bytes, %.0f flops per launch)"
+          % (args.kernel_only, units, b, fl))
+
+
 def main():
     args = parse()
+    if args.kernel_only:
+        kernel_only(args)
+        return
     rank, world = dist_init(args.gpus)
     config = {"workload": args.workload, "macro_cells": None, "L": None, "precision": args.precision,
+              "equal_error": "fp64: FMG + %d extra V-cycles; mixed: binary32 FMG + %d x %d binary32 V-cycles "
+                             "in binary64 refinement (both within 0.5 %% of the converged L2 error)"
+                             % (FP64_EXTRA, MIXED_DEFAULT["ir_steps"], MIXED_DEFAULT["ir_vcycles"]),
               "cycle": "FMG nu=2 V(2,1), estimator j=1, marking 12.5%",
               "l2": "level-L vectors exceed the 129 MB L2 (no flush needed)"}
     co, ce, L, *_ = make_problem(args.workload)
@@ -328,7 +375,7 @@ def main():
     if args.impl == "reference":
         r = run_reference(args, rank, world)
         if rank == 0:
-            line = {"impl": "reference", "metric": "FMG DoF/s (FMG + estimator + marking per step)",
+            line = {"impl": "reference", "metric": "FMG DoF/s (FMG + estimator + marking per step, equal error)",
                     "value": r["value"], "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
                     "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
                     "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
@@ -338,16 +385,27 @@ def main():
                             "d2h_bytes_per_step": 0}}
             print(json.dumps(line), flush=True)
         return
-    r = run_gpu(args, rank, world)
+    su = Setup(args)
+    arms = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    res = {a: run_arm(args, rank, world, su, a) for a in arms}
+    head = res[arms[-1]]
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload)
     if rank == 0:
-        line = {"metric": "FMG DoF/s (FMG + estimator + marking per step)", "value": r["value"], "unit": "DoF/s",
-                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"],
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if args.precision == "fp64" else "f32+bf16-storage+f64-refinement",
-                "data": "synthetic", "config": config, "unknowns": r["unknowns"],
-                "l2_error_vs_exact": r["err"], "eta_1": r["eta"], "clocks": r["clocks"], "e2e": r["e2e"],
-                "roofline": r["roofline"], "cpu_baseline": r["cpu"], "gpu_launches": r["launches"] * args.steps,
-                "host_wall_s": r["wall"]}
+        def arm_summary(r):
+            return {"value": r["value"], "ms_per_step": r["ms"], "l2_error_vs_exact": r["err"], "eta_1": r["eta"],
+                    "params": r["params"], "roofline": r["roofline"], "gpu_launches_per_step": r["launches"],
+                    "clocks": r["clocks"]}
+        line = {"metric": "FMG DoF/s (FMG + estimator + marking per step, equal error)", "value": head["value"],
+                "unit": "DoF/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if arms[-1] == "fp64" else "f32+f64-refinement", "data": "synthetic",
+                "config": config, "unknowns": head["unknowns"], "l2_error_vs_exact": head["err"],
+                "clocks": head["clocks"], "e2e": head["e2e"], "roofline": head["roofline"], "cpu_baseline": cpu,
+                "gpu_launches": head["launches"] * args.steps, "arms": {a: arm_summary(res[a]) for a in arms}}
+        if len(arms) == 2:
+            line["speedup_mixed_vs_fp64"] = res["fp64"]["ms"] / res["mixed"]["ms"]
         print(json.dumps(line), flush=True)
 
 

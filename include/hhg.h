@@ -23,8 +23,10 @@
  *     vertices/edges/faces appear once per adjacent cell; inputs must give them equal values,
  *     outputs give them equal values.  N_l = n_cells * closure(2^l) entries, closure(n) =
  *     (n+1)(n+2)/2 in 2D and (n+1)(n+2)(n+3)/6 in 3D.
- *   - All device work of a mesh is ordered on the CUDA stream given at creation (NULL = the
- *     legacy default stream).  Functions that return host results synchronise that stream.
+ *   - All device work of a mesh is ordered on the CUDA stream given at creation.  With NULL the
+ *     mesh creates its own non-blocking stream and, at every entry point, orders it after the work
+ *     the caller queued on the legacy default stream.  Functions that return host results (and
+ *     hhg_fmg_solve, which checks its result for NaN/Inf) synchronise that stream before returning.
  *   - Floating-point is IEEE binary64 unless the solve parameters select the mixed mode.
  */
 #ifndef HHG_H
@@ -163,8 +165,8 @@ int hhg_lattice_selfcheck(int dim, int n);
 /* Profiling support.  Enqueue `reps` launches of one kernel of the solve on the mesh's stream,
  * exactly as the solve launches it, without synchronising (bracket it with events on that stream).
  * kernel 0: macro-interior smoothing stage of colour 0 on level L for the first cell group.
- * precision 0: the binary64 kernel; 1: the binary32 kernel of the mixed path (needs one mixed solve
- * first).  units: nodes updated per launch; bytes / flops: algorithmic bytes and floating-point
+ * precision 0: the binary64 kernel; 1: the binary32 kernel of the mixed path (its buffers are
+ * allocated on first use).  units: nodes updated per launch; bytes / flops: algorithmic bytes and floating-point
  * operations of one launch (the model is stated in the library's design notes).  The launches
  * modify the level-L iterate: run a solve again before hhg_estimate. */
 hhg_status hhg_profile_kernel(hhg_mesh mesh, int kernel, int precision, int reps, long long* units,

@@ -1,0 +1,56 @@
+"""torch.autograd wrapper of the adjoint FMG solve (no counterpart in the paper).
+
+`L2Functional.apply(f_L, k, mesh, in_S, params)` returns J(u) = u^T M_S u, the squared L2 norm of the
+level-L solution u over the macro cells flagged in `in_S`, where u solves the HHG system with nodal
+source f_L (level-L layout, one value per interface copy, equal copies) and per-cell coefficients k.
+Backward returns dJ/df_L and dJ/dk from one adjoint solve in the library (hhg_adjoint_l2): the
+forward solution is kept by the mesh, not stored by autograd, and recomputed only when the inputs
+change.
+
+The gradient with respect to f_L is the derivative with respect to the distinct nodal value, written
+to every interface copy of that node; summing over copies would double count.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from .hhg import Mesh, solve_params
+
+
+class L2Functional(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, f_L, k, mesh: Mesh, in_S, params, g_L):
+        if not f_L.is_cuda:
+            raise ValueError("f_L must be a CUDA tensor in the mesh's level-L layout")
+        kk = k.detach().to("cpu", torch.float64).numpy()
+        mesh.set_coefficient(kk)
+        f = f_L.detach().to(torch.float64).contiguous()
+        g = g_L.detach().to(device=f.device, dtype=torch.float64).contiguous()
+        mesh.set_data(f, g)
+        u = torch.empty_like(f)
+        mesh.solve(params, out=u)
+        mask = np.asarray(in_S, dtype=np.uint8)
+        grad_f = torch.empty_like(f)
+        J, _, grad_k = mesh.adjoint_l2(mask, params=params, grad_f=grad_f)
+        ctx.save_for_backward(grad_f, torch.from_numpy(grad_k))
+        ctx.k_device = k.device
+        ctx.k_dtype = k.dtype
+        return torch.tensor(J, dtype=torch.float64, device=f.device)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        grad_f, grad_k = ctx.saved_tensors
+        gf = gJ * grad_f
+        gk = (gJ.to("cpu") * grad_k).to(device=ctx.k_device, dtype=ctx.k_dtype)
+        return gf, gk, None, None, None, None
+
+
+def l2_functional(f_L, k, mesh, in_S, g_L=None, params=None):
+    """J(u(f_L, k)) = u^T M_S u with gradients through torch.autograd."""
+    if params is None:
+        params = solve_params(nu=2, pre=2, post=1, n_extra=40)
+    if g_L is None:
+        g_L = torch.zeros_like(f_L)
+    return L2Functional.apply(f_L, k, mesh, in_S, params, g_L)

@@ -172,6 +172,20 @@ hhg_status run_graph(hhg_mesh_s* m, const std::string& key, F enqueue) {
   return HHG_OK;
 }
 
+// order the mesh's own stream after work the caller queued on the legacy default stream
+hhg_status enter(hhg_mesh_s* m) {
+  if (!m->own) return HHG_OK;
+  CK(cudaEventRecord(m->ev_legacy, (cudaStream_t)0));
+  CK(cudaStreamWaitEvent(m->own, m->ev_legacy, 0));
+  return HHG_OK;
+}
+
+#define ENTER(m)                        \
+  do {                                  \
+    hhg_status st_e = enter(m);         \
+    if (st_e != HHG_OK) return st_e;    \
+  } while (0)
+
 hhg_status copy_out(hhg_mesh_s* m, void* dst, const void* src, size_t bytes) {
   CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, m->stream));
   return HHG_OK;
@@ -204,7 +218,16 @@ hhg_status hhg_mesh_create(int dim, int n_verts, const double* coords, int n_cel
   m->device = dev;
   m->stream = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess && m->stream == nullptr) {
+    // NULL: the mesh works on its own stream, ordered after the caller's legacy-stream work at
+    // every entry point (and every entry point returning results synchronises it)
+    e = cudaStreamCreateWithFlags(&m->own, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->ev_legacy, cudaEventDisableTiming);
+    m->stream = m->own;
+  }
   if (e != cudaSuccess) {
+    if (m->cap) cudaStreamDestroy(m->cap);
+    if (m->own) cudaStreamDestroy(m->own);
     delete m;
     return cuda_fail(e, "cudaStreamCreate");
   }
@@ -287,6 +310,7 @@ hhg_status hhg_set_coefficient(hhg_mesh m, const double* k) {
 hhg_status hhg_set_data(hhg_mesh m, const double* f, const double* gv) {
   REQUIRE(m && f && gv, HHG_ERR_ARG, "NULL argument");
   DeviceGuard g(m->device);
+  ENTER(m);
   size_t bytes = sizeof(double) * (size_t)m->lv[m->L].N;
   CK(cudaMemcpyAsync(m->fL, f, bytes, cudaMemcpyDefault, m->stream));
   CK(cudaMemcpyAsync(m->gL, gv, bytes, cudaMemcpyDefault, m->stream));
@@ -300,6 +324,7 @@ hhg_status hhg_fmg_solve(hhg_mesh m, const hhg_solve_params* params, double* u_L
   if (st != HHG_OK) return st;
   REQUIRE(m->have_data, HHG_ERR_STATE, "hhg_set_data must be called before hhg_fmg_solve");
   DeviceGuard g(m->device);
+  ENTER(m);
   const hhg_solve_params p = *params;
   if (p.precision == 0) {
     st = run_graph(m, graph_key("fmg", p), [&](cudaStream_t s) { enqueue_fmg(m, p, false, s); });
@@ -313,11 +338,10 @@ hhg_status hhg_fmg_solve(hhg_mesh m, const hhg_solve_params* params, double* u_L
     st = copy_out(m, u_L, m->lv[m->L].u, sizeof(double) * (size_t)m->lv[m->L].N);
     if (st != HHG_OK) return st;
   }
-  int flag = 0;
-  CK(cudaMemcpyAsync(&flag, m->d_flag, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaMemcpyAsync(m->h_flag, m->d_flag, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
   CK(cudaStreamSynchronize(m->stream));
   m->solved = true;
-  REQUIRE(flag == 0, HHG_ERR_DIVERGED, "solution contains NaN or Inf");
+  REQUIRE(*m->h_flag == 0, HHG_ERR_DIVERGED, "solution contains NaN or Inf");
   return HHG_OK;
 }
 
@@ -327,6 +351,7 @@ hhg_status hhg_estimate(hhg_mesh m, int j, double* eta_T, double* eta_jT, hhg_es
   const int L = m->L;
   REQUIRE(j >= 1 && j <= L - 1, HHG_ERR_ARG, "need 1 <= j <= L-1 (L = %d)", L);
   DeviceGuard g(m->device);
+  ENTER(m);
   cudaStream_t s = m->stream;
   const int l = L - j;
   const int nc = m->nc;
@@ -341,32 +366,36 @@ hhg_status hhg_estimate(hhg_mesh m, int j, double* eta_T, double* eta_jT, hhg_es
   CHECK_PTR(m->dM);
   CHECK_PTR(m->lv[L].d_ijk);
   CHECK_PTR(m->lv[L].tmp);
-  DBG_SYNC("before estimate");
-  // e~_{L-1} = u_L - w_{L-1} (eta_T)
-  launch_mass_norm_sq(m, uL, m->lv[L - 1].w, red, s);
-  DBG_SYNC("mass norm of u_L - w_{L-1}");
-  // e~_l = u_L - I w_l (w_l on level l+1)
-  const double* v = m->lv[l].w;
-  for (int q = l + 2; q <= L; ++q) {
-    launch_prolong(m, q, v, m->lv[q].tmp, s);
-    DBG_SYNC("prolong w_l");
-    v = m->lv[q].tmp;
-  }
-  launch_mass_norm_sq(m, uL, v, red + nc, s);
-  DBG_SYNC("mass norm of e_l");
-  // e~_{l-1} = u_L - I w_{l-1} (w_{l-1} on level l)
-  v = m->lv[l - 1].w;
-  for (int q = l + 1; q <= L; ++q) {
-    launch_prolong(m, q, v, m->lv[q].tmp, s);
-    DBG_SYNC("prolong w_{l-1}");
-    v = m->lv[q].tmp;
-  }
-  launch_mass_norm_sq(m, uL, v, red + 2 * nc, s);
-  DBG_SYNC("mass norm of e_{l-1}");
-  std::vector<double> h((size_t)3 * nc);
-  CK(cudaMemcpyAsync(h.data(), red, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  const int jj = j;
+  hhg_status st = run_graph(m, "est:" + std::to_string(jj), [&](cudaStream_t cs) {
+    // e~_{L-1} = u_L - w_{L-1} (eta_T)
+    launch_mass_norm_sq(m, uL, m->lv[L - 1].w, red, cs);
+    // e~_l = u_L - I w_l (w_l lives on level l+1); for j = 1 it is e~_{L-1} again
+    if (l == L - 1) {
+      cudaMemcpyAsync(red + nc, red, sizeof(double) * nc, cudaMemcpyDeviceToDevice, cs);
+    } else {
+      const double* v = m->lv[l].w;
+      for (int q = l + 2; q <= L; ++q) {
+        launch_prolong(m, q, v, m->lv[q].tmp, cs);
+        v = m->lv[q].tmp;
+      }
+      launch_mass_norm_sq(m, uL, v, red + nc, cs);
+    }
+    const double* v;
+    // e~_{l-1} = u_L - I w_{l-1} (w_{l-1} lives on level l)
+    v = m->lv[l - 1].w;
+    for (int q = l + 1; q <= L; ++q) {
+      launch_prolong(m, q, v, m->lv[q].tmp, cs);
+      v = m->lv[q].tmp;
+    }
+    launch_mass_norm_sq(m, uL, v, red + 2 * nc, cs);
+  });
+  if (st != HHG_OK) return st;
+  DBG_SYNC("estimator graph");
+  CK(cudaMemcpyAsync(m->h_red, red, sizeof(double) * 3 * (size_t)nc, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
+  const double* h = m->h_red;
   double sT = 0, sl = 0, slm1 = 0;
   for (int c = 0; c < nc; ++c) {
     sT += h[c];
@@ -396,6 +425,7 @@ hhg_status hhg_get_vector(hhg_mesh m, int which, int level, double* out) {
   REQUIRE(m && out, HHG_ERR_ARG, "NULL argument");
   REQUIRE(level >= 0 && level <= m->L, HHG_ERR_ARG, "level out of range");
   DeviceGuard g(m->device);
+  ENTER(m);
   const LevelData& Lv = m->lv[level];
   if (which == 0) {
     CK(cudaMemcpyAsync(out, Lv.u, sizeof(double) * Lv.N, cudaMemcpyDefault, m->stream));
@@ -426,6 +456,7 @@ hhg_status hhg_apply(hhg_mesh m, int level, int op, const double* in, double* ou
   REQUIRE(op != 2 || level >= 1, HHG_ERR_ARG, "interpolation needs level >= 1");
   REQUIRE(op != 3 || (level >= 1 && nsweeps >= 0), HHG_ERR_ARG, "sweeps need level >= 1");
   DeviceGuard g(m->device);
+  ENTER(m);
   cudaStream_t s = m->stream;
   LevelData& Lv = m->lv[level];
   size_t nin = (size_t)(op == 2 ? m->lv[level - 1].N : Lv.N);
@@ -467,6 +498,7 @@ hhg_status hhg_adjoint_l2(hhg_mesh m, const hhg_solve_params* params, const unsi
   REQUIRE(params->precision == 0, HHG_ERR_ARG, "the adjoint solve runs in binary64 (precision = 0)");
   REQUIRE(m->solved, HHG_ERR_STATE, "hhg_adjoint_l2 needs a previous hhg_fmg_solve");
   DeviceGuard g(m->device);
+  ENTER(m);
   cudaStream_t s = m->stream;
   const int L = m->L, nc = m->nc;
   LevelData& LL = m->lv[L];
@@ -533,9 +565,11 @@ hhg_status hhg_profile_kernel(hhg_mesh m, int kernel, int precision, int reps, l
   REQUIRE(precision == 0 || precision == 1, HHG_ERR_ARG, "precision must be 0 or 1");
   REQUIRE(reps >= 0 && reps <= 100000, HHG_ERR_ARG, "reps in [0, 100000]");
   DeviceGuard g(m->device);
+  ENTER(m);
   if (precision == 1) {
-    REQUIRE(m->mixed_alloc, HHG_ERR_STATE, "run a mixed solve before profiling its kernel");
-    hhg_status st = mixed_profile_interior(m, reps, m->stream, units, bytes, flops);
+    hhg_status st = mixed_prepare(m, m->mixed_alloc ? m->last_storage : 1);
+    if (st != HHG_OK) return st;
+    st = mixed_profile_interior(m, reps, m->stream, units, bytes, flops);
     if (st != HHG_OK) return st;
   } else {
     launch_profile_interior(m, 0, reps, m->stream, units, bytes, flops);

@@ -46,6 +46,10 @@ struct LevelData {
   // face colour lists (3D): colour c entries [fcol_off[c], fcol_off[c+1]) of a | b << 16
   int64_t fcol_off[4] = {0, 0, 0, 0};
   int32_t* d_fcol = nullptr;
+  // the same split into rim (next to a face edge) and inner entries per colour
+  int64_t frim_off[4] = {0, 0, 0, 0}, fin_off[4] = {0, 0, 0, 0};
+  int32_t* d_frim = nullptr;
+  int32_t* d_fin = nullptr;
   // binary64 vectors
   double* u = nullptr;    // solution / correction
   double* b = nullptr;    // rhs M_l f_l (partial at interfaces)
@@ -67,6 +71,10 @@ struct hhg_mesh_s {
   int dim = 2, L = 1, nc = 0, nv = 0, device = 0;
   cudaStream_t stream = nullptr;  // caller's stream
   cudaStream_t cap = nullptr;     // internal stream used for graph capture
+  cudaStream_t own = nullptr;     // stream owned by the mesh when the caller passes NULL
+  cudaEvent_t ev_legacy = nullptr;  // orders the mesh stream after the caller's legacy-stream work
+  double* h_red = nullptr;        // pinned host staging of per-cell reductions (4 x n_cells)
+  int* h_flag = nullptr;          // pinned host copy of the non-finite flag
   std::vector<double> coords;
   std::vector<int> cells;
   std::vector<double> k;
@@ -75,6 +83,8 @@ struct hhg_mesh_s {
   double* dM = nullptr;           // mass stencils (unit level scale)
   float* dS32 = nullptr;
   float* dM32 = nullptr;
+  double* d_inv0 = nullptr;       // 1 / interior diagonal per cell (unit level scale, with k_T)
+  float* d_inv0f = nullptr;
   uint16_t* d_dirmask = nullptr;  // per cell: bit t set if nodes of boundary type t are Dirichlet
   std::vector<uint16_t> dirmask;
   std::vector<hhg::Group> groups;

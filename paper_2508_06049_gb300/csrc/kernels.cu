@@ -73,8 +73,8 @@ static void interior_stage(hhg_mesh_s* m, int l, int gi, int colour, double* u, 
   if (b <= a || G.cells.empty()) return;
   dim3 grid(blocks_for(b - a), (unsigned)G.cells.size());
   k_smooth_interior<DIM, PM, double, double, double><<<grid, kBlock, 0, s>>>(
-      G.d_cells, Lv.d_icol + a, b - a, ctx(m, l), m->dS, stiff_scale(DIM, Lv.n), Vec<double, double>{u, nullptr},
-      CVec<double, double>{rhs, nullptr});
+      G.d_cells, Lv.d_icol + a, b - a, ctx(m, l), m->dS, stiff_scale(DIM, Lv.n), m->d_inv0,
+      1.0 / stiff_scale(DIM, Lv.n), Vec<double, double>{u, nullptr}, CVec<double, double>{rhs, nullptr});
 }
 
 // compile-time stencil patterns: the full stencil and the Kuhn / right-isosceles patterns
@@ -98,19 +98,21 @@ static void interior_stage_dispatch(hhg_mesh_s* m, int l, int gi, int colour, do
 }
 
 template <int DIM>
-static void iface_stage(hhg_mesh_s* m, int l, const Prims& P, int nverts, int cnt, int parity, const int32_t* flist,
-                        double* u, const double* rhs, cudaStream_t s) {
-  if (P.count == 0 || cnt <= 0) return;
+static void iface_stage(hhg_mesh_s* m, int l, const Prims& P, int nverts, int parity, int cnt_rim, int cnt_inner,
+                        const int32_t* rim_list, const int32_t* inner_list, double* u, const double* rhs,
+                        cudaStream_t s) {
+  if (P.count == 0 || (cnt_rim <= 0 && cnt_inner <= 0)) return;
   const LevelData& Lv = m->lv[l];
-  int64_t nthreads = (int64_t)P.count * cnt;
-  double* du = Lv.tmp;  // residual scratch is free during a sweep (sized N_l >= nthreads)
+  int64_t nthreads = (int64_t)P.count * (cnt_rim + cnt_inner);
+  double* du = Lv.tmp;  // residual scratch is free during a sweep (sized N_l >= the rim nodes)
   double ss = stiff_scale(DIM, Lv.n);
-  k_iface_compute<DIM, double, double, double><<<blocks_for(nthreads), kBlock, 0, s>>>(
-      P.count, nverts, cnt, parity, flist, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l), m->dS, ss,
-      CVec<double, double>{u, nullptr}, CVec<double, double>{rhs, nullptr}, du);
-  k_iface_apply<DIM, double, double><<<blocks_for(nthreads), kBlock, 0, s>>>(
-      P.count, nverts, cnt, parity, flist, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l),
-      Vec<double, double>{u, nullptr}, du);
+  k_iface_stage<DIM, double, double, double><<<blocks_for(nthreads), kBlock, 0, s>>>(
+      P.count, nverts, parity, cnt_rim, cnt_inner, rim_list, inner_list, P.d_ptr, P.d_cell, P.d_loc, P.d_dir,
+      ctx(m, l), m->dS, ss, Vec<double, double>{u, nullptr}, CVec<double, double>{rhs, nullptr}, du);
+  if (cnt_rim > 0)
+    k_iface_apply<DIM, double, double><<<blocks_for((int64_t)P.count * cnt_rim), kBlock, 0, s>>>(
+        P.count, nverts, parity, cnt_rim, rim_list, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l),
+        Vec<double, double>{u, nullptr}, du);
 }
 
 template <int DIM>
@@ -126,17 +128,20 @@ static void sweep_impl(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s, 
     if (st == 0) {
       const Prims& P = m->verts;
       if (P.count)
-        k_smooth_vertex<DIM, double, double, double><<<blocks_for(P.count), kBlock, 0, s>>>(
+        k_smooth_vertex<DIM, double, double, double><<<blocks_for((int64_t)P.count * 32), kBlock, 0, s>>>(
             P.count, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l), m->dS, ss, Vec<double, double>{u, nullptr},
             CVec<double, double>{rhs, nullptr});
     } else if (st <= 2) {
-      int parity = (st == 2);  // stage 1: even local index, stage 2: odd
-      int cnt = parity ? n / 2 : n / 2 - 1;
-      iface_stage<DIM>(m, l, m->edges, 2, cnt, parity, nullptr, u, rhs, s);
+      // stage 1: even local index (no coupling inside the stage); stage 2: odd, t = 1 and n-1 are rim
+      int parity = (st == 2);
+      int cnt_rim = parity ? (n == 2 ? 1 : 2) : 0;
+      int cnt_inner = parity ? (n == 2 ? 0 : n / 2 - 2) : n / 2 - 1;
+      iface_stage<DIM>(m, l, m->edges, 2, parity, cnt_rim, cnt_inner, nullptr, nullptr, u, rhs, s);
     } else if (DIM == 3 && st <= 5) {
       int c = st - 3;
-      int64_t a = Lv.fcol_off[c], b = Lv.fcol_off[c + 1];
-      iface_stage<DIM>(m, l, m->faces, 3, (int)(b - a), 0, Lv.d_fcol + a, u, rhs, s);
+      iface_stage<DIM>(m, l, m->faces, 3, 0, (int)(Lv.frim_off[c + 1] - Lv.frim_off[c]),
+                       (int)(Lv.fin_off[c + 1] - Lv.fin_off[c]), Lv.d_frim + Lv.frim_off[c],
+                       Lv.d_fin + Lv.fin_off[c], u, rhs, s);
     } else {
       int c = st - (DIM == 3 ? 6 : 3);
       for (size_t gi = 0; gi < m->groups.size(); ++gi)

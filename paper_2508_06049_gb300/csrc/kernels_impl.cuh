@@ -56,6 +56,7 @@ __device__ __forceinline__ R partial_residual(const R* __restrict__ S, int T, in
   int64_t off[15];
   neighbour_offsets(DIM, n, j, k, off);
   uint32_t vm = valid_dirs(DIM, t);
+  mask_offsets(DIM, vm, off);
   const R* s = S + (size_t)T * kStencilStride + t * kMaxDirs;
   R acc = 0;
 #pragma unroll
@@ -123,7 +124,8 @@ __global__ void k_init_coarse(LevelCtx lc, int nL, int64_t NtL, int shift, const
 template <int DIM, int PM, typename R, typename U, typename B>
 __global__ void __launch_bounds__(kBlock) k_smooth_interior(const int* __restrict__ gcells, const int32_t* __restrict__ list,
                                                             int64_t len, LevelCtx lc, const R* __restrict__ S, R sscale,
-                                                            Vec<R, U> u, CVec<R, B> rhs) {
+                                                            const R* __restrict__ inv0, R isscale, Vec<R, U> u,
+                                                            CVec<R, B> rhs) {
   int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (pos >= len) return;
   int T = gcells[blockIdx.y];
@@ -148,31 +150,41 @@ __global__ void __launch_bounds__(kBlock) k_smooth_interior(const int* __restric
       acc += s[2 * q + 2] * u.get(g + off[2 * q + 2]);
     }
   }
+  // residual and update; 1/(sscale * a_ii) = inv0[T] * (1/sscale) exactly (power-of-two scale)
   R r = rhs.get(g) - sscale * acc;
-  u.set(g, uc + r / (sscale * s[0]));
+  u.set(g, uc + r * (inv0[T] * isscale));
 }
 
-// macro vertices: never coupled to each other on levels >= 1, so one pass
+// macro vertices: never coupled to each other on levels >= 1, so one pass.  One warp per vertex,
+// lanes over the vertex's cell copies (scattered loads in parallel), fixed-order shuffle sums.
 template <int DIM, typename R, typename U, typename B>
 __global__ void k_smooth_vertex(int nprim, const int* __restrict__ ptr, const int* __restrict__ cell,
                                 const int* __restrict__ locv, const unsigned char* __restrict__ dir, LevelCtx lc,
                                 const R* __restrict__ S, R sscale, Vec<R, U> u, CVec<R, B> rhs) {
-  int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= nprim || dir[v]) return;
+  int v = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (v >= nprim || dir[v]) return;  // uniform across the warp
   CVec<R, U> uc{u.p, u.scale};
   R res = 0, diag = 0;
-  int64_t g0 = 0;
-  for (int c = ptr[v]; c < ptr[v + 1]; ++c) {
+  int c0 = ptr[v], c1 = ptr[v + 1];
+  int i0, j0, k0;
+  prim_position(locv[c0], 1, lc.n, 0, 0, i0, j0, k0);
+  R uold = u.get((int64_t)cell[c0] * lc.Nt + packed_index(DIM, lc.n, i0, j0, k0));
+  for (int c = c0 + lane; c < c1; c += 32) {
     int i, j, k;
     prim_position(locv[c], 1, lc.n, 0, 0, i, j, k);
     R dg;
     int64_t g;
     res += partial_residual<DIM>(S, cell[c], lc.n, lc.Nt, i, j, k, sscale, uc, rhs, dg, g);
     diag += dg;
-    g0 = g;
   }
-  R unew = u.get(g0) + res / diag;
-  for (int c = ptr[v]; c < ptr[v + 1]; ++c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    res += __shfl_xor_sync(0xffffffffu, res, o);
+    diag += __shfl_xor_sync(0xffffffffu, diag, o);
+  }
+  R unew = uold + res / diag;
+  for (int c = c0 + lane; c < c1; c += 32) {
     int i, j, k;
     prim_position(locv[c], 1, lc.n, 0, 0, i, j, k);
     int64_t p = packed_index(DIM, lc.n, i, j, k);
@@ -181,58 +193,82 @@ __global__ void k_smooth_vertex(int nprim, const int* __restrict__ ptr, const in
   }
 }
 
-// edge (parity) and face (colour list) stages: compute all updates from stage-start values, then
-// apply (nodes of one stage may couple across a shared macro vertex or edge)
-template <int DIM, typename R, typename U, typename B>
-__global__ void k_iface_compute(int nprim, int nverts, int cnt, int parity, const int32_t* __restrict__ flist,
-                                const int* __restrict__ ptr, const int* __restrict__ cell, const int* __restrict__ locv,
-                                const unsigned char* __restrict__ dir, LevelCtx lc, const R* __restrict__ S, R sscale,
-                                CVec<R, U> u, CVec<R, B> rhs, R* __restrict__ du) {
-  int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= (int64_t)nprim * cnt) return;
-  int e = (int)(tid / cnt), q = (int)(tid % cnt);
-  if (dir[e]) {
-    du[tid] = 0;
-    return;
-  }
-  int s, t;
+// Edge (parity) and face (colour) stages.  Every node of a stage is updated from the values at the
+// start of the stage.  Nodes of one stage can couple only next to a shared macro vertex (odd edge
+// nodes t = 1, n-1) or a shared macro edge (face nodes with a = 1, b = 1 or a + b = n-1): these "rim"
+// nodes are computed into du and applied by a second kernel.  All other ("inner") nodes of the stage
+// have no neighbour in the stage, so one pass updates them in place.
+//
+// Position of entry q of a stage: edges: rim q -> t in {1, n-1} (odd stage only), inner q ->
+// t = 2q+3 (odd) or 2q+2 (even); faces: (a, b) from the stage's rim or inner list.
+__device__ __forceinline__ void stage_position(int nverts, int parity, bool rim, int n, int q,
+                                               const int32_t* __restrict__ list, int& s, int& t) {
   if (nverts == 2) {
-    s = parity ? 2 * q + 1 : 2 * q + 2;
     t = 0;
+    if (rim) s = (q == 0) ? 1 : n - 1;
+    else s = parity ? 2 * q + 3 : 2 * q + 2;
   } else {
-    int32_t ab = flist[q];
+    int32_t ab = list[q];
     s = ab & 0xffff;
     t = ab >> 16;
   }
+}
+
+template <int DIM, typename R, typename U, typename B>
+__global__ void k_iface_stage(int nprim, int nverts, int parity, int cnt_rim, int cnt_inner,
+                              const int32_t* __restrict__ rim_list, const int32_t* __restrict__ inner_list,
+                              const int* __restrict__ ptr, const int* __restrict__ cell, const int* __restrict__ locv,
+                              const unsigned char* __restrict__ dir, LevelCtx lc, const R* __restrict__ S, R sscale,
+                              Vec<R, U> u, CVec<R, B> rhs, R* __restrict__ du) {
+  int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t n_rim = (int64_t)nprim * cnt_rim;
+  bool rim = tid < n_rim;
+  int64_t lt = rim ? tid : tid - n_rim;
+  int cnt = rim ? cnt_rim : cnt_inner;
+  if (!rim && lt >= (int64_t)nprim * cnt_inner) return;
+  int e = (int)(lt / cnt), q = (int)(lt % cnt);
+  if (dir[e]) {
+    if (rim) du[tid] = 0;
+    return;
+  }
+  int s, t;
+  stage_position(nverts, parity, rim, lc.n, q, rim ? rim_list : inner_list, s, t);
+  CVec<R, U> uc{u.p, u.scale};
   R res = 0, diag = 0;
+  int64_t g0 = -1;
   for (int c = ptr[e]; c < ptr[e + 1]; ++c) {
     int i, j, k;
     prim_position(locv[c], nverts, lc.n, s, t, i, j, k);
     R dg;
     int64_t g;
-    res += partial_residual<DIM>(S, cell[c], lc.n, lc.Nt, i, j, k, sscale, u, rhs, dg, g);
+    res += partial_residual<DIM>(S, cell[c], lc.n, lc.Nt, i, j, k, sscale, uc, rhs, dg, g);
     diag += dg;
+    if (g0 < 0) g0 = g;
   }
-  du[tid] = res / diag;
+  if (rim) {
+    du[tid] = res / diag;
+    return;
+  }
+  R unew = u.get(g0) + res / diag;
+  for (int c = ptr[e]; c < ptr[e + 1]; ++c) {
+    int i, j, k;
+    prim_position(locv[c], nverts, lc.n, s, t, i, j, k);
+    int64_t p = packed_index(DIM, lc.n, i, j, k);
+    if (HHG_OOB(p, lc.Nt, 91)) continue;
+    u.set((int64_t)cell[c] * lc.Nt + p, unew);
+  }
 }
 
 template <int DIM, typename R, typename U>
-__global__ void k_iface_apply(int nprim, int nverts, int cnt, int parity, const int32_t* __restrict__ flist,
+__global__ void k_iface_apply(int nprim, int nverts, int parity, int cnt_rim, const int32_t* __restrict__ rim_list,
                               const int* __restrict__ ptr, const int* __restrict__ cell, const int* __restrict__ locv,
                               const unsigned char* __restrict__ dir, LevelCtx lc, Vec<R, U> u, const R* __restrict__ du) {
   int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= (int64_t)nprim * cnt) return;
-  int e = (int)(tid / cnt), q = (int)(tid % cnt);
+  if (tid >= (int64_t)nprim * cnt_rim) return;
+  int e = (int)(tid / cnt_rim), q = (int)(tid % cnt_rim);
   if (dir[e]) return;
   int s, t;
-  if (nverts == 2) {
-    s = parity ? 2 * q + 1 : 2 * q + 2;
-    t = 0;
-  } else {
-    int32_t ab = flist[q];
-    s = ab & 0xffff;
-    t = ab >> 16;
-  }
+  stage_position(nverts, parity, true, lc.n, q, rim_list, s, t);
   R d = du[tid];
   for (int c = ptr[e]; c < ptr[e + 1]; ++c) {
     int i, j, k;
@@ -275,6 +311,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(const int* __restrict__ gce
     }
   } else {
     uint32_t vm = valid_dirs(DIM, t);
+    mask_offsets(DIM, vm, off);
 #pragma unroll
     for (int d = 1; d < ndirs<DIM>(); ++d)
       if ((vm >> d & 1) && !HHG_OOB(loc + off[d], lc.Nt, 51)) acc += s[d] * u.get(g + off[d]);
@@ -302,6 +339,7 @@ __global__ void k_restrict(LevelCtx fc, LevelCtx cc, const uint16_t* __restrict_
   int64_t off[15];
   neighbour_offsets(DIM, fc.n, 2 * j, 2 * k, off);
   uint32_t vm = valid_dirs(DIM, t);
+  mask_offsets(DIM, vm, off);
   R acc = 0;
 #pragma unroll
   for (int d = 1; d < ndirs<DIM>(); ++d)
@@ -388,16 +426,22 @@ __global__ void __launch_bounds__(1024) k_coarse(int n0f, const int* __restrict_
   extern __shared__ double r[];
   CVec<double, double> uc{u, nullptr};
   CVec<double, double> rc{rhs, nullptr};
-  for (int q = threadIdx.x; q < n0f; q += blockDim.x) {
-    int v = cf[q];
-    double res = 0, dg;
-    for (int c = ptr[v]; c < ptr[v + 1]; ++c) {
-      int i, j, k;
-      prim_position(locv[c], 1, lc.n, 0, 0, i, j, k);
-      int64_t g;
-      res += partial_residual<DIM>(S, cell[c], lc.n, lc.Nt, i, j, k, 1.0, uc, rc, dg, g);
+  {
+    // residual of each free coarse vertex: one warp per vertex, lanes over its cell copies
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int q = warp; q < n0f; q += nw) {
+      int v = cf[q];
+      double res = 0, dg;
+      for (int c = ptr[v] + lane; c < ptr[v + 1]; c += 32) {
+        int i, j, k;
+        prim_position(locv[c], 1, lc.n, 0, 0, i, j, k);
+        int64_t g;
+        res += partial_residual<DIM>(S, cell[c], lc.n, lc.Nt, i, j, k, 1.0, uc, rc, dg, g);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) res += __shfl_xor_sync(0xffffffffu, res, o);
+      if (lane == 0) r[q] = res;
     }
-    r[q] = res;
   }
   __syncthreads();
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -422,9 +466,13 @@ __global__ void __launch_bounds__(1024) k_coarse(int n0f, const int* __restrict_
 
 // ---------------------------------------------------------------- reductions (row 8, row 11)
 
-// Per node p of a cell's closure: c_p = x_p * sum_d Stab[t][d] y_{p+d}, with x = y = a - b (mass form
-// of a difference; b may be null) or x = a, y = b (bilinear form).  Written to a level-L scratch
-// vector; k_cell_sum then adds the contributions of each cell in a fixed order.
+// Per node p of a cell's closure, the symmetric-form contribution
+//   c_p = S[t][0] x_p y_p + sum_{d positive, valid} S[t][d] (x_p y_{p+d} + x_{p+d} y_p),
+// with x = y = a - b (b may be null) for the mass form, or x = a, y = b for a bilinear form.  Summed
+// over the closure this is x^T S_T y, because the partial stencil of a cell is symmetric (the entry
+// p->p+d seen from p equals the entry p+d->p seen from p+d: both sum the cell's elements on that
+// edge), so each lattice edge is visited once.  Written to a level-L scratch vector; k_cell_sum adds
+// each cell's contributions in a fixed order.
 template <int DIM, bool DIFF>
 __global__ void k_node_form(LevelCtx lc, const double* __restrict__ tab, const double* __restrict__ a,
                             const double* __restrict__ b, double* __restrict__ contrib) {
@@ -439,25 +487,36 @@ __global__ void k_node_form(LevelCtx lc, const double* __restrict__ tab, const d
   int64_t off[15];
   neighbour_offsets(DIM, lc.n, j, k, off);
   uint32_t vm = valid_dirs(DIM, t);
+  mask_offsets(DIM, vm, off);
   const double* s = tab + (size_t)T * kStencilStride + t * kMaxDirs;
-  double x = a[g];
-  if (DIFF && b) x -= b[g];
-  double sum = 0;
-  for (int d = 0; d < ndirs<DIM>(); ++d) {
+  double xp, yp;
+  if (DIFF) {
+    xp = a[g];
+    if (b) xp -= b[g];
+    yp = xp;
+  } else {
+    xp = a[g];
+    yp = b[g];
+  }
+  double sum = s[0] * xp * yp;
+#pragma unroll
+  for (int q = 0; q < npairs<DIM>(); ++q) {
+    int d = 2 * q + 1;
     if (!(vm >> d & 1)) continue;
     if (HHG_OOB(loc + off[d], lc.Nt, 13)) continue;
-    double y;
+    double xq, yq;
     if (DIFF) {
-      y = a[g + off[d]];
-      if (b) y -= b[g + off[d]];
+      xq = a[g + off[d]];
+      if (b) xq -= b[g + off[d]];
+      yq = xq;
     } else {
-      y = b[g + off[d]];
+      xq = a[g + off[d]];
+      yq = b[g + off[d]];
     }
-    sum += s[d] * y;
+    sum += s[d] * (xp * yq + xq * yp);
   }
-  contrib[g] = x * sum;
+  contrib[g] = sum;
 }
-
 
 // ---------------------------------------------------------------- operators for testing / adjoint
 
@@ -481,6 +540,7 @@ __global__ void k_apply_partial(LevelCtx lc, const double* __restrict__ tab, dou
   int64_t off[15];
   neighbour_offsets(DIM, lc.n, j, k, off);
   uint32_t vm = valid_dirs(DIM, t);
+  mask_offsets(DIM, vm, off);
   const double* s = tab + (size_t)T * kStencilStride + t * kMaxDirs;
   double acc = 0;
   for (int d = 0; d < ndirs<DIM>(); ++d)
@@ -516,5 +576,34 @@ __global__ void k_sum_prims(int nprim, int nverts, int cnt, const int32_t* __res
 }
 
 
+
+// Collect partial interface values: the sum over a primitive node's copies goes to its first copy,
+// the other copies get 0 (still a partial split of the same row).  Used before narrowing a binary64
+// residual, whose partials cancel, to binary32.
+template <int DIM>
+__global__ void k_owner_collect(int nprim, int nverts, int cnt, const int32_t* __restrict__ flist,
+                                const int* __restrict__ ptr, const int* __restrict__ cell, const int* __restrict__ locv,
+                                LevelCtx lc, double* __restrict__ v) {
+  int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)nprim * cnt) return;
+  int e = (int)(tid / cnt), q = (int)(tid % cnt);
+  int s = 0, t = 0;
+  if (nverts == 2) s = q + 1;
+  else if (nverts == 3) {
+    s = flist[q] & 0xffff;
+    t = flist[q] >> 16;
+  }
+  double sum = 0;
+  for (int c = ptr[e]; c < ptr[e + 1]; ++c) {
+    int i, j, k;
+    prim_position(locv[c], nverts, lc.n, s, t, i, j, k);
+    sum += v[(int64_t)cell[c] * lc.Nt + packed_index(DIM, lc.n, i, j, k)];
+  }
+  for (int c = ptr[e]; c < ptr[e + 1]; ++c) {
+    int i, j, k;
+    prim_position(locv[c], nverts, lc.n, s, t, i, j, k);
+    v[(int64_t)cell[c] * lc.Nt + packed_index(DIM, lc.n, i, j, k)] = (c == ptr[e]) ? sum : 0.0;
+  }
+}
 
 }  // namespace hhg

