@@ -609,6 +609,7 @@ int hhg_lattice_selfcheck(int dim, int n) {
         neighbour_offsets(dim, n, j, k, off);
         int t = boundary_type(dim, n, i, j, k);
         uint32_t vm = valid_dirs(dim, t);
+        if (vm != valid_dirs_tab(dim, t)) ++bad;
         for (int d = 0; d < (dim == 2 ? 7 : 15); ++d) {
           int di, dj, dk;
           dir_vec(dim, d, di, dj, dk);

@@ -55,7 +55,7 @@ __device__ __forceinline__ R partial_residual(const R* __restrict__ S, int T, in
   if (HHG_OOB(p, Nt, 31)) return (R)0;
   int64_t off[15];
   neighbour_offsets(DIM, n, j, k, off);
-  uint32_t vm = valid_dirs(DIM, t);
+  uint32_t vm = valid_dirs_tab(DIM, t);
   mask_offsets(DIM, vm, off);
   const R* s = S + (size_t)T * kStencilStride + t * kMaxDirs;
   R acc = 0;
@@ -84,7 +84,7 @@ __global__ void k_build_rhs(LevelCtx lc, int nL, int64_t NtL, int shift, const d
     b[g] = 0.0;
     return;
   }
-  uint32_t vm = valid_dirs(DIM, t);
+  uint32_t vm = valid_dirs_tab(DIM, t);
   const double* s = Mst + (size_t)T * kStencilStride + t * kMaxDirs;
   double acc = 0;
   for (int d = 0; d < ndirs<DIM>(); ++d) {
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(const int* __restrict__ gce
       }
     }
   } else {
-    uint32_t vm = valid_dirs(DIM, t);
+    uint32_t vm = valid_dirs_tab(DIM, t);
     mask_offsets(DIM, vm, off);
 #pragma unroll
     for (int d = 1; d < ndirs<DIM>(); ++d)
@@ -338,7 +338,7 @@ __global__ void k_restrict(LevelCtx fc, LevelCtx cc, const uint16_t* __restrict_
   int64_t gf = (int64_t)T * fc.Nt + pf;
   int64_t off[15];
   neighbour_offsets(DIM, fc.n, 2 * j, 2 * k, off);
-  uint32_t vm = valid_dirs(DIM, t);
+  uint32_t vm = valid_dirs_tab(DIM, t);
   mask_offsets(DIM, vm, off);
   R acc = 0;
 #pragma unroll
@@ -486,7 +486,7 @@ __global__ void k_node_form(LevelCtx lc, const double* __restrict__ tab, const d
   int64_t g = (int64_t)T * lc.Nt + loc;
   int64_t off[15];
   neighbour_offsets(DIM, lc.n, j, k, off);
-  uint32_t vm = valid_dirs(DIM, t);
+  uint32_t vm = valid_dirs_tab(DIM, t);
   mask_offsets(DIM, vm, off);
   const double* s = tab + (size_t)T * kStencilStride + t * kMaxDirs;
   double xp, yp;
@@ -539,7 +539,7 @@ __global__ void k_apply_partial(LevelCtx lc, const double* __restrict__ tab, dou
   }
   int64_t off[15];
   neighbour_offsets(DIM, lc.n, j, k, off);
-  uint32_t vm = valid_dirs(DIM, t);
+  uint32_t vm = valid_dirs_tab(DIM, t);
   mask_offsets(DIM, vm, off);
   const double* s = tab + (size_t)T * kStencilStride + t * kMaxDirs;
   double acc = 0;

@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(1024) k_coarse_mixed(int n0f, const int* __res
         int64_t g = (int64_t)T * lc.Nt + p;
         int64_t off[15];
         neighbour_offsets(DIM, lc.n, j, k, off);
-        uint32_t vm = valid_dirs(DIM, t);
+        uint32_t vm = valid_dirs_tab(DIM, t);
         mask_offsets(DIM, vm, off);
         const double* s = S + (size_t)T * kStencilStride + t * kMaxDirs;
         double acc = 0;

@@ -96,6 +96,13 @@ HHG_HD uint32_t valid_dirs(int dim, int t) {
   return m;
 }
 
+// valid_dirs() tabulated (checked against the loop by hhg_lattice_selfcheck)
+HHG_HD uint32_t valid_dirs_tab(int dim, int t) {
+  constexpr uint32_t k2[16] = {0x7f, 0x3b, 0x4f, 0xb, 0x75, 0x31, 0x45, 0x1, 0x7f, 0x3b, 0x4f, 0xb, 0x75, 0x31, 0x45, 0x1};
+  constexpr uint32_t k3[16] = {0x7fff, 0x3afb, 0x4f6f, 0xa6b, 0x35bf, 0x30bb, 0x52f, 0x2b, 0x5fd5, 0x1ad1, 0x4f45, 0xa41, 0x1595, 0x1091, 0x505, 0x1};
+  return dim == 2 ? k2[t & 15] : k3[t & 15];
+}
+
 // Packed-index offsets of all direction slots from the node at (j, k) (independent of i).
 // off[0] = 0.  Offsets of directions leaving the closure are meaningless and must be masked.
 HHG_HD void neighbour_offsets(int dim, int64_t n, int64_t j, int64_t k, int64_t* off) {
