@@ -176,6 +176,23 @@ hhg_status hhg_profile_kernel(hhg_mesh mesh, int kernel, int precision, int reps
  * hhg_fmg_solve with the same parameters), i.e. kernel launches per solve. */
 hhg_status hhg_solve_launch_count(hhg_mesh mesh, const hhg_solve_params* params, long long* n_kernels);
 
+/* Per-cell squared L2 norms of a difference on level L without allocating anything: out[T] =
+ * (a - b)^T M_{L,T} (a - b) over the micro elements of macro cell T (b may be NULL).  The paper has no
+ * counterpart: this is for callers that cannot allocate device memory when they need the local
+ * indicators -- a caller recording its own CUDA stream capture (cudaMalloc is not allowed there) or a
+ * process running under a fixed, pre-reserved device-memory budget.  With a = u_L and b = w_{L-1}
+ * it gives eta_T^2 of hhg_estimate.
+ * a, b: device, N_L doubles (mesh layout); out: device, n_cells doubles.  Work is queued on the
+ * mesh's stream; the call does not synchronise (read `out` after synchronising that stream).
+ * Scratch: a file-scope device array of 2^20 doubles (8 MiB) that every GPU which loads the library
+ * holds until the process exits; cells x chunks must fit it (HHG_ERR_ARG beyond 65535 cells).  The
+ * first call on a device looks up the array's device address (make that first call before any stream
+ * capture).  All calls share the array and every call overwrites the part it uses before reading it
+ * (nothing has to start at zero); calls that overlap on the GPU (e.g. on two streams) race on it.
+ * No cudaMalloc, cudaFree or allocating library routine is called.  The mesh's device must be
+ * current. */
+hhg_status hhg_cell_mass_norms_noalloc(hhg_mesh mesh, const double* a, const double* b, double* out);
+
 /* Debug builds (compiled with HHG_CHECK): first recorded out-of-range index of a kernel
  * (code, block x, block y, thread, index, bound, 0, 1), then cleared; all zeros otherwise. */
 hhg_status hhg_debug_check(long long* out8);

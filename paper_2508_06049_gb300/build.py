@@ -18,7 +18,7 @@ LIBDIR = os.path.join(HERE, "lib")
 BUILD = os.path.join(HERE, "_build")
 LIBNAME = "libhhg.so"
 
-CUDA_SOURCES = ["setup.cu", "kernels.cu", "kernels_mixed.cu", "capi.cu"]
+CUDA_SOURCES = ["setup.cu", "kernels.cu", "kernels_mixed.cu", "kernels_noalloc.cu", "capi.cu"]
 CXX_SOURCES = ["rg2d.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -77,6 +77,7 @@ def lib():
         "hhg_debug_check": [vp],
         "hhg_profile_kernel": [vp, i, i, i, C.POINTER(C.c_longlong), C.POINTER(d), C.POINTER(d)],
         "hhg_solve_launch_count": [vp, C.POINTER(SolveParams), C.POINTER(C.c_longlong)],
+        "hhg_cell_mass_norms_noalloc": [vp, vp, vp, vp],
         "hhg_last_error": [],
     }
     for name, args in sig.items():
@@ -196,6 +197,12 @@ class Mesh:
         _check(lib().hhg_profile_kernel(self._h, int(kernel), int(precision), int(reps), C.byref(u),
                                          C.byref(b), C.byref(f)))
         return u.value, b.value, f.value
+
+    def cell_mass_norms_noalloc(self, a, b, out):
+        """(a-b)^T M_T (a-b) per cell into the device tensor `out` without allocating (queued on the
+        mesh stream, not synchronised); a, b, out are CUDA tensors."""
+        _check(lib().hhg_cell_mass_norms_noalloc(self._h, _ptr(a), _ptr(b), _ptr(out)))
+        return out
 
     def launch_count(self, params):
         n = C.c_longlong()
