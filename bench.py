@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel-only", type=int, default=0,
                     help="set up the workload, launch the dominant kernel this many times, exit (for ncu)")
+    ap.add_argument("--kernel-id", type=int, default=0, help="with --kernel-only: 0 interior stage, 1 face stage")
     return ap.parse_args()
 
 
@@ -148,8 +149,11 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# measured binary64 FMA throughput of this machine's GB300 (probe in profiles/fp64_fma_peak.md)
+# measured binary64 FMA throughput of the GB300 (paper_2508_06049_gb300/peak_probe.cu, summarised under profiles/)
 FP64_PEAK_TFLOPS = 1.205
+# DRAM bytes (read + write) of one launch of the roofline kernel on the 384-tet cube at L = 6, from
+# one ncu capture of that kernel (summarised under profiles/); None for other workloads
+TRAFFIC_BYTES = {("cube384_l6", "fp64"): 369.5e6, ("cube384_l6", "mixed"): 166.9e6}
 
 
 # ----------------------------------------------------------------------------- arms
@@ -254,6 +258,21 @@ def run_arm(args, rank, world, su, precision):
         e2e = {"value": world * unknowns / (ms_e2e * 1e-3), "unit": "DoF/s", "ms_per_step": ms_e2e,
                "h2d_bytes_per_step": 2 * 8 * len(x), "d2h_bytes_per_step": 8 * len(x) + 8 * len(ce)}
 
+    # device time of each phase of the step, called alone (the estimate includes its D2H of eta_T)
+    phases = {}
+    for name, fn in (("solve", lambda: mesh.solve(prm, out=ud)), ("estimate", lambda: mesh.estimate(1)),
+                     ("mark", lambda: P.mark(est["eta_T"], frac))):
+        fn()
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(s)
+        for _ in range(5):
+            fn()
+        p1.record(s)
+        torch.cuda.synchronize()
+        phases[name] = p0.elapsed_time(p1) / 5
+
     # roofline of the dominant kernel: the level-L interior smoothing stage, timed with CUDA events
     # on the library's stream (same launch configuration as inside the solve graph)
     pk, pk_kind = peaks()
@@ -272,20 +291,20 @@ def run_arm(args, rank, world, su, precision):
     tfl = kflops / (ms_k * 1e-3) / 1e12
     if precision == "fp64":
         rf_obj = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                  "frac": tfl / FP64_PEAK_TFLOPS, "traffic": None,
-                  "peak_kind": "measured binary64 FMA throughput (profiles/fp64_fma_peak.md)",
+                  "frac": tfl / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES.get((args.workload, precision)),
+                  "peak_kind": "measured binary64 FMA throughput (paper_2508_06049_gb300/peak_probe.cu)",
                   "hbm_gbs": gbs, "hbm_frac": gbs / pk.get("hbm_gbs", 6800.0)}
     else:
         peak = pk.get("hbm_gbs", 6800.0)
         rf_obj = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                  "traffic": None, "peak_kind": pk_kind + " (MEASURED_PEAKS.json hbm_gbs)", "tflops": tfl}
+                  "traffic": TRAFFIC_BYTES.get((args.workload, precision)), "peak_kind": pk_kind + " (MEASURED_PEAKS.json hbm_gbs)", "tflops": tfl}
     rf_obj.update({"kernel": "k_smooth_interior (level L, colour 0)", "ms_per_launch": ms_k,
                    "units_per_launch": units, "algorithmic_bytes_per_launch": kbytes,
                    "algorithmic_flops_per_launch": kflops})
     launches = mesh.launch_count(prm) + 7   # solve graph + estimator kernels (j = 1)
 
     return dict(value=value, ms=ms, wall=wall, clocks=clocks, e2e=e2e, roofline=rf_obj, err=err,
-                unknowns=unknowns, launches=launches, eta=est["eta_j"],
+                unknowns=unknowns, launches=launches, eta=est["eta_j"], phases=phases,
                 params={"nu": prm.nu, "pre": prm.pre, "post": prm.post, "n_extra": prm.n_extra,
                         "precision": prm.precision, "storage": prm.storage, "ir_steps": prm.ir_steps,
                         "ir_vcycles": prm.ir_vcycles})
@@ -351,10 +370,11 @@ def kernel_only(args):
     mesh = P.Mesh(co, ce, L, stream=s)
     x = mesh.level_coords(L)
     mesh.set_data(np.ascontiguousarray(f(x)), np.ascontiguousarray(g(x)))
-    units, b, fl = mesh.profile_kernel(0, 0 if args.precision == "fp64" else 1, args.kernel_only)
+    prec = 0 if args.precision in ("fp64", "both") else 1
+    units, b, fl = mesh.profile_kernel(args.kernel_id, prec, args.kernel_only)
     torch.cuda.synchronize()
-    print("launched %d x k_smooth_interior (%d nodes, %.0f bytes, %.0f flops per launch)"
-          % (args.kernel_only, units, b, fl))
+    print("launched %d x kernel %d (%d nodes, %.0f bytes, %.0f flops per launch)"
+          % (args.kernel_only, args.kernel_id, units, b, fl))
 
 
 def main():
@@ -396,7 +416,7 @@ def main():
         def arm_summary(r):
             return {"value": r["value"], "ms_per_step": r["ms"], "l2_error_vs_exact": r["err"], "eta_1": r["eta"],
                     "params": r["params"], "roofline": r["roofline"], "gpu_launches_per_step": r["launches"],
-                    "clocks": r["clocks"]}
+                    "clocks": r["clocks"], "phases_ms": r["phases"]}
         line = {"metric": "FMG DoF/s (FMG + estimator + marking per step, equal error)", "value": head["value"],
                 "unit": "DoF/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -16,6 +16,7 @@ void launch_fmg_prolong_g(hhg_mesh_s* m, int l, const double* g, double* w, cuda
 void launch_restrict_rhs_chain(hhg_mesh_s* m, cudaStream_t s);
 hhg_status read_check(long long* out);
 hhg_status preload_kernels();
+void launch_profile_face(hhg_mesh_s* m, int reps, cudaStream_t s, long long* units);
 hhg_status mixed_profile_interior(hhg_mesh_s* m, int reps, cudaStream_t s, long long* units, double* bytes,
                                   double* flops);
 hhg_status mixed_prepare(hhg_mesh_s* m, int storage);
@@ -105,7 +106,7 @@ void enqueue_vcycle(hhg_mesh_s* m, int l, const double* rhs, const hhg_solve_par
     return;
   }
   for (int q = 0; q < p.pre; ++q) launch_sweep(m, l, rhs, s, false);
-  launch_residual(m, l, rhs, s);
+  launch_residual_after(m, l, rhs, s, p.pre > 0);
   launch_restrict(m, l, m->lv[l].tmp, m->lv[l - 1].rc, s);
   cudaMemsetAsync(m->lv[l - 1].u, 0, sizeof(double) * (size_t)m->lv[l - 1].N, s);
   enqueue_vcycle(m, l - 1, m->lv[l - 1].rc, p, s);
@@ -561,12 +562,17 @@ hhg_status hhg_adjoint_l2(hhg_mesh m, const hhg_solve_params* params, const unsi
 hhg_status hhg_profile_kernel(hhg_mesh m, int kernel, int precision, int reps, long long* units, double* bytes,
                               double* flops) {
   REQUIRE(m && units && bytes && flops, HHG_ERR_ARG, "NULL argument");
-  REQUIRE(kernel == 0, HHG_ERR_ARG, "kernel must be 0");
+  REQUIRE(kernel == 0 || kernel == 1, HHG_ERR_ARG, "kernel must be 0 or 1");
   REQUIRE(precision == 0 || precision == 1, HHG_ERR_ARG, "precision must be 0 or 1");
   REQUIRE(reps >= 0 && reps <= 100000, HHG_ERR_ARG, "reps in [0, 100000]");
   DeviceGuard g(m->device);
   ENTER(m);
-  if (precision == 1) {
+  if (kernel == 1) {
+    REQUIRE(precision == 0, HHG_ERR_ARG, "the face-stage probe is binary64");
+    launch_profile_face(m, reps, m->stream, units);
+    *bytes = 0;
+    *flops = 0;
+  } else if (precision == 1) {
     hhg_status st = mixed_prepare(m, m->mixed_alloc ? m->last_storage : 1);
     if (st != HHG_OK) return st;
     st = mixed_profile_interior(m, reps, m->stream, units, bytes, flops);
@@ -617,6 +623,8 @@ int hhg_lattice_selfcheck(int dim, int n) {
           bool inside = a >= 0 && b >= 0 && c >= 0 && a + b + c <= n;
           if (inside != (bool)(vm >> d & 1)) ++bad;
           if (inside && packed_index(dim, n, a, b, c) != g + off[d]) ++bad;
+          PlaneBasis pb = plane_basis(dim, n, k);
+          if (inside && d > 0 && dir_offset(dim, d, pb.m, j, pb.Tm, pb.Tm1) != off[d]) ++bad;
         }
       }
   for (int64_t g = 0; g < Nt; ++g)

@@ -59,10 +59,21 @@ template <typename R, typename S> struct CVec {
 };
 
 // ---- per-level lattice context ----
+// Every kernel is launched with programmatic stream serialisation (hhg_launch): the next kernel in a
+// stream or graph may be scheduled while the current one drains.  Each kernel therefore starts by
+// waiting (griddepcontrol.wait, a hardware wait, before any global memory access) until the
+// preceding grid has completed and its writes are visible, and then allows its own successor to be
+// scheduled.  Launched without the attribute, both instructions have no effect.
+__device__ __forceinline__ void grid_dependency_sync() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 struct LevelCtx {
   int n;             // 2^l
   int64_t Nt;        // closure nodes per macro cell
   const int32_t* ijk;  // decode table: packed index -> i | j<<10 | k<<20
+  const uint16_t* nzs;  // [cell][type]: stiffness slots with a nonzero entry (nullptr: all)
 };
 
 __device__ __forceinline__ void decode(int32_t c, int& i, int& j, int& k) {

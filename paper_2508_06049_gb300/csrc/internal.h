@@ -34,15 +34,24 @@ struct Prims {
   int* d_loc = nullptr;
   unsigned char* d_dir = nullptr;
   int max_copies = 0;
+  // per primitive: 1 / (assembled diagonal of its interior nodes) at unit level scale (0 if Dirichlet)
+  double* d_pinv = nullptr;
+  float* d_pinvf = nullptr;
 };
 
 struct LevelData {
   int l = 0, n = 1;
   int64_t Nt = 0, N = 0;
   int32_t* d_ijk = nullptr;
-  // interior colour lists: for group g and colour c, entries [icol_off[g][c], icol_off[g][c+1])
+  // interior colour lists: for group g and colour c, entries [icol_off[g][c], icol_off[g][c+1]) of
+  // (packed local index, j | k << 16)
   std::vector<std::vector<int64_t>> icol_off;
-  int32_t* d_icol = nullptr;
+  int2* d_icol = nullptr;
+  // boundary-type closure nodes (type != 0), sorted by type: (packed local index, i | j << 10 | k << 20)
+  int2* d_bnd = nullptr;
+  int64_t nbnd = 0;
+  double* d_invl = nullptr;  // per cell: 1 / (level-l interior diagonal)
+  float* d_invlf = nullptr;
   // face colour lists (3D): colour c entries [fcol_off[c], fcol_off[c+1]) of a | b << 16
   int64_t fcol_off[4] = {0, 0, 0, 0};
   int32_t* d_fcol = nullptr;
@@ -85,7 +94,10 @@ struct hhg_mesh_s {
   float* dM32 = nullptr;
   double* d_inv0 = nullptr;       // 1 / interior diagonal per cell (unit level scale, with k_T)
   float* d_inv0f = nullptr;
+  double* d_tnorm = nullptr;      // per cell: interior stencil divided by its diagonal [cell][16]
+  float* d_tnormf = nullptr;
   uint16_t* d_dirmask = nullptr;  // per cell: bit t set if nodes of boundary type t are Dirichlet
+  uint16_t* d_nzs = nullptr;      // per cell and boundary type: stiffness slots with a nonzero entry
   std::vector<uint16_t> dirmask;
   std::vector<hhg::Group> groups;
   std::vector<int> group_of_cell;
@@ -129,6 +141,8 @@ void launch_build_rhs(hhg_mesh_s* m, int l, cudaStream_t s);
 void launch_init_coarse(hhg_mesh_s* m, cudaStream_t s);
 void launch_sweep(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s, bool reverse);
 void launch_residual(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s);
+// the same directly after a Gauss-Seidel sweep (last interior colour has zero residual)
+void launch_residual_after(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s, bool after_sweep);
 void launch_restrict(hhg_mesh_s* m, int l, const double* fine, double* coarse, cudaStream_t s);
 void launch_prolong_add(hhg_mesh_s* m, int l, cudaStream_t s);
 void launch_fmg_prolong(hhg_mesh_s* m, int l, cudaStream_t s);

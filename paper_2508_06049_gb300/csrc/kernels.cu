@@ -11,6 +11,7 @@ namespace hhg {
 // One block per cell: deterministic shared-memory tree sum of the cell's node contributions.
 __global__ void __launch_bounds__(256) k_cell_sum(int64_t Nt, double scale, const double* __restrict__ contrib,
                                                   double* __restrict__ out) {
+  grid_dependency_sync();
   __shared__ double sh[256];
   int T = blockIdx.x;
   const double* c = contrib + (int64_t)T * Nt;
@@ -26,6 +27,7 @@ __global__ void __launch_bounds__(256) k_cell_sum(int64_t Nt, double scale, cons
 }
 
 __global__ void k_finite(const double* __restrict__ v, int64_t n, int* __restrict__ flag) {
+  grid_dependency_sync();
   int bad = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     if (!isfinite(v[i])) bad = 1;
@@ -36,13 +38,13 @@ __global__ void k_finite(const double* __restrict__ v, int64_t n, int* __restric
 
 static LevelCtx ctx(const hhg_mesh_s* m, int l) {
   const LevelData& Lv = m->lv[l];
-  return LevelCtx{Lv.n, Lv.Nt, Lv.d_ijk};
+  return LevelCtx{Lv.n, Lv.Nt, Lv.d_ijk, m->d_nzs};
 }
 
-#define DISPATCH_DIM(m, KER, ...)          \
-  do {                                     \
-    if ((m)->dim == 2) KER<2> __VA_ARGS__; \
-    else KER<3> __VA_ARGS__;               \
+#define DISPATCH_DIM(m, KER, ...)                 \
+  do {                                            \
+    if ((m)->dim == 2) hhg_launch(KER<2>, __VA_ARGS__); \
+    else hhg_launch(KER<3>, __VA_ARGS__);               \
   } while (0)
 
 void launch_build_rhs(hhg_mesh_s* m, int l, cudaStream_t s) {
@@ -50,8 +52,8 @@ void launch_build_rhs(hhg_mesh_s* m, int l, cudaStream_t s) {
   dim3 grid(blocks_for(Lv.Nt), m->nc);
   double ms = mass_scale(m->dim, Lv.n);
   const LevelData& LL = m->lv[m->L];
-  DISPATCH_DIM(m, k_build_rhs, <<<grid, kBlock, 0, s>>>(ctx(m, l), LL.n, LL.Nt, m->L - l, m->fL, m->dM, ms,
-                                                       m->d_dirmask, Lv.b));
+  DISPATCH_DIM(m, k_build_rhs, grid, kBlock, 0, s, ctx(m, l), LL.n, LL.Nt, m->L - l, m->fL, m->dM, ms,
+                                                       m->d_dirmask, Lv.b);
 }
 
 void launch_build_rhs_restricted(hhg_mesh_s* m, cudaStream_t s);
@@ -60,7 +62,7 @@ void launch_init_coarse_g(hhg_mesh_s* m, const double* g, cudaStream_t s) {
   const LevelData& Lv = m->lv[0];
   const LevelData& LL = m->lv[m->L];
   dim3 grid(blocks_for(Lv.Nt), m->nc);
-  DISPATCH_DIM(m, k_init_coarse, <<<grid, kBlock, 0, s>>>(ctx(m, 0), LL.n, LL.Nt, m->L, g, m->d_dirmask, Lv.u));
+  DISPATCH_DIM(m, k_init_coarse, grid, kBlock, 0, s, ctx(m, 0), LL.n, LL.Nt, m->L, g, m->d_dirmask, Lv.u);
 }
 
 void launch_init_coarse(hhg_mesh_s* m, cudaStream_t s) { launch_init_coarse_g(m, m->gL, s); }
@@ -72,9 +74,9 @@ static void interior_stage(hhg_mesh_s* m, int l, int gi, int colour, double* u, 
   int64_t a = Lv.icol_off[gi][colour], b = Lv.icol_off[gi][colour + 1];
   if (b <= a || G.cells.empty()) return;
   dim3 grid(blocks_for(b - a), (unsigned)G.cells.size());
-  k_smooth_interior<DIM, PM, double, double, double><<<grid, kBlock, 0, s>>>(
-      G.d_cells, Lv.d_icol + a, b - a, ctx(m, l), m->dS, stiff_scale(DIM, Lv.n), m->d_inv0,
-      1.0 / stiff_scale(DIM, Lv.n), Vec<double, double>{u, nullptr}, CVec<double, double>{rhs, nullptr});
+  hhg_launch(k_smooth_interior<DIM, PM, double, double, double>, grid, kBlock, 0, s, 
+      G.d_cells, Lv.d_icol + a, b - a, ctx(m, l), m->d_tnorm, Lv.d_invl, Vec<double, double>{u, nullptr},
+      CVec<double, double>{rhs, nullptr});
 }
 
 // compile-time stencil patterns: the full stencil and the Kuhn / right-isosceles patterns
@@ -103,16 +105,17 @@ static void iface_stage(hhg_mesh_s* m, int l, const Prims& P, int nverts, int pa
                         cudaStream_t s) {
   if (P.count == 0 || (cnt_rim <= 0 && cnt_inner <= 0)) return;
   const LevelData& Lv = m->lv[l];
-  int64_t nthreads = (int64_t)P.count * (cnt_rim + cnt_inner);
   double* du = Lv.tmp;  // residual scratch is free during a sweep (sized N_l >= the rim nodes)
   double ss = stiff_scale(DIM, Lv.n);
-  k_iface_stage<DIM, double, double, double><<<blocks_for(nthreads), kBlock, 0, s>>>(
-      P.count, nverts, parity, cnt_rim, cnt_inner, rim_list, inner_list, P.d_ptr, P.d_cell, P.d_loc, P.d_dir,
-      ctx(m, l), m->dS, ss, Vec<double, double>{u, nullptr}, CVec<double, double>{rhs, nullptr}, du);
-  if (cnt_rim > 0)
-    k_iface_apply<DIM, double, double><<<blocks_for((int64_t)P.count * cnt_rim), kBlock, 0, s>>>(
-        P.count, nverts, parity, cnt_rim, rim_list, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l),
-        Vec<double, double>{u, nullptr}, du);
+  // Face stages with many nodes are DFMA-bound in binary64: one lane per node and only the nonzero
+  // stencil terms.  Smaller stages are latency-bound: copies spread over lanes, all loads together.
+  int64_t nodes = (int64_t)P.count * (cnt_rim + cnt_inner);
+  bool sparse = nverts == 3 && nodes >= kSparseFaceNodes;
+  int lanes = sparse ? 1 : iface_lanes(P.max_copies);
+  launch_iface<DIM, double, double, double>(lanes, sparse, P.count, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, nverts, parity,
+                                            cnt_rim, cnt_inner, rim_list, inner_list, ctx(m, l), m->dS, ss, P.d_pinv,
+                                            Vec<double, double>{u, nullptr}, CVec<double, double>{rhs, nullptr}, du,
+                                            s);
 }
 
 template <int DIM>
@@ -128,9 +131,9 @@ static void sweep_impl(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s, 
     if (st == 0) {
       const Prims& P = m->verts;
       if (P.count)
-        k_smooth_vertex<DIM, double, double, double><<<blocks_for((int64_t)P.count * 32), kBlock, 0, s>>>(
-            P.count, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l), m->dS, ss, Vec<double, double>{u, nullptr},
-            CVec<double, double>{rhs, nullptr});
+        hhg_launch(k_smooth_vertex<DIM, double, double, double>, blocks_for((int64_t)P.count * 32), kBlock, 0, s, 
+            P.count, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l), m->dS, ss, P.d_pinv, 1.0 / ss,
+            Vec<double, double>{u, nullptr}, CVec<double, double>{rhs, nullptr});
     } else if (st <= 2) {
       // stage 1: even local index (no coupling inside the stage); stage 2: odd, t = 1 and n-1 are rim
       int parity = (st == 2);
@@ -156,28 +159,36 @@ void launch_sweep(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s, bool 
 }
 
 template <int DIM, int PM>
-static void residual_group(hhg_mesh_s* m, int l, int gi, const double* rhs, cudaStream_t s) {
+static void residual_group(hhg_mesh_s* m, int l, int gi, const double* rhs, cudaStream_t s, bool after_sweep) {
   const LevelData& Lv = m->lv[l];
   const Group& G = m->groups[gi];
-  dim3 grid(blocks_for(Lv.Nt), (unsigned)G.cells.size());
-  k_residual<DIM, PM, double, double, double, double><<<grid, kBlock, 0, s>>>(
+  ResidualSegments rs = residual_segments(Lv, G, gi, after_sweep);
+  dim3 grid(rs.bcomp + rs.bzero + blocks_for(Lv.nbnd), (unsigned)G.cells.size());
+  hhg_launch(k_residual_list<DIM, PM, double, double, double, double>, grid, kBlock, 0, s, 
       G.d_cells, ctx(m, l), m->dS, m->d_dirmask, stiff_scale(DIM, Lv.n), CVec<double, double>{Lv.u, nullptr},
-      CVec<double, double>{rhs, nullptr}, Lv.tmp);
+      CVec<double, double>{rhs, nullptr}, Lv.tmp, rs.ilist, rs.ncomp, rs.nzero, Lv.d_bnd, Lv.nbnd, rs.bcomp,
+      rs.bzero);
 }
 
+void launch_residual_after(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s, bool after_sweep);
+
 void launch_residual(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s) {
+  launch_residual_after(m, l, rhs, s, false);
+}
+
+void launch_residual_after(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s, bool after_sweep) {
   for (size_t gi = 0; gi < m->groups.size(); ++gi) {
     int pm = m->groups[gi].pmask;
     if (m->dim == 2) {
       switch (pm) {
-        case 0x3: residual_group<2, 0x3>(m, l, (int)gi, rhs, s); break;
-        case 0x5: residual_group<2, 0x5>(m, l, (int)gi, rhs, s); break;
-        case 0x6: residual_group<2, 0x6>(m, l, (int)gi, rhs, s); break;
-        default: residual_group<2, 0x7>(m, l, (int)gi, rhs, s); break;
+        case 0x3: residual_group<2, 0x3>(m, l, (int)gi, rhs, s, after_sweep); break;
+        case 0x5: residual_group<2, 0x5>(m, l, (int)gi, rhs, s, after_sweep); break;
+        case 0x6: residual_group<2, 0x6>(m, l, (int)gi, rhs, s, after_sweep); break;
+        default: residual_group<2, 0x7>(m, l, (int)gi, rhs, s, after_sweep); break;
       }
     } else {
-      if (pm == 0x29) residual_group<3, 0x29>(m, l, (int)gi, rhs, s);
-      else residual_group<3, 0x7f>(m, l, (int)gi, rhs, s);
+      if (pm == 0x29) residual_group<3, 0x29>(m, l, (int)gi, rhs, s, after_sweep);
+      else residual_group<3, 0x7f>(m, l, (int)gi, rhs, s, after_sweep);
     }
   }
 }
@@ -186,9 +197,9 @@ void launch_restrict(hhg_mesh_s* m, int l, const double* fine, double* coarse, c
   const LevelData& C = m->lv[l - 1];
   dim3 grid(blocks_for(C.Nt), m->nc);
   if (m->dim == 2)
-    k_restrict<2, double, double, double><<<grid, kBlock, 0, s>>>(ctx(m, l), ctx(m, l - 1), m->d_dirmask, fine, coarse);
+    hhg_launch(k_restrict<2, double, double, double>, grid, kBlock, 0, s, ctx(m, l), ctx(m, l - 1), m->d_dirmask, fine, coarse);
   else
-    k_restrict<3, double, double, double><<<grid, kBlock, 0, s>>>(ctx(m, l), ctx(m, l - 1), m->d_dirmask, fine, coarse);
+    hhg_launch(k_restrict<3, double, double, double>, grid, kBlock, 0, s, ctx(m, l), ctx(m, l - 1), m->d_dirmask, fine, coarse);
 }
 
 void launch_prolong_add(hhg_mesh_s* m, int l, cudaStream_t s) {
@@ -197,17 +208,17 @@ void launch_prolong_add(hhg_mesh_s* m, int l, cudaStream_t s) {
   CVec<double, double> uc{m->lv[l - 1].u, nullptr};
   Vec<double, double> uf{F.u, nullptr};
   if (m->dim == 2)
-    k_prolong_add<2, double><<<grid, kBlock, 0, s>>>(ctx(m, l), ctx(m, l - 1), m->d_dirmask, uc, uf);
+    hhg_launch(k_prolong_add<2, double, double, double>, grid, kBlock, 0, s, ctx(m, l), ctx(m, l - 1), m->d_dirmask, uc, uf);
   else
-    k_prolong_add<3, double><<<grid, kBlock, 0, s>>>(ctx(m, l), ctx(m, l - 1), m->d_dirmask, uc, uf);
+    hhg_launch(k_prolong_add<3, double, double, double>, grid, kBlock, 0, s, ctx(m, l), ctx(m, l - 1), m->d_dirmask, uc, uf);
 }
 
 void launch_fmg_prolong_g(hhg_mesh_s* m, int l, const double* g, double* w, cudaStream_t s) {
   const LevelData& F = m->lv[l + 1];
   const LevelData& LL = m->lv[m->L];
   dim3 grid(blocks_for(F.Nt), m->nc);
-  DISPATCH_DIM(m, k_fmg_prolong, <<<grid, kBlock, 0, s>>>(ctx(m, l + 1), ctx(m, l), LL.n, LL.Nt, m->L - l - 1, g,
-                                                         m->d_dirmask, m->lv[l].u, F.u, w));
+  DISPATCH_DIM(m, k_fmg_prolong, grid, kBlock, 0, s, ctx(m, l + 1), ctx(m, l), LL.n, LL.Nt, m->L - l - 1, g,
+                                                         m->d_dirmask, m->lv[l].u, F.u, w);
 }
 
 void launch_fmg_prolong(hhg_mesh_s* m, int l, cudaStream_t s) { launch_fmg_prolong_g(m, l, m->gL, m->lv[l].w, s); }
@@ -215,7 +226,7 @@ void launch_fmg_prolong(hhg_mesh_s* m, int l, cudaStream_t s) { launch_fmg_prolo
 void launch_prolong(hhg_mesh_s* m, int l, const double* coarse, double* fine, cudaStream_t s) {
   const LevelData& F = m->lv[l];
   dim3 grid(blocks_for(F.Nt), m->nc);
-  DISPATCH_DIM(m, k_prolong, <<<grid, kBlock, 0, s>>>(ctx(m, l), ctx(m, l - 1), coarse, fine));
+  DISPATCH_DIM(m, k_prolong, grid, kBlock, 0, s, ctx(m, l), ctx(m, l - 1), coarse, fine);
 }
 
 void launch_coarse_solve(hhg_mesh_s* m, const double* rhs, cudaStream_t s) {
@@ -233,12 +244,12 @@ void launch_coarse_solve(hhg_mesh_s* m, const double* rhs, cudaStream_t s) {
     }
   }
   const Prims& P = m->verts;
-  DISPATCH_DIM(m, k_coarse, <<<1, 1024, smem, s>>>(m->n0f, m->d_cf_vert, P.d_ptr, P.d_cell, P.d_loc, ctx(m, 0), m->dS,
-                                                  rhs, m->lv[0].u, m->d_Ainv));
+  DISPATCH_DIM(m, k_coarse, 1, 1024, smem, s, m->n0f, m->d_cf_vert, P.d_ptr, P.d_cell, P.d_loc, ctx(m, 0), m->dS,
+                                                  rhs, m->lv[0].u, m->d_Ainv);
 }
 
 void launch_finite_check(hhg_mesh_s* m, const double* v, int64_t n, cudaStream_t s) {
-  k_finite<<<304, kBlock, 0, s>>>(v, n, m->d_flag);
+  hhg_launch(k_finite, 304, kBlock, 0, s, v, n, m->d_flag);
 }
 
 static void cell_form(hhg_mesh_s* m, bool diff, const double* tab, double scale, const double* a, const double* b,
@@ -247,13 +258,13 @@ static void cell_form(hhg_mesh_s* m, bool diff, const double* tab, double scale,
   double* contrib = m->d_part;  // N_L doubles of scratch
   dim3 grid(blocks_for(Lv.Nt), m->nc);
   if (diff) {
-    if (m->dim == 2) k_node_form<2, true><<<grid, kBlock, 0, s>>>(ctx(m, m->L), tab, a, b, contrib);
-    else k_node_form<3, true><<<grid, kBlock, 0, s>>>(ctx(m, m->L), tab, a, b, contrib);
+    if (m->dim == 2) hhg_launch(k_node_form<2, true>, grid, kBlock, 0, s, ctx(m, m->L), tab, a, b, contrib);
+    else hhg_launch(k_node_form<3, true>, grid, kBlock, 0, s, ctx(m, m->L), tab, a, b, contrib);
   } else {
-    if (m->dim == 2) k_node_form<2, false><<<grid, kBlock, 0, s>>>(ctx(m, m->L), tab, a, b, contrib);
-    else k_node_form<3, false><<<grid, kBlock, 0, s>>>(ctx(m, m->L), tab, a, b, contrib);
+    if (m->dim == 2) hhg_launch(k_node_form<2, false>, grid, kBlock, 0, s, ctx(m, m->L), tab, a, b, contrib);
+    else hhg_launch(k_node_form<3, false>, grid, kBlock, 0, s, ctx(m, m->L), tab, a, b, contrib);
   }
-  k_cell_sum<<<m->nc, 256, 0, s>>>(Lv.Nt, scale, contrib, out);
+  hhg_launch(k_cell_sum, m->nc, 256, 0, s, Lv.Nt, scale, contrib, out);
 }
 
 void launch_mass_norm_sq(hhg_mesh_s* m, const double* a, const double* b, double* out, cudaStream_t s) {
@@ -269,16 +280,16 @@ void launch_sum_interfaces(hhg_mesh_s* m, int l, double* v, cudaStream_t s) {
   int n = Lv.n;
   const Prims& PV = m->verts;
   if (PV.count)
-    DISPATCH_DIM(m, k_sum_prims, <<<blocks_for(PV.count), kBlock, 0, s>>>(PV.count, 1, 1, nullptr, PV.d_ptr, PV.d_cell,
-                                                                          PV.d_loc, ctx(m, l), v));
+    DISPATCH_DIM(m, k_sum_prims, blocks_for(PV.count), kBlock, 0, s, PV.count, 1, 1, nullptr, PV.d_ptr, PV.d_cell,
+                                                                          PV.d_loc, ctx(m, l), v);
   const Prims& PE = m->edges;
   if (PE.count && n >= 2)
-    DISPATCH_DIM(m, k_sum_prims, <<<blocks_for((int64_t)PE.count * (n - 1)), kBlock, 0, s>>>(
-                                     PE.count, 2, n - 1, nullptr, PE.d_ptr, PE.d_cell, PE.d_loc, ctx(m, l), v));
+    DISPATCH_DIM(m, k_sum_prims, blocks_for((int64_t)PE.count * (n - 1)), kBlock, 0, s, 
+                                     PE.count, 2, n - 1, nullptr, PE.d_ptr, PE.d_cell, PE.d_loc, ctx(m, l), v);
   const Prims& PF = m->faces;
   int64_t nf = Lv.fcol_off[3];
   if (m->dim == 3 && PF.count && nf > 0)
-    k_sum_prims<3><<<blocks_for((int64_t)PF.count * nf), kBlock, 0, s>>>(PF.count, 3, (int)nf, Lv.d_fcol, PF.d_ptr,
+    hhg_launch(k_sum_prims<3>, blocks_for((int64_t)PF.count * nf), kBlock, 0, s, PF.count, 3, (int)nf, Lv.d_fcol, PF.d_ptr,
                                                                          PF.d_cell, PF.d_loc, ctx(m, l), v);
 }
 
@@ -287,14 +298,14 @@ void launch_apply_op(hhg_mesh_s* m, int l, int op, const double* in, double* out
   dim3 grid(blocks_for(Lv.Nt), m->nc);
   const double* tab = op == 0 ? m->dS : m->dM;
   double sc = op == 0 ? stiff_scale(m->dim, Lv.n) : mass_scale(m->dim, Lv.n);
-  DISPATCH_DIM(m, k_apply_partial, <<<grid, kBlock, 0, s>>>(ctx(m, l), tab, sc, in, out, nullptr, m->d_dirmask));
+  DISPATCH_DIM(m, k_apply_partial, grid, kBlock, 0, s, ctx(m, l), tab, sc, in, out, nullptr, m->d_dirmask);
 }
 
 void launch_adjoint_rhs(hhg_mesh_s* m, const unsigned char* d_inS, const double* u, double* out, cudaStream_t s) {
   const LevelData& Lv = m->lv[m->L];
   dim3 grid(blocks_for(Lv.Nt), m->nc);
-  DISPATCH_DIM(m, k_apply_partial, <<<grid, kBlock, 0, s>>>(ctx(m, m->L), m->dM, 2.0 * mass_scale(m->dim, Lv.n), u,
-                                                           out, d_inS, m->d_dirmask));
+  DISPATCH_DIM(m, k_apply_partial, grid, kBlock, 0, s, ctx(m, m->L), m->dM, 2.0 * mass_scale(m->dim, Lv.n), u,
+                                                           out, d_inS, m->d_dirmask);
 }
 
 // adjoint FMG right-hand sides on the coarser levels: b_{l-1} = P^T b_l
@@ -304,8 +315,19 @@ void launch_restrict_rhs_chain(hhg_mesh_s* m, cudaStream_t s) {
 
 // Algorithmic model of one interior-colour launch on level L (group 0, colour 0): every closure
 // value u of the group's cells is read once (the neighbours are the other colours), b is read and u
-// written for the updated nodes; flops = 2 (1 + 2 p) + 3 per updated node (p nonzero coupling pairs;
-// FMA = 2 flops, plus the residual subtraction, scaling and the diagonal division).
+// written for the updated nodes; flops = 4 p + 1 per updated node (p coupled direction pairs: one FMA
+// per neighbour, FMA = 2 flops, plus b_i / a_ii).
+// kernel 1: the level-L face stage of colour 0 (3D), timed only.
+void launch_profile_face(hhg_mesh_s* m, int reps, cudaStream_t s, long long* units) {
+  const int L = m->L;
+  LevelData& Lv = m->lv[L];
+  *units = (long long)m->faces.count * (Lv.fcol_off[1] - Lv.fcol_off[0]);
+  if (m->dim != 3) return;
+  for (int r = 0; r < reps; ++r)
+    iface_stage<3>(m, L, m->faces, 3, 0, (int)(Lv.frim_off[1] - Lv.frim_off[0]), (int)(Lv.fin_off[1] - Lv.fin_off[0]),
+                   Lv.d_frim, Lv.d_fin, Lv.u, Lv.b, s);
+}
+
 void launch_profile_interior(hhg_mesh_s* m, int precision, int reps, cudaStream_t s, long long* units,
                              double* bytes, double* flops) {
   const int L = m->L;
@@ -317,7 +339,7 @@ void launch_profile_interior(hhg_mesh_s* m, int precision, int reps, cudaStream_
   double sval = precision == 0 ? 8.0 : 4.0;
   *units = nodes;
   *bytes = sval * ((double)Lv.Nt * G.cells.size() + 2.0 * nodes);
-  *flops = (2.0 * (1 + 2 * p) + 3.0) * nodes;
+  *flops = (4.0 * p + 1.0) * nodes;
   if (precision != 0) return;  // the binary32 variant is launched by the mixed-path module
   for (int r = 0; r < reps; ++r) {
     if (m->dim == 2) interior_stage_dispatch<2>(m, L, 0, 0, Lv.u, Lv.b, s);

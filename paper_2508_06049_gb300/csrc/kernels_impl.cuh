@@ -5,6 +5,8 @@
 // interface row is the sum over copies (the additive interface collection of Sec. 4.4).
 #pragma once
 
+#include <utility>
+
 #include "device_common.cuh"
 
 namespace hhg {
@@ -18,6 +20,24 @@ inline double mass_scale(int d, int n) {
   return d == 3 ? s / (double)n : s;
 }
 inline unsigned blocks_for(int64_t n, int b = kBlock) { return (unsigned)((n + b - 1) / b); }
+
+// Launch on stream s with programmatic stream serialisation allowed (see grid_dependency_sync).
+// Launch errors surface through cudaGetLastError / the stream, as with <<< >>>.
+template <typename... KArgs, typename... Args>
+inline void hhg_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 __device__ __forceinline__ void local_vertex_vec(int a, int& x, int& y, int& z) {
   x = (a == 1);
@@ -43,27 +63,42 @@ __device__ __forceinline__ void prim_position(int loc, int nverts, int n, int s,
   }
 }
 
-// partial residual of one cell copy at node (i,j,k): rhs - scale * sum_d S[t][d] u[g + off[d]]
-template <int DIM, typename R, typename U, typename B>
-__device__ __forceinline__ R partial_residual(const R* __restrict__ S, int T, int n, int64_t Nt, int i, int j, int k,
-                                              R sscale, const CVec<R, U>& u, const CVec<R, B>& rhs, R& diag,
-                                              int64_t& g) {
+// Stencil terms of one cell copy of an interface node (i,j,k): acc += sum_d S[t][d] u[g + off_d] over
+// the slots whose neighbour lies in the closure and whose entry is nonzero, bsum += rhs[g]; returns
+// g.  SPARSE: a loop over the set bits of that mask, so a warp whose lanes share the mask (nodes of
+// one primitive in one cell) issues only the nonzero terms (fewer binary64 instructions where the
+// stage is DFMA-bound, but one memory round trip per term).  Dense: all slots unrolled, loads issued
+// together (for latency-bound stages).
+template <int DIM, bool SPARSE, typename R, typename U, typename B>
+__device__ __forceinline__ int64_t copy_terms(const R* __restrict__ S, const uint16_t* __restrict__ nzs, int T, int n,
+                                              int64_t Nt, int i, int j, int k, const CVec<R, U>& u,
+                                              const CVec<R, B>& rhs, R& acc, R& bsum) {
   int t = boundary_type(DIM, n, i, j, k);
   int64_t p = packed_index(DIM, n, i, j, k);
-  g = (int64_t)T * Nt + p;
-  diag = (R)1;
-  if (HHG_OOB(p, Nt, 31)) return (R)0;
-  int64_t off[15];
-  neighbour_offsets(DIM, n, j, k, off);
-  uint32_t vm = valid_dirs_tab(DIM, t);
-  mask_offsets(DIM, vm, off);
+  int64_t g = (int64_t)T * Nt + p;
+  if (HHG_OOB(p, Nt, 31)) return g;
+  uint32_t vm = valid_dirs_tab(DIM, t) & nzs[T * kMaxTypes + t];
   const R* s = S + (size_t)T * kStencilStride + t * kMaxDirs;
-  R acc = 0;
+  R a = s[0] * u.get(g);
+  if (SPARSE) {
+    PlaneBasis pb = plane_basis(DIM, n, k);
+    for (uint32_t mm = vm & ~1u; mm; mm &= mm - 1) {
+      int d = __ffs(mm) - 1;
+      int64_t o = dir_offset(DIM, d, pb.m, j, pb.Tm, pb.Tm1);
+      if (HHG_OOB(p + o, Nt, 32)) continue;
+      a += s[d] * u.get(g + o);
+    }
+  } else {
+    int64_t off[15];
+    neighbour_offsets(DIM, n, j, k, off);
+    mask_offsets(DIM, vm, off);
 #pragma unroll
-  for (int d = 0; d < ndirs<DIM>(); ++d)
-    if ((vm >> d & 1) && !HHG_OOB(p + off[d], Nt, 32)) acc += s[d] * u.get(g + off[d]);
-  diag = sscale * s[0];
-  return rhs.get(g) - sscale * acc;
+    for (int d = 1; d < ndirs<DIM>(); ++d)
+      if ((vm >> d & 1) && !HHG_OOB(p + off[d], Nt, 32)) a += s[d] * u.get(g + off[d]);
+  }
+  acc += a;
+  bsum += rhs.get(g);
+  return g;
 }
 
 // ---------------------------------------------------------------- right-hand sides (row 2)
@@ -73,6 +108,7 @@ template <int DIM>
 __global__ void k_build_rhs(LevelCtx lc, int nL, int64_t NtL, int shift, const double* __restrict__ fL,
                             const double* __restrict__ Mst, double mscale, const uint16_t* __restrict__ dirmask,
                             double* __restrict__ b) {
+  grid_dependency_sync();
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (loc >= lc.Nt) return;
   int T = blockIdx.y;
@@ -103,6 +139,7 @@ __global__ void k_build_rhs(LevelCtx lc, int nL, int64_t NtL, int shift, const d
 template <int DIM>
 __global__ void k_init_coarse(LevelCtx lc, int nL, int64_t NtL, int shift, const double* __restrict__ gL,
                               const uint16_t* __restrict__ dirmask, double* __restrict__ u) {
+  grid_dependency_sync();
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (loc >= lc.Nt) return;
   int T = blockIdx.y;
@@ -120,39 +157,40 @@ __global__ void k_init_coarse(LevelCtx lc, int nL, int64_t NtL, int shift, const
 
 // ---------------------------------------------------------------- smoother stages (row 3)
 
-// macro-cell interior nodes of one colour: race free (no coupling inside a colour)
+// Macro-cell interior nodes of one colour: race free (no coupling inside a colour).  The update
+// u_i <- u_i + (b_i - (A u)_i) / a_ii is evaluated in the equivalent form
+// u_i <- b_i / a_ii - sum_d (a_id / a_ii) u_{i+d}: with the normalised stencil t = a / a_ii of the cell
+// and inv = 1 / a_ii of the level, one multiply and one FMA per coupled neighbour.  The list entries
+// carry (packed index, j | k << 16), so the neighbour offsets need no further lookup.
 template <int DIM, int PM, typename R, typename U, typename B>
-__global__ void __launch_bounds__(kBlock) k_smooth_interior(const int* __restrict__ gcells, const int32_t* __restrict__ list,
-                                                            int64_t len, LevelCtx lc, const R* __restrict__ S, R sscale,
-                                                            const R* __restrict__ inv0, R isscale, Vec<R, U> u,
-                                                            CVec<R, B> rhs) {
+__global__ void __launch_bounds__(kBlock) k_smooth_interior(const int* __restrict__ gcells, const int2* __restrict__ list,
+                                                            int64_t len, LevelCtx lc, const R* __restrict__ tnorm,
+                                                            const R* __restrict__ invl, Vec<R, U> u, CVec<R, B> rhs) {
+  grid_dependency_sync();
   int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (pos >= len) return;
   int T = gcells[blockIdx.y];
-  int32_t loc = list[pos];
+  int2 e = list[pos];
+  int loc = e.x;
   if (HHG_OOB(loc, lc.Nt, 41)) return;
-  int i, j, k;
-  decode(lc.ijk[loc], i, j, k);
+  int j = e.y & 0xffff, k = e.y >> 16;
   int64_t off[15];
   neighbour_offsets(DIM, lc.n, j, k, off);
 #ifdef HHG_CHECK
   for (int d = 1; d < ndirs<DIM>(); ++d)
     if (HHG_OOB(loc + off[d], lc.Nt, 42)) return;
 #endif
-  const R* s = S + (size_t)T * kStencilStride;
+  const R* t = tnorm + (size_t)T * 16;
   int64_t g = (int64_t)T * lc.Nt + loc;
-  R uc = u.get(g);
-  R acc = s[0] * uc;
+  R acc = rhs.get(g) * invl[T];
 #pragma unroll
   for (int q = 0; q < npairs<DIM>(); ++q) {
     if (PM >> q & 1) {
-      acc += s[2 * q + 1] * u.get(g + off[2 * q + 1]);
-      acc += s[2 * q + 2] * u.get(g + off[2 * q + 2]);
+      acc -= t[2 * q + 1] * u.get(g + off[2 * q + 1]);
+      acc -= t[2 * q + 2] * u.get(g + off[2 * q + 2]);
     }
   }
-  // residual and update; 1/(sscale * a_ii) = inv0[T] * (1/sscale) exactly (power-of-two scale)
-  R r = rhs.get(g) - sscale * acc;
-  u.set(g, uc + r * (inv0[T] * isscale));
+  u.set(g, acc);
 }
 
 // macro vertices: never coupled to each other on levels >= 1, so one pass.  One warp per vertex,
@@ -160,12 +198,14 @@ __global__ void __launch_bounds__(kBlock) k_smooth_interior(const int* __restric
 template <int DIM, typename R, typename U, typename B>
 __global__ void k_smooth_vertex(int nprim, const int* __restrict__ ptr, const int* __restrict__ cell,
                                 const int* __restrict__ locv, const unsigned char* __restrict__ dir, LevelCtx lc,
-                                const R* __restrict__ S, R sscale, Vec<R, U> u, CVec<R, B> rhs) {
+                                const R* __restrict__ S, R sscale, const R* __restrict__ pinv, R isscale, Vec<R, U> u,
+                                CVec<R, B> rhs) {
+  grid_dependency_sync();
   int v = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   int lane = threadIdx.x & 31;
   if (v >= nprim || dir[v]) return;  // uniform across the warp
   CVec<R, U> uc{u.p, u.scale};
-  R res = 0, diag = 0;
+  R acc = 0, bs = 0;
   int c0 = ptr[v], c1 = ptr[v + 1];
   int i0, j0, k0;
   prim_position(locv[c0], 1, lc.n, 0, 0, i0, j0, k0);
@@ -173,17 +213,15 @@ __global__ void k_smooth_vertex(int nprim, const int* __restrict__ ptr, const in
   for (int c = c0 + lane; c < c1; c += 32) {
     int i, j, k;
     prim_position(locv[c], 1, lc.n, 0, 0, i, j, k);
-    R dg;
-    int64_t g;
-    res += partial_residual<DIM>(S, cell[c], lc.n, lc.Nt, i, j, k, sscale, uc, rhs, dg, g);
-    diag += dg;
+    copy_terms<DIM, false>(S, lc.nzs, cell[c], lc.n, lc.Nt, i, j, k, uc, rhs, acc, bs);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    res += __shfl_xor_sync(0xffffffffu, res, o);
-    diag += __shfl_xor_sync(0xffffffffu, diag, o);
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    bs += __shfl_xor_sync(0xffffffffu, bs, o);
   }
-  R unew = uold + res / diag;
+  // u += (b - A u) / a_ii with 1 / a_ii = pinv (unit level scale) / sscale
+  R unew = uold + (bs - sscale * acc) * (pinv[v] * isscale);
   for (int c = c0 + lane; c < c1; c += 32) {
     int i, j, k;
     prim_position(locv[c], 1, lc.n, 0, 0, i, j, k);
@@ -214,43 +252,68 @@ __device__ __forceinline__ void stage_position(int nverts, int parity, bool rim,
   }
 }
 
-template <int DIM, typename R, typename U, typename B>
+// One interface stage (edge parity or face colour) on the nodes of nprim primitives.  G lanes
+// (a power of two dividing 32) serve one node: lane r takes the copies ptr[e] + r, + r + G, ...,
+// and the partial residuals and diagonals are summed over the lanes by an xor butterfly, so every
+// lane holds the same sum.  Rim nodes (those that can neighbour another node of the same stage in
+// some cell) store their correction in du for k_iface_apply; inner nodes are updated in place.
+template <int DIM, int G, bool SPARSE, typename R, typename U, typename B>
 __global__ void k_iface_stage(int nprim, int nverts, int parity, int cnt_rim, int cnt_inner,
                               const int32_t* __restrict__ rim_list, const int32_t* __restrict__ inner_list,
                               const int* __restrict__ ptr, const int* __restrict__ cell, const int* __restrict__ locv,
                               const unsigned char* __restrict__ dir, LevelCtx lc, const R* __restrict__ S, R sscale,
-                              Vec<R, U> u, CVec<R, B> rhs, R* __restrict__ du) {
-  int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                              const R* __restrict__ pinv, R isscale, Vec<R, U> u, CVec<R, B> rhs,
+                              R* __restrict__ du) {
+  grid_dependency_sync();
+  int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int lane = (int)(gid & (G - 1));
+  int64_t tid = gid / G;
   int64_t n_rim = (int64_t)nprim * cnt_rim;
   bool rim = tid < n_rim;
   int64_t lt = rim ? tid : tid - n_rim;
   int cnt = rim ? cnt_rim : cnt_inner;
-  if (!rim && lt >= (int64_t)nprim * cnt_inner) return;
-  int e = (int)(lt / cnt), q = (int)(lt % cnt);
-  if (dir[e]) {
-    if (rim) du[tid] = 0;
-    return;
+  bool active = rim || lt < (int64_t)nprim * cnt_inner;
+  int e = 0, q = 0;
+  if (active) {
+    e = (int)(lt / cnt);
+    q = (int)(lt % cnt);
+    if (dir[e]) {
+      if (rim && lane == 0) du[tid] = 0;
+      active = false;
+    }
   }
-  int s, t;
-  stage_position(nverts, parity, rim, lc.n, q, rim ? rim_list : inner_list, s, t);
-  CVec<R, U> uc{u.p, u.scale};
-  R res = 0, diag = 0;
+  int s = 0, t = 0;
+  R acc = 0, bs = 0;
   int64_t g0 = -1;
-  for (int c = ptr[e]; c < ptr[e + 1]; ++c) {
-    int i, j, k;
-    prim_position(locv[c], nverts, lc.n, s, t, i, j, k);
-    R dg;
-    int64_t g;
-    res += partial_residual<DIM>(S, cell[c], lc.n, lc.Nt, i, j, k, sscale, uc, rhs, dg, g);
-    diag += dg;
-    if (g0 < 0) g0 = g;
+  CVec<R, U> uc{u.p, u.scale};
+  if (active) {
+    stage_position(nverts, parity, rim, lc.n, q, rim ? rim_list : inner_list, s, t);
+    for (int c = ptr[e] + lane; c < ptr[e + 1]; c += G) {
+      int i, j, k;
+      prim_position(locv[c], nverts, lc.n, s, t, i, j, k);
+      int64_t g = copy_terms<DIM, SPARSE>(S, lc.nzs, cell[c], lc.n, lc.Nt, i, j, k, uc, rhs, acc, bs);
+      if (g0 < 0) g0 = g;
+    }
   }
+#pragma unroll
+  for (int w = 1; w < G; w <<= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, w);
+    bs += __shfl_xor_sync(0xffffffffu, bs, w);
+  }
+  // correction (b - A u) / a_ii with 1 / a_ii = pinv (unit level scale) / sscale; the new value is
+  // taken from the first copy (lane 0) and broadcast to the group
+  R corr = 0, unew = 0;
+  if (active && lane == 0) {
+    corr = (bs - sscale * acc) * (pinv[e] * isscale);
+    if (!rim) unew = u.get(g0) + corr;
+  }
+  if (G > 1) unew = __shfl_sync(0xffffffffu, unew, 0, G);
+  if (!active) return;
   if (rim) {
-    du[tid] = res / diag;
+    if (lane == 0) du[tid] = corr;
     return;
   }
-  R unew = u.get(g0) + res / diag;
-  for (int c = ptr[e]; c < ptr[e + 1]; ++c) {
+  for (int c = ptr[e] + lane; c < ptr[e + 1]; c += G) {
     int i, j, k;
     prim_position(locv[c], nverts, lc.n, s, t, i, j, k);
     int64_t p = packed_index(DIM, lc.n, i, j, k);
@@ -259,18 +322,22 @@ __global__ void k_iface_stage(int nprim, int nverts, int parity, int cnt_rim, in
   }
 }
 
-template <int DIM, typename R, typename U>
+// second phase of a stage for its rim nodes: u += du on every copy (G lanes per node, as above)
+template <int DIM, int G, typename R, typename U>
 __global__ void k_iface_apply(int nprim, int nverts, int parity, int cnt_rim, const int32_t* __restrict__ rim_list,
                               const int* __restrict__ ptr, const int* __restrict__ cell, const int* __restrict__ locv,
                               const unsigned char* __restrict__ dir, LevelCtx lc, Vec<R, U> u, const R* __restrict__ du) {
-  int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  grid_dependency_sync();
+  int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int lane = (int)(gid & (G - 1));
+  int64_t tid = gid / G;
   if (tid >= (int64_t)nprim * cnt_rim) return;
   int e = (int)(tid / cnt_rim), q = (int)(tid % cnt_rim);
   if (dir[e]) return;
   int s, t;
   stage_position(nverts, parity, true, lc.n, q, rim_list, s, t);
   R d = du[tid];
-  for (int c = ptr[e]; c < ptr[e + 1]; ++c) {
+  for (int c = ptr[e] + lane; c < ptr[e + 1]; c += G) {
     int i, j, k;
     prim_position(locv[c], nverts, lc.n, s, t, i, j, k);
     int64_t p = packed_index(DIM, lc.n, i, j, k);
@@ -280,28 +347,103 @@ __global__ void k_iface_apply(int nprim, int nverts, int parity, int cnt_rim, co
   }
 }
 
-// ---------------------------------------------------------------- residual, restriction (row 4)
+// binary64 face stages with at least this many nodes run one lane per node with the sparse stencil
+// loop (the 384-tet cube has 5.6e5 face nodes per colour at level 6, 1.3e5 at 5, 3.0e4 at 4)
+constexpr int64_t kSparseFaceNodes = 100000;
 
-template <int DIM, int PM, typename R, typename U, typename B, typename O>
-__global__ void __launch_bounds__(kBlock) k_residual(const int* __restrict__ gcells, LevelCtx lc, const R* __restrict__ S,
-                                                     const uint16_t* __restrict__ dirmask, R sscale, CVec<R, U> u,
-                                                     CVec<R, B> rhs, O* __restrict__ out) {
-  int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (loc >= lc.Nt) return;
-  int T = gcells[blockIdx.y];
-  int i, j, k;
-  decode(lc.ijk[loc], i, j, k);
-  int t = boundary_type(DIM, lc.n, i, j, k);
-  int64_t g = (int64_t)T * lc.Nt + loc;
-  if (dirmask[T] >> t & 1) {
-    out[g] = (O)0;
+// lanes per interface node: the copy count rounded up to a power of two, at most a warp
+inline int iface_lanes(int max_copies) {
+  int g = 1;
+  while (g < max_copies && g < 32) g <<= 1;
+  return g;
+}
+
+// launch one interface stage over the primitives of P, then (if it has rim nodes) its apply phase
+template <int DIM, int G, bool SPARSE, typename R, typename U, typename B>
+void launch_iface_g(int nprim, const int* ptr, const int* cell, const int* locv, const unsigned char* dir,
+                    int nverts, int parity, int cnt_rim, int cnt_inner, const int32_t* rim_list,
+                    const int32_t* inner_list, LevelCtx lc, const R* S, R ss, const R* pinv, Vec<R, U> u,
+                    CVec<R, B> rhs, R* du, cudaStream_t s) {
+  int64_t nodes = (int64_t)nprim * (cnt_rim + cnt_inner);
+  hhg_launch(k_iface_stage<DIM, G, SPARSE, R, U, B>, blocks_for(nodes * G), kBlock, 0, s, 
+      nprim, nverts, parity, cnt_rim, cnt_inner, rim_list, inner_list, ptr, cell, locv, dir, lc, S, ss, pinv,
+      (R)1 / ss, u, rhs, du);
+  if (cnt_rim > 0)
+    hhg_launch(k_iface_apply<DIM, G, R, U>, blocks_for((int64_t)nprim * cnt_rim * G), kBlock, 0, s, 
+        nprim, nverts, parity, cnt_rim, rim_list, ptr, cell, locv, dir, lc, u, du);
+}
+
+template <int DIM, typename R, typename U, typename B>
+void launch_iface(int lanes, bool sparse, int nprim, const int* ptr, const int* cell, const int* locv,
+                  const unsigned char* dir, int nverts, int parity, int cnt_rim, int cnt_inner,
+                  const int32_t* rim_list, const int32_t* inner_list, LevelCtx lc, const R* S, R ss, const R* pinv,
+                  Vec<R, U> u, CVec<R, B> rhs, R* du, cudaStream_t s) {
+#define HHG_IFACE_G(GL, SP)                                                                                        \
+  launch_iface_g<DIM, GL, SP, R, U, B>(nprim, ptr, cell, locv, dir, nverts, parity, cnt_rim, cnt_inner, rim_list, \
+                                       inner_list, lc, S, ss, pinv, u, rhs, du, s)
+  if (sparse && lanes == 1) {
+    HHG_IFACE_G(1, true);
     return;
   }
-  int64_t off[15];
-  neighbour_offsets(DIM, lc.n, j, k, off);
-  const R* s = S + (size_t)T * kStencilStride + t * kMaxDirs;
-  R acc = s[0] * u.get(g);
-  if (t == 0) {
+  switch (lanes) {
+    case 1: HHG_IFACE_G(1, false); break;
+    case 2: HHG_IFACE_G(2, false); break;
+    case 4: HHG_IFACE_G(4, false); break;
+    case 8: HHG_IFACE_G(8, false); break;
+    case 16: HHG_IFACE_G(16, false); break;
+    default: HHG_IFACE_G(32, false); break;
+  }
+#undef HHG_IFACE_G
+}
+
+// ---------------------------------------------------------------- residual, restriction (row 4)
+
+// list segments of k_residual_list for one group on one level: directly after a sweep the last
+// interior colour's entries are zeroed instead of computed
+struct ResidualSegments {
+  const int2* ilist;
+  int64_t ncomp, nzero;
+  unsigned bcomp, bzero;
+};
+inline ResidualSegments residual_segments(const LevelData& Lv, const Group& G, int gi, bool after_sweep) {
+  const std::vector<int64_t>& off = Lv.icol_off[gi];
+  int64_t a = off[0], z = off[G.m - 1], b = off[G.m];
+  ResidualSegments r;
+  r.ilist = Lv.d_icol + a;
+  r.ncomp = after_sweep ? z - a : b - a;
+  r.nzero = after_sweep ? b - z : 0;
+  r.bcomp = blocks_for(r.ncomp);
+  r.bzero = blocks_for(r.nzero);
+  return r;
+}
+
+// Partial residual r = b - A u on every closure node of the group's cells (grid.y), zero on
+// Dirichlet rows, from node lists in three block-uniform segments: blocks [0, bcomp) take interior list entries [0, ncomp) with the compile-time stencil
+// pattern PM; blocks [bcomp, bcomp + bzero) write 0 at entries [ncomp, ncomp + nzero) (the interior
+// colour updated last, directly after a sweep); the remaining blocks take the boundary-type nodes
+// (list sorted by type, so a warp mostly shares one slot mask), zero on Dirichlet types.
+template <int DIM, int PM, typename R, typename U, typename B, typename O>
+__global__ void __launch_bounds__(kBlock) k_residual_list(const int* __restrict__ gcells, LevelCtx lc,
+                                                          const R* __restrict__ S, const uint16_t* __restrict__ dirmask,
+                                                          R sscale, CVec<R, U> u, CVec<R, B> rhs, O* __restrict__ out,
+                                                          const int2* __restrict__ ilist, int64_t ncomp, int64_t nzero,
+                                                          const int2* __restrict__ blist, int64_t nbnd, unsigned bcomp,
+                                                          unsigned bzero) {
+  grid_dependency_sync();
+  int T = gcells[blockIdx.y];
+  unsigned bx = blockIdx.x;
+  const int64_t cell0 = (int64_t)T * lc.Nt;
+  if (bx < bcomp) {
+    int64_t pos = (int64_t)bx * blockDim.x + threadIdx.x;
+    if (pos >= ncomp) return;
+    int2 e = ilist[pos];
+    if (HHG_OOB(e.x, lc.Nt, 52)) return;
+    int j = e.y & 0xffff, k = e.y >> 16;
+    int64_t g = cell0 + e.x;
+    int64_t off[15];
+    neighbour_offsets(DIM, lc.n, j, k, off);
+    const R* s = S + (size_t)T * kStencilStride;  // interior type 0
+    R acc = s[0] * u.get(g);
 #pragma unroll
     for (int q = 0; q < npairs<DIM>(); ++q) {
       if (PM >> q & 1) {
@@ -309,20 +451,45 @@ __global__ void __launch_bounds__(kBlock) k_residual(const int* __restrict__ gce
         acc += s[2 * q + 2] * u.get(g + off[2 * q + 2]);
       }
     }
+    out[g] = (dirmask[T] & 1) ? (O)0 : (O)(rhs.get(g) - sscale * acc);
+  } else if (bx < bcomp + bzero) {
+    int64_t pos = (int64_t)(bx - bcomp) * blockDim.x + threadIdx.x;
+    if (pos >= nzero) return;
+    int loc = ilist[ncomp + pos].x;
+    if (HHG_OOB(loc, lc.Nt, 53)) return;
+    out[cell0 + loc] = (O)0;
   } else {
-    uint32_t vm = valid_dirs_tab(DIM, t);
-    mask_offsets(DIM, vm, off);
-#pragma unroll
-    for (int d = 1; d < ndirs<DIM>(); ++d)
-      if ((vm >> d & 1) && !HHG_OOB(loc + off[d], lc.Nt, 51)) acc += s[d] * u.get(g + off[d]);
+    int64_t pos = (int64_t)(bx - bcomp - bzero) * blockDim.x + threadIdx.x;
+    if (pos >= nbnd) return;
+    int2 e = blist[pos];
+    if (HHG_OOB(e.x, lc.Nt, 54)) return;
+    int i, j, k;
+    decode(e.y, i, j, k);
+    int t = boundary_type(DIM, lc.n, i, j, k);
+    int64_t g = cell0 + e.x;
+    if (dirmask[T] >> t & 1) {
+      out[g] = (O)0;
+      return;
+    }
+    uint32_t vm = valid_dirs_tab(DIM, t) & lc.nzs[T * kMaxTypes + t];
+    PlaneBasis pb = plane_basis(DIM, lc.n, k);
+    const R* s = S + (size_t)T * kStencilStride + t * kMaxDirs;
+    R acc = s[0] * u.get(g);
+    for (uint32_t mm = vm & ~1u; mm; mm &= mm - 1) {
+      int d = __ffs(mm) - 1;
+      int64_t o = dir_offset(DIM, d, pb.m, j, pb.Tm, pb.Tm1);
+      if (HHG_OOB(e.x + o, lc.Nt, 55)) continue;
+      acc += s[d] * u.get(g + o);
+    }
+    out[g] = (O)(rhs.get(g) - sscale * acc);
   }
-  out[g] = (O)(rhs.get(g) - sscale * acc);
 }
 
 // coarse partial rhs = P^T (fine partial residual), per cell: r_c(q) = r_f(2q) + 1/2 sum_d r_f(2q+d)
 template <int DIM, typename R, typename I, typename O>
 __global__ void k_restrict(LevelCtx fc, LevelCtx cc, const uint16_t* __restrict__ dirmask, const I* __restrict__ rf,
                            O* __restrict__ rcv) {
+  grid_dependency_sync();
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (loc >= cc.Nt) return;
   int T = blockIdx.y;
@@ -367,6 +534,7 @@ __device__ __forceinline__ R interp(LevelCtx cc, int T, int i, int j, int k, con
 template <int DIM, typename R, typename UC, typename UF>
 __global__ void k_prolong_add(LevelCtx fc, LevelCtx cc, const uint16_t* __restrict__ dirmask, CVec<R, UC> uc,
                               Vec<R, UF> uf) {
+  grid_dependency_sync();
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (loc >= fc.Nt) return;
   int T = blockIdx.y;
@@ -383,6 +551,7 @@ template <int DIM>
 __global__ void k_fmg_prolong(LevelCtx fc, LevelCtx cc, int nL, int64_t NtL, int shift, const double* __restrict__ gL,
                               const uint16_t* __restrict__ dirmask, const double* __restrict__ uc,
                               double* __restrict__ uf, double* __restrict__ w) {
+  grid_dependency_sync();
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (loc >= fc.Nt) return;
   int T = blockIdx.y;
@@ -405,6 +574,7 @@ __global__ void k_fmg_prolong(LevelCtx fc, LevelCtx cc, int nL, int64_t NtL, int
 // plain interpolation v_f = I v_c (all nodes)
 template <int DIM>
 __global__ void k_prolong(LevelCtx fc, LevelCtx cc, const double* __restrict__ vc, double* __restrict__ vf) {
+  grid_dependency_sync();
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (loc >= fc.Nt) return;
   int T = blockIdx.y;
@@ -423,6 +593,7 @@ __global__ void __launch_bounds__(1024) k_coarse(int n0f, const int* __restrict_
                                                  LevelCtx lc, const double* __restrict__ S,
                                                  const double* __restrict__ rhs, double* __restrict__ u,
                                                  const double* __restrict__ Ainv) {
+  grid_dependency_sync();
   extern __shared__ double r[];
   CVec<double, double> uc{u, nullptr};
   CVec<double, double> rc{rhs, nullptr};
@@ -431,13 +602,13 @@ __global__ void __launch_bounds__(1024) k_coarse(int n0f, const int* __restrict_
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int q = warp; q < n0f; q += nw) {
       int v = cf[q];
-      double res = 0, dg;
+      double acc = 0, bs = 0;
       for (int c = ptr[v] + lane; c < ptr[v + 1]; c += 32) {
         int i, j, k;
         prim_position(locv[c], 1, lc.n, 0, 0, i, j, k);
-        int64_t g;
-        res += partial_residual<DIM>(S, cell[c], lc.n, lc.Nt, i, j, k, 1.0, uc, rc, dg, g);
+        copy_terms<DIM, false>(S, lc.nzs, cell[c], lc.n, lc.Nt, i, j, k, uc, rc, acc, bs);
       }
+      double res = bs - acc;  // level 0: unit stiffness scale
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) res += __shfl_xor_sync(0xffffffffu, res, o);
       if (lane == 0) r[q] = res;
@@ -476,6 +647,7 @@ __global__ void __launch_bounds__(1024) k_coarse(int n0f, const int* __restrict_
 template <int DIM, bool DIFF>
 __global__ void k_node_form(LevelCtx lc, const double* __restrict__ tab, const double* __restrict__ a,
                             const double* __restrict__ b, double* __restrict__ contrib) {
+  grid_dependency_sync();
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (loc >= lc.Nt) return;
   int T = blockIdx.y;
@@ -498,23 +670,24 @@ __global__ void k_node_form(LevelCtx lc, const double* __restrict__ tab, const d
     xp = a[g];
     yp = b[g];
   }
-  double sum = s[0] * xp * yp;
+  // x_p (M y)_p restricted to the half stencil: s0 x_p y_p + sum_{+d} s_d (x_p y_q + x_q y_p),
+  // grouped as x_p (s0 y_p + sum s_d y_q) + y_p sum s_d x_q (one accumulator when x = y)
+  double ay = 0, ax = 0;
 #pragma unroll
   for (int q = 0; q < npairs<DIM>(); ++q) {
     int d = 2 * q + 1;
     if (!(vm >> d & 1)) continue;
     if (HHG_OOB(loc + off[d], lc.Nt, 13)) continue;
-    double xq, yq;
     if (DIFF) {
-      xq = a[g + off[d]];
+      double xq = a[g + off[d]];
       if (b) xq -= b[g + off[d]];
-      yq = xq;
+      ay += s[d] * xq;
     } else {
-      xq = a[g + off[d]];
-      yq = b[g + off[d]];
+      ay += s[d] * b[g + off[d]];
+      ax += s[d] * a[g + off[d]];
     }
-    sum += s[d] * (xp * yq + xq * yp);
   }
+  double sum = DIFF ? xp * (s[0] * xp + 2.0 * ay) : xp * (s[0] * yp + ay) + yp * ax;
   contrib[g] = sum;
 }
 
@@ -526,6 +699,7 @@ template <int DIM>
 __global__ void k_apply_partial(LevelCtx lc, const double* __restrict__ tab, double scale,
                                 const double* __restrict__ in, double* __restrict__ out,
                                 const unsigned char* __restrict__ inS, const uint16_t* __restrict__ dirmask) {
+  grid_dependency_sync();
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (loc >= lc.Nt) return;
   int T = blockIdx.y;
@@ -553,6 +727,7 @@ template <int DIM>
 __global__ void k_sum_prims(int nprim, int nverts, int cnt, const int32_t* __restrict__ flist, const int* __restrict__ ptr,
                             const int* __restrict__ cell, const int* __restrict__ locv, LevelCtx lc,
                             double* __restrict__ v) {
+  grid_dependency_sync();
   int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (int64_t)nprim * cnt) return;
   int e = (int)(tid / cnt), q = (int)(tid % cnt);
@@ -584,6 +759,7 @@ template <int DIM>
 __global__ void k_owner_collect(int nprim, int nverts, int cnt, const int32_t* __restrict__ flist,
                                 const int* __restrict__ ptr, const int* __restrict__ cell, const int* __restrict__ locv,
                                 LevelCtx lc, double* __restrict__ v) {
+  grid_dependency_sync();
   int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (int64_t)nprim * cnt) return;
   int e = (int)(tid / cnt), q = (int)(tid % cnt);

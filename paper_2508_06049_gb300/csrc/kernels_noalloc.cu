@@ -28,6 +28,7 @@ template <int DIM>
 __global__ void __launch_bounds__(256) k_noalloc_form(LevelCtx lc, int items, int nchunks, const double* __restrict__ tab,
                                                       const double* __restrict__ a, const double* __restrict__ b,
                                                       double* __restrict__ part) {
+  grid_dependency_sync();
   __shared__ double sh[256];
   int T = blockIdx.y, chunk = blockIdx.x;
   double acc = 0;
@@ -65,6 +66,7 @@ __global__ void __launch_bounds__(256) k_noalloc_form(LevelCtx lc, int items, in
 
 __global__ void k_noalloc_sum(int nc, int nchunks, double scale, const double* __restrict__ part,
                               double* __restrict__ out) {
+  grid_dependency_sync();
   int T = blockIdx.x * blockDim.x + threadIdx.x;
   if (T >= nc) return;
   double s = 0;
@@ -118,13 +120,13 @@ extern "C" hhg_status hhg_cell_mass_norms_noalloc(hhg_mesh m, const double* a, c
     if ((e = cudaEventRecord(m->ev_legacy, (cudaStream_t)0)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     if ((e = cudaStreamWaitEvent(s, m->ev_legacy, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
   }
-  LevelCtx lc{Lv.n, Lv.Nt, Lv.d_ijk};
+  LevelCtx lc{Lv.n, Lv.Nt, Lv.d_ijk, nullptr};
   dim3 grid((unsigned)nchunks, (unsigned)m->nc);
-  if (m->dim == 2) k_noalloc_form<2><<<grid, 256, 0, s>>>(lc, items, (int)nchunks, m->dM, a, b, part);
-  else k_noalloc_form<3><<<grid, 256, 0, s>>>(lc, items, (int)nchunks, m->dM, a, b, part);
+  if (m->dim == 2) hhg_launch(k_noalloc_form<2>, grid, 256, 0, s, lc, items, (int)nchunks, m->dM, a, b, part);
+  else hhg_launch(k_noalloc_form<3>, grid, 256, 0, s, lc, items, (int)nchunks, m->dM, a, b, part);
   double n = (double)Lv.n;
   double scale = m->dim == 2 ? 1.0 / (n * n) : 1.0 / (n * n * n);
-  k_noalloc_sum<<<(m->nc + 255) / 256, 256, 0, s>>>(m->nc, (int)nchunks, scale, part, out);
+  hhg_launch(k_noalloc_sum, (m->nc + 255) / 256, 256, 0, s, m->nc, (int)nchunks, scale, part, out);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "hhg_cell_mass_norms_noalloc launch");
   return HHG_OK;

@@ -135,6 +135,48 @@ HHG_HD void neighbour_offsets(int dim, int64_t n, int64_t j, int64_t k, int64_t*
   off[14] = -Tm1 + m + 1;        // -e1+e2-e3
 }
 
+// The same offsets one slot at a time, for loops over a bit mask of slots: every offset is
+// c0 + cm m + cj j + cT T(m) + cT1 T(m+1) with m the side of the node's plane (n in 2D).
+HHG_HD int64_t dir_offset(int dim, int slot, int64_t m, int64_t j, int64_t Tm, int64_t Tm1) {
+  if (dim == 2) {
+    switch (slot) {
+      case 1: return 1;
+      case 2: return -1;
+      case 3: return m + 1 - j;
+      case 4: return -(m + 2 - j);
+      case 5: return -(m + 1 - j);
+      case 6: return m - j;
+      default: return 0;
+    }
+  }
+  switch (slot) {
+    case 1: return 1;
+    case 2: return -1;
+    case 3: return m + 1 - j;
+    case 4: return -(m + 2 - j);
+    case 5: return Tm - j;
+    case 6: return -Tm1 + j;
+    case 7: return -(m + 1 - j);
+    case 8: return m - j;
+    case 9: return 1 - Tm1 + j;
+    case 10: return -1 + Tm - j;
+    case 11: return -Tm1 + m + 2;
+    case 12: return Tm - m - 1;
+    case 13: return Tm - m;
+    case 14: return -Tm1 + m + 1;
+    default: return 0;
+  }
+}
+
+// plane side m and triangle sizes T(m), T(m+1) of a node at (j, k) for dir_offset()
+struct PlaneBasis {
+  int64_t m, Tm, Tm1;
+};
+HHG_HD PlaneBasis plane_basis(int dim, int64_t n, int64_t k) {
+  int64_t m = dim == 2 ? n : n - k;
+  return PlaneBasis{m, tri_size(m), tri_size(m + 1)};
+}
+
 // Replace the offsets of directions that leave the closure by 0 (the node itself), so that no
 // address outside the cell's closure is ever formed; the stencil entries of those directions are 0.
 HHG_HD void mask_offsets(int dim, uint32_t vm, int64_t* off) {

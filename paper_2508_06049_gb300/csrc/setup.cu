@@ -264,6 +264,27 @@ static void type_primitive(int dim, int t, int& nv, int a[3]) {
   }
 }
 
+// Boundary type, in its cell, of the interior nodes of a primitive with nverts local vertices packed
+// in loc (a0 | a1 << 2 | a2 << 4): the node n E_a0 + s (E_a1 - E_a0) + t (E_a2 - E_a0) with n = 4,
+// s = t = 1 (s = t = 0 for a vertex) lies inside the primitive.
+static int prim_interior_type(int dim, int nverts, int loc) {
+  const int n = 4;
+  int a[3] = {loc & 3, (loc >> 2) & 3, (loc >> 4) & 3};
+  int e[3][3];
+  for (int q = 0; q < 3; ++q) {
+    e[q][0] = a[q] == 1;
+    e[q][1] = a[q] == 2;
+    e[q][2] = a[q] == 3;
+  }
+  int x[3];
+  for (int c = 0; c < 3; ++c) {
+    x[c] = n * e[0][c];
+    if (nverts >= 2) x[c] += e[1][c] - e[0][c];
+    if (nverts >= 3) x[c] += e[2][c] - e[0][c];
+  }
+  return boundary_type(dim, n, x[0], x[1], x[2]);
+}
+
 hhg_status upload_coefficient(hhg_mesh_s* m) {
   const int NS = kMaxTypes * kMaxDirs;
   std::vector<double> S((size_t)m->nc * NS);
@@ -271,22 +292,79 @@ hhg_status upload_coefficient(hhg_mesh_s* m) {
   for (int c = 0; c < m->nc; ++c)
     for (int q = 0; q < NS; ++q) {
       S[(size_t)c * NS + q] = m->k[c] * m->hS1[(size_t)c * NS + q];
-      S32[(size_t)c * NS + q] = (float)S[(size_t)c * NS + q];
       M32[(size_t)c * NS + q] = (float)m->hM[(size_t)c * NS + q];
     }
+  // Couplings below 1e-12 of the largest off-diagonal entry of a partial stencil are rounding
+  // residue of exact zeros (the same threshold decides the interior zero pattern and colouring):
+  // they are set to zero, and the kernels skip the zero slots (nzs mask, centre always kept).
+  std::vector<uint16_t> nzs((size_t)m->nc * kMaxTypes, 0);
+  for (int c = 0; c < m->nc; ++c)
+    for (int t = 0; t < kMaxTypes; ++t) {
+      double* st = &S[(size_t)c * NS + t * kMaxDirs];
+      double vmax = 0;
+      for (int q = 1; q < kMaxDirs; ++q) vmax = std::max(vmax, std::fabs(st[q]));
+      uint16_t mk = 1;
+      for (int q = 1; q < kMaxDirs; ++q) {
+        if (std::fabs(st[q]) <= 1e-12 * vmax) st[q] = 0.0;
+        if (st[q] != 0.0) mk |= (uint16_t)(1u << q);
+      }
+      nzs[(size_t)c * kMaxTypes + t] = mk;
+    }
+  for (size_t q = 0; q < S.size(); ++q) S32[q] = (float)S[q];
+  CK(cudaMemcpy(m->d_nzs, nzs.data(), nzs.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(m->dS, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice));
   {
-    std::vector<double> inv(m->nc);
-    std::vector<float> invf(m->nc);
+    std::vector<double> inv(m->nc), tn((size_t)m->nc * 16, 0.0);
+    std::vector<float> invf(m->nc), tnf((size_t)m->nc * 16, 0.0f);
     for (int c = 0; c < m->nc; ++c) {
-      inv[c] = 1.0 / S[(size_t)c * NS];  // interior type 0, centre slot 0
+      const double* s0 = &S[(size_t)c * NS];  // interior type 0
+      inv[c] = 1.0 / s0[0];
       invf[c] = (float)inv[c];
+      for (int d = 0; d < kMaxDirs; ++d) {
+        tn[(size_t)c * 16 + d] = s0[d] / s0[0];
+        tnf[(size_t)c * 16 + d] = (float)tn[(size_t)c * 16 + d];
+      }
     }
     CK(cudaMemcpy(m->d_inv0, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(m->d_inv0f, invf.data(), invf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->d_tnorm, tn.data(), tn.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->d_tnormf, tnf.data(), tnf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    // per level: 1 / (sscale_l * a_ii) = inv0 / sscale_l (power-of-two scale: exact)
+    for (auto& Lv : m->lv) {
+      double isc = m->dim == 2 ? 1.0 : (double)Lv.n;
+      std::vector<double> il(m->nc);
+      std::vector<float> ilf(m->nc);
+      for (int c = 0; c < m->nc; ++c) {
+        il[c] = inv[c] * isc;
+        ilf[c] = (float)il[c];
+      }
+      CK(cudaMemcpy(Lv.d_invl, il.data(), il.size() * sizeof(double), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(Lv.d_invlf, ilf.data(), ilf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
   }
   CK(cudaMemcpy(m->dS32, S32.data(), S32.size() * sizeof(float), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(m->dM32, M32.data(), M32.size() * sizeof(float), cudaMemcpyHostToDevice));
+  // inverse assembled diagonal of each primitive's interior nodes: the sum over its cell copies of
+  // the centre entry of the copy's partial stencil (the copy's boundary type is the same for all
+  // interior nodes of the primitive)
+  for (int kind = 0; kind < 3; ++kind) {
+    Prims& P = kind == 0 ? m->verts : (kind == 1 ? m->edges : m->faces);
+    if (P.count == 0) continue;
+    std::vector<double> pv(P.count, 0.0);
+    std::vector<float> pf(P.count, 0.0f);
+    for (int e = 0; e < P.count; ++e) {
+      if (P.dir[e]) continue;
+      double dsum = 0;
+      for (int c = P.ptr[e]; c < P.ptr[e + 1]; ++c) {
+        int t = prim_interior_type(m->dim, kind + 1, P.loc[c]);
+        dsum += S[(size_t)P.cell[c] * NS + t * kMaxDirs];
+      }
+      pv[e] = 1.0 / dsum;
+      pf[e] = (float)pv[e];
+    }
+    CK(cudaMemcpy(P.d_pinv, pv.data(), pv.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P.d_pinvf, pf.data(), pf.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
   // coarse operator on the free macro vertices (level 0: n = 1, unit scale)
   int n0 = m->n0f;
   if (n0 > 0) {
@@ -329,6 +407,8 @@ static hhg_status upload_prims(hhg_mesh_s* m, Prims& P) {
   if ((st = upload(m, &P.d_cell, P.cell)) != HHG_OK) return st;
   if ((st = upload(m, &P.d_loc, P.loc)) != HHG_OK) return st;
   if ((st = upload(m, &P.d_dir, P.dir)) != HHG_OK) return st;
+  if ((st = dalloc(m, &P.d_pinv, (size_t)P.count)) != HHG_OK) return st;
+  if ((st = dalloc(m, &P.d_pinvf, (size_t)P.count)) != HHG_OK) return st;
   for (int i = 0; i < P.count; ++i) P.max_copies = std::max(P.max_copies, P.ptr[i + 1] - P.ptr[i]);
   return HHG_OK;
 }
@@ -547,11 +627,14 @@ hhg_status build_mesh(hhg_mesh_s* m, const double* coords, const int* cells, con
   // ---- device: stencils, masks, primitives
   hhg_status st;
   if ((st = dalloc(m, &m->dS, (size_t)nc * NS)) != HHG_OK) return st;
+  if ((st = dalloc(m, &m->d_nzs, (size_t)nc * kMaxTypes)) != HHG_OK) return st;
   if ((st = upload(m, &m->dM, m->hM)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->dS32, (size_t)nc * NS)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->dM32, (size_t)nc * NS)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->d_inv0, (size_t)nc)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->d_inv0f, (size_t)nc)) != HHG_OK) return st;
+  if ((st = dalloc(m, &m->d_tnorm, (size_t)nc * 16)) != HHG_OK) return st;
+  if ((st = dalloc(m, &m->d_tnormf, (size_t)nc * 16)) != HHG_OK) return st;
   if ((st = upload(m, &m->d_dirmask, m->dirmask)) != HHG_OK) return st;
   if ((st = upload_prims(m, m->verts)) != HHG_OK) return st;
   if ((st = upload_prims(m, m->edges)) != HHG_OK) return st;
@@ -599,7 +682,7 @@ hhg_status build_mesh(hhg_mesh_s* m, const double* coords, const int* cells, con
         for (int i = 0; i <= Lv.n - k - j; ++i) ijk[packed_index(d, Lv.n, i, j, k)] = i | (j << 10) | (k << 20);
     if ((st = upload(m, &Lv.d_ijk, ijk)) != HHG_OK) return st;
     // interior colour lists per group
-    std::vector<int32_t> icol;
+    std::vector<int2> icol;
     Lv.icol_off.assign(m->groups.size(), {});
     for (size_t g = 0; g < m->groups.size(); ++g) {
       const Group& G = m->groups[g];
@@ -609,12 +692,27 @@ hhg_status build_mesh(hhg_mesh_s* m, const double* coords, const int* cells, con
           int i = ijk[q] & 1023, j = (ijk[q] >> 10) & 1023, k = ijk[q] >> 20;
           if (boundary_type(d, Lv.n, i, j, k) != 0) continue;
           int col = ((G.alpha[0] * i + G.alpha[1] * j + G.alpha[2] * k) % G.m + G.m) % G.m;
-          if (col == c) icol.push_back((int32_t)q);
+          if (col == c) icol.push_back(make_int2((int)q, j | (k << 16)));
         }
         Lv.icol_off[g].push_back((int64_t)icol.size());
       }
     }
     if ((st = upload(m, &Lv.d_icol, icol)) != HHG_OK) return st;
+    // boundary-type nodes, sorted by type (stable: packed order inside a type)
+    std::vector<std::pair<int, int64_t>> bt;
+    for (int64_t q = 0; q < Lv.Nt; ++q) {
+      int i = ijk[q] & 1023, j = (ijk[q] >> 10) & 1023, k = ijk[q] >> 20;
+      int t = boundary_type(d, Lv.n, i, j, k);
+      if (t != 0) bt.push_back({t, q});
+    }
+    std::stable_sort(bt.begin(), bt.end(),
+                     [](const std::pair<int, int64_t>& x, const std::pair<int, int64_t>& y) { return x.first < y.first; });
+    std::vector<int2> bnd;
+    for (auto& e : bt) bnd.push_back(make_int2((int)e.second, ijk[e.second]));
+    Lv.nbnd = (int64_t)bnd.size();
+    if ((st = upload(m, &Lv.d_bnd, bnd)) != HHG_OK) return st;
+    if ((st = dalloc(m, &Lv.d_invl, (size_t)nc)) != HHG_OK) return st;
+    if ((st = dalloc(m, &Lv.d_invlf, (size_t)nc)) != HHG_OK) return st;
     // face colour lists: face-local (a, b), a, b >= 1, a + b <= n - 1, colour (a + 2b) mod 3
     std::vector<int32_t> fcol;
     for (int c = 0; c < 3; ++c) {
@@ -683,14 +781,15 @@ void free_mesh(hhg_mesh_s* m) {
   };
   for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second);
   m->graphs.clear();
-  F(m->dS); F(m->dM); F(m->dS32); F(m->dM32); F(m->d_inv0); F(m->d_inv0f); F(m->d_dirmask);
+  F(m->dS); F(m->dM); F(m->dS32); F(m->dM32); F(m->d_inv0); F(m->d_inv0f); F(m->d_tnorm); F(m->d_tnormf);
+  F(m->d_dirmask); F(m->d_nzs);
   for (hhg::Prims* P : {&m->verts, &m->edges, &m->faces}) {
-    F(P->d_ptr); F(P->d_cell); F(P->d_loc); F(P->d_dir);
+    F(P->d_ptr); F(P->d_cell); F(P->d_loc); F(P->d_dir); F(P->d_pinv); F(P->d_pinvf);
   }
   for (auto& g : m->groups) F(g.d_cells);
   F(m->d_Ainv); F(m->d_cf_vert);
   for (auto& Lv : m->lv) {
-    F(Lv.d_ijk); F(Lv.d_icol); F(Lv.d_fcol); F(Lv.d_frim); F(Lv.d_fin); F(Lv.u); F(Lv.b); F(Lv.rc); F(Lv.w); F(Lv.tmp);
+    F(Lv.d_ijk); F(Lv.d_icol); F(Lv.d_bnd); F(Lv.d_invl); F(Lv.d_invlf); F(Lv.d_fcol); F(Lv.d_frim); F(Lv.d_fin); F(Lv.u); F(Lv.b); F(Lv.rc); F(Lv.w); F(Lv.tmp);
     F(Lv.c16); F(Lv.r32); F(Lv.t32); F(Lv.cscale); F(Lv.x32); F(Lv.b32);
   }
   F(m->fL); F(m->gL); F(m->d_part); F(m->d_red); F(m->d_flag); F(m->d_scal32);

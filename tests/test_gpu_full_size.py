@@ -1,0 +1,152 @@
+"""GPU checks at the full sizes of the two largest 3D workloads, through the C ABI.
+
+The oracle cannot assemble these hierarchies (10^9 and 1.6 * 10^7 nodes), so the checks are
+properties that hold at any size:
+
+* 3072-tet cube, L = 7 (1.07e9 unknowns, f = 1, k_T log-uniform over four decades): the binary64
+  FMG with extra V-cycles and the mixed-precision solve both reach the discretisation error to two
+  digits (algebraic error <= 1 % of the estimate eta_1, Sec. 5's equal-error criterion) against a
+  converged binary64 reference, and the marked top 12.5 % agrees with the reference's marking.
+* Fichera corner, L = 6 (f = 1, k_T uniform in [0.5, 2]): the adjoint gradients of
+  J = int_S u^2 satisfy the homogeneity identities sum_i f_i dJ/df_i = 2J and
+  sum_T k_T dJ/dk_T = -2J (J is quadratic in f and of degree -2 in k), and match central
+  differences along random directions in f and in k.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2508_06049_gb300 as pkg
+    pkg.lib()
+    return pkg, torch
+
+
+def mass_norm(mesh, torch, a, b, cells_out):
+    """||a - b||_M over the whole domain (sum of the per-cell mass norms, on the device)."""
+    mesh.cell_mass_norms_noalloc(a, b, cells_out)
+    torch.cuda.synchronize()
+    return math.sqrt(float(cells_out.sum().item()))
+
+
+def test_cube3072_l7_equal_error(env):
+    P, torch = env
+    co, ce, L, f, g, k, _ = W.workload("cube3072_l7")
+    mesh = P.Mesh(co, ce, L)
+    mesh.set_coefficient(k)
+    N = mesh.n_nodes(L)
+    dev = torch.device("cuda:0")
+    fd = torch.ones(N, dtype=torch.float64, device=dev)   # f = 1, g = 0
+    gd = torch.zeros(N, dtype=torch.float64, device=dev)
+    mesh.set_data(fd, gd)
+    del gd
+    cells = torch.empty(len(ce), dtype=torch.float64, device=dev)
+    ref = torch.empty(N, dtype=torch.float64, device=dev)
+    u = torch.empty(N, dtype=torch.float64, device=dev)
+    assert mesh.info.n_unknowns == (8 * 2 ** L - 1) ** 3
+
+    # binary64 reference: FMG + 100 V-cycles, checked against 20 further V-cycles.  With k_T over four
+    # decades the V(2,1) cycle contracts slowly (about 0.9 per cycle on this mesh), so the
+    # equal-error budgets below are tens of cycles.
+    mesh.solve(P.solve_params(n_extra=100), out=ref)
+    torch.cuda.synchronize()
+    est_ref = mesh.estimate(1)
+    eta = est_ref["eta_j"]
+    mark_ref = P.mark(est_ref["eta_T"], 0.125)
+    mesh.solve(P.solve_params(n_extra=120), out=u)
+    assert mass_norm(mesh, torch, u, ref, cells) <= 1e-3 * eta
+
+    def within(params):
+        mesh.solve(params, out=u)
+        torch.cuda.synchronize()
+        err = mass_norm(mesh, torch, u, ref, cells)
+        return err, err <= 0.01 * eta
+
+    # binary64 arm: FMG + n extra V-cycles
+    n64 = None
+    for n in (0, 8, 16, 32, 48, 64, 96):
+        err, ok = within(P.solve_params(n_extra=n))
+        if ok:
+            n64 = n
+            break
+    assert n64 is not None, err
+    # eta_1 shares the FMG's coarse iterates with the reference: it moves only with u_L
+    est = mesh.estimate(1)
+    assert abs(est["eta_j"] - eta) <= 0.02 * eta
+
+    # mixed arm: binary32 FMG, then refinement steps of 2 binary32 V-cycles, bf16 correction storage
+    nir = None
+    for steps in (2, 4, 8, 16, 24, 32, 48):
+        err, ok = within(P.solve_params(precision=1, storage=1, ir_steps=steps, ir_vcycles=2))
+        if ok:
+            nir = steps
+            break
+    assert nir is not None, err
+    # the binary32 FMG's coarse iterates differ from binary64's by binary32 rounding (about 1e-5 of
+    # u, against |u_L - w_{L-1}| near 1e-3 |u|): eta_1 agrees to a few per cent
+    est = mesh.estimate(1)
+    assert abs(est["eta_j"] - eta) <= 0.05 * eta
+    # marking agrees with the reference except for cells within 5 % of the threshold
+    mk = P.mark(est["eta_T"], 0.125)
+    thr = np.sort(est_ref["eta_T"])[::-1][int(math.ceil(0.125 * len(ce))) - 1]
+    near = np.abs(est_ref["eta_T"] - thr) <= 0.05 * thr
+    assert np.array_equal(mk[~near], mark_ref[~near])
+    print("cube3072_l7: eta_1 %.4e, binary64 FMG + %d extra V-cycles, mixed %d refinement steps x 2 V-cycles"
+          % (eta, n64, nir))
+    mesh.close()
+
+
+def test_fichera336_l6_adjoint_identities(env):
+    P, torch = env
+    co, ce, L, f, g, k, _ = W.workload("fichera336_l6")
+    mesh = P.Mesh(co, ce, L)
+    mesh.set_coefficient(k)
+    x = mesh.level_coords(L)
+    f0 = np.ascontiguousarray(f(x))
+    zero = np.zeros(len(x))
+    in_S = np.all(co[ce].mean(axis=1) > 0.5, axis=1)
+    assert in_S.any()
+    prm = P.solve_params(n_extra=40)
+
+    def J_of(fv, kv):
+        mesh.set_coefficient(kv)
+        mesh.set_data(np.ascontiguousarray(fv), zero)
+        mesh.solve(prm)
+        J, gf, gk = mesh.adjoint_l2(in_S, params=prm)
+        return J, gf, gk
+
+    J, gf, gk = J_of(f0, k)
+    assert J > 0
+    # weight of each interface copy: 1 / (number of copies of its node)
+    key = np.round(x * 2 ** (L + 3)).astype(np.int64) + 4096
+    key = key[:, 0] | (key[:, 1] << 16) | (key[:, 2] << 32)
+    _, inv, cnt = np.unique(key, return_inverse=True, return_counts=True)
+    w = 1.0 / cnt[inv.ravel()]
+    assert abs(np.sum(w * f0 * gf) - 2 * J) <= 1e-9 * J
+    assert abs(np.sum(k * gk) + 2 * J) <= 1e-9 * J
+
+    rng = np.random.default_rng(11)
+    eps = 1e-4
+    v = rng.choice([-1.0, 1.0], size=len(k))
+    Jp, _, _ = J_of(f0, k * (1 + eps * v))
+    Jm, _, _ = J_of(f0, k * (1 - eps * v))
+    fd_k = (Jp - Jm) / (2 * eps)
+    assert abs(fd_k - np.sum(gk * k * v)) <= 1e-6 * J, (fd_k, np.sum(gk * k * v))
+
+    phi = np.sin(3 * x[:, 0]) * np.cos(2 * x[:, 1]) + x[:, 2]
+    Jp, _, _ = J_of(f0 + eps * phi, k)
+    Jm, _, _ = J_of(f0 - eps * phi, k)
+    fd_f = (Jp - Jm) / (2 * eps)
+    assert abs(fd_f - np.sum(w * phi * gf)) <= 1e-6 * J, (fd_f, np.sum(w * phi * gf))
+    mesh.close()
