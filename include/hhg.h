@@ -47,7 +47,8 @@ typedef enum {
   HHG_ERR_OOM = 4,            /* device or host allocation failed                           */
   HHG_ERR_NOT_CONVERGED = 5,  /* an iteration did not reach its target                      */
   HHG_ERR_DIVERGED = 6,       /* NaN/Inf or growth detected in the solution                 */
-  HHG_ERR_STATE = 7           /* call order violated (e.g. estimate before a solve)         */
+  HHG_ERR_STATE = 7,          /* call order violated (e.g. estimate before a solve)         */
+  HHG_ERR_TIMEOUT = 8         /* a bounded device-side wait ran out (results invalid)       */
 } hhg_status;
 
 /* Solve parameters (Alg. 4).  nu: V-cycles per FMG level; pre/post: Gauss-Seidel sweeps
@@ -109,7 +110,8 @@ hhg_status hhg_set_data(hhg_mesh mesh, const double* f_L, const double* g_L);
 
 /* FMG solve (Alg. 4): b_l = M_l f_l on every level, FMG with the given parameters, w_l kept
  * for hhg_estimate.  u_L: host or device, N_L doubles (output).  Returns HHG_ERR_DIVERGED
- * if the result holds NaN/Inf. */
+ * if the result holds NaN/Inf, HHG_ERR_TIMEOUT if a kernel's bounded wait for its asynchronous
+ * shared-memory copies ran out (the flag is cleared; the mesh stays usable). */
 hhg_status hhg_fmg_solve(hhg_mesh mesh, const hhg_solve_params* params, double* u_L);
 
 /* ErrorEstimate of Alg. 4 with offset j (1 <= j <= L-1) on the last solve.

@@ -39,6 +39,14 @@ struct Prims {
   float* d_pinvf = nullptr;
 };
 
+// nodes of the u window (planes k0-1 .. k1+1) of one staged interior tile, at most (a single plane
+// range may exceed it)
+constexpr int64_t kTileNodes = 8192;
+// dynamic shared memory a staged tile may use (tiles beyond it fall back to the list kernel)
+constexpr size_t kMaxTileSmem = 200 * 1024;
+// spare values past the last node of every vector the staged kernel reads
+constexpr int64_t kVecPad = 16;
+
 struct LevelData {
   int l = 0, n = 1;
   int64_t Nt = 0, N = 0;
@@ -47,6 +55,13 @@ struct LevelData {
   // (packed local index, j | k << 16)
   std::vector<std::vector<int64_t>> icol_off;
   int2* d_icol = nullptr;
+  // staged interior stage (3D): plane-range tiles {k0, k1, lo, hi} of group g, colour c at
+  // d_tiles[tile_off[g][c] .. + nranges); tile_smem4: largest dynamic shared memory of one tile
+  // with 4-byte values
+  std::vector<std::vector<int64_t>> tile_off;
+  int nranges = 0;
+  int4* d_tiles = nullptr;
+  size_t tile_smem4 = 0;
   // boundary-type closure nodes (type != 0), sorted by type: (packed local index, i | j << 10 | k << 20)
   int2* d_bnd = nullptr;
   int64_t nbnd = 0;
@@ -114,6 +129,7 @@ struct hhg_mesh_s {
   int64_t part_len = 0;
   double* d_red = nullptr;        // per-cell reduction results (3 x n_cells)
   int* d_flag = nullptr;
+  int* d_err = nullptr;  // sticky: set by a device-side bounded wait that ran out
   float* d_scal32 = nullptr;      // scratch scalars for the mixed path
   std::map<std::string, cudaGraphExec_t> graphs;
   std::map<std::string, long long> graph_kernels;  // kernel nodes per captured graph

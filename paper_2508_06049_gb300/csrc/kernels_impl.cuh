@@ -7,6 +7,7 @@
 
 #include <utility>
 
+#include "bulk_copy.cuh"
 #include "device_common.cuh"
 
 namespace hhg {
@@ -191,6 +192,87 @@ __global__ void __launch_bounds__(kBlock) k_smooth_interior(const int* __restric
     }
   }
   u.set(g, acc);
+}
+
+// The same interior colour stage (3D) with the cell's data staged in shared memory.  One CTA takes
+// one plane range [k0, k1] of one cell (tile = {k0, k1, lo, hi}): the u planes k0-1 .. k1+1 and
+// the b planes k0 .. k1 are contiguous in the packed layout, and the colour's list entries of those
+// planes are the contiguous list range [lo, hi); three bulk asynchronous copies (16-byte aligned
+// windows around them) bring them in, completing on one mbarrier, and the update then reads only
+// shared memory.  Neighbouring CTAs copy each other's boundary planes while those CTAs write
+// their own colour's nodes there; a proper colouring means such values are never used.
+// The vectors read here carry 16 bytes of padding past their last node.  A copy that does not
+// complete within the bounded wait sets *err and the CTA returns without updating.
+constexpr int kBulkWaitTries = 1 << 20;
+
+template <int PM, typename R>
+__global__ void __launch_bounds__(kBlock) k_smooth_interior_tiled(const int* __restrict__ gcells, LevelCtx lc,
+                                                                  const int4* __restrict__ tiles,
+                                                                  const int2* __restrict__ list,
+                                                                  const R* __restrict__ tnorm,
+                                                                  const R* __restrict__ invl, R* u,
+                                                                  const R* __restrict__ b, int* err) {
+  grid_dependency_sync();
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int4 tl = tiles[blockIdx.x];
+  if (tl.w <= tl.z) return;  // no node of this colour in the range (uniform across the CTA)
+  const int T = gcells[blockIdx.y];
+  const int n = lc.n;
+  const int64_t cell0 = (int64_t)T * lc.Nt;
+  const int64_t tn = tet_size(n);
+  const int64_t ua = tn - tet_size(n - tl.x + 1), ue = tn - tet_size(n - tl.y - 2);
+  const int64_t ba = tn - tet_size(n - tl.x), be = tn - tet_size(n - tl.y - 1);
+  const uintptr_t gu0 = (uintptr_t)(u + cell0 + ua), gb0 = (uintptr_t)(b + cell0 + ba), gl0 = (uintptr_t)(list + tl.z);
+  const uintptr_t au = gu0 & ~(uintptr_t)15, ab = gb0 & ~(uintptr_t)15, al = gl0 & ~(uintptr_t)15;
+  const uint32_t nu = (uint32_t)((((uintptr_t)(u + cell0 + ue) - au) + 15) & ~(uintptr_t)15);
+  const uint32_t nb = (uint32_t)((((uintptr_t)(b + cell0 + be) - ab) + 15) & ~(uintptr_t)15);
+  const uint32_t nl = (uint32_t)((((uintptr_t)(list + tl.w) - al) + 15) & ~(uintptr_t)15);
+  R* su = (R*)(smem + 16);
+  R* sb = (R*)(smem + 16 + nu);
+  int2* sl = (int2*)(smem + 16 + nu + nb);
+  const uint32_t bar = smem_addr(smem);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_arrive_expect_tx(bar, nu + nb + nl);
+    bulk_g2s(smem_addr(su), (const void*)au, nu, bar);
+    bulk_g2s(smem_addr(sb), (const void*)ab, nb, bar);
+    bulk_g2s(smem_addr(sl), (const void*)al, nl, bar);
+  }
+  __syncthreads();
+  if (!mbar_wait_bounded(bar, 0, kBulkWaitTries)) {
+    if (threadIdx.x == 0) atomicOr(err, 1);
+    mbar_wait_bounded(bar, 0, kBulkWaitTries);  // let copies in flight land before the CTA exits
+    return;
+  }
+  const int upad = (int)((gu0 - au) / sizeof(R)), bpad = (int)((gb0 - ab) / sizeof(R));
+  const int lpad = (int)((gl0 - al) / sizeof(int2));
+  const R* t = tnorm + (size_t)T * 16;
+  R tv[15];
+#pragma unroll
+  for (int d = 1; d < 15; ++d) tv[d] = ((PM >> ((d - 1) >> 1)) & 1) ? t[d] : (R)0;
+  const R il = invl[T];
+  for (int e = threadIdx.x; e < tl.w - tl.z; e += blockDim.x) {
+    int2 en = sl[lpad + e];
+    int q = en.x, j = en.y & 0xffff, k = en.y >> 16;
+    int64_t off[15];
+    neighbour_offsets(3, n, j, k, off);
+    int c = upad + (int)(q - ua);
+#ifdef HHG_CHECK
+    bool bad = HHG_OOB(c, (int64_t)(nu / sizeof(R)), 43);
+    for (int d = 1; d < 15; ++d)
+      if ((PM >> ((d - 1) >> 1)) & 1) bad |= HHG_OOB(c + off[d], (int64_t)(nu / sizeof(R)), 44);
+    if (bad) continue;
+#endif
+    R acc = sb[bpad + (int)(q - ba)] * il;
+#pragma unroll
+    for (int qq = 0; qq < 7; ++qq) {
+      if (PM >> qq & 1) {
+        acc -= tv[2 * qq + 1] * su[c + off[2 * qq + 1]];
+        acc -= tv[2 * qq + 2] * su[c + off[2 * qq + 2]];
+      }
+    }
+    u[cell0 + q] = acc;
+  }
 }
 
 // macro vertices: never coupled to each other on levels >= 1, so one pass.  One warp per vertex,

@@ -8,6 +8,8 @@
 //         A_L c = r with V-cycles computed in binary32 (same storage rule for the coarse levels).
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "internal.h"
 #include "kernels_impl.cuh"
 
@@ -176,6 +178,15 @@ static void interior32(hhg_mesh_s* m, int l, int gi, int colour, U* u, const flo
   const Group& G = m->groups[gi];
   int64_t a = Lv.icol_off[gi][colour], b = Lv.icol_off[gi][colour + 1];
   if (b <= a || G.cells.empty()) return;
+  // 3D binary32 values: the stage staged through shared memory, one CTA per plane range and cell
+  if (DIM == 3 && std::is_same<U, float>::value && Lv.nranges > 0 && Lv.tile_smem4 <= kMaxTileSmem) {
+    cudaFuncSetAttribute(k_smooth_interior_tiled<PM, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kMaxTileSmem);
+    dim3 grid((unsigned)Lv.nranges, (unsigned)G.cells.size());
+    hhg_launch(k_smooth_interior_tiled<PM, float>, grid, kBlock, Lv.tile_smem4, s, G.d_cells, ctx(m, l),
+               Lv.d_tiles + Lv.tile_off[gi][colour], Lv.d_icol, m->d_tnormf, Lv.d_invlf, (float*)u, rhs, m->d_err);
+    return;
+  }
   dim3 grid(blocks_for(b - a), (unsigned)G.cells.size());
   hhg_launch(k_smooth_interior<DIM, PM, float, U, float>, grid, kBlock, 0, s, 
       G.d_cells, Lv.d_icol + a, b - a, ctx(m, l), m->d_tnormf, Lv.d_invlf, vec_of<U>(m, l, u),
@@ -400,14 +411,17 @@ hhg_status mixed_prepare(hhg_mesh_s* m, int storage) {
   for (auto& Lv : m->lv) {
     if (!m->mixed_alloc) {
       cudaError_t e;
-      if ((e = cudaMalloc(&Lv.x32, sizeof(float) * Lv.N)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-      if ((e = cudaMalloc(&Lv.b32, sizeof(float) * Lv.N)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-      if ((e = cudaMalloc(&Lv.r32, sizeof(float) * Lv.N)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-      if ((e = cudaMalloc(&Lv.t32, sizeof(float) * Lv.N)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+      // kVecPad spare values: the staged interior stage copies 16-byte windows that may end past
+      // the last node
+      const size_t nb = sizeof(float) * (Lv.N + kVecPad);
+      if ((e = cudaMalloc(&Lv.x32, nb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+      if ((e = cudaMalloc(&Lv.b32, nb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+      if ((e = cudaMalloc(&Lv.r32, nb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+      if ((e = cudaMalloc(&Lv.t32, nb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
       if ((e = cudaMalloc(&Lv.cscale, sizeof(float))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-      m->bytes += (long long)(16 * Lv.N + 4);
+      m->bytes += (long long)(4 * nb + 4);
       for (float* q : {Lv.x32, Lv.b32, Lv.r32, Lv.t32})
-        if ((e = cudaMemset(q, 0, sizeof(float) * Lv.N)) != cudaSuccess) return cuda_fail(e, "cudaMemset");
+        if ((e = cudaMemset(q, 0, nb)) != cudaSuccess) return cuda_fail(e, "cudaMemset");
       float one = 1.0f;
       if ((e = cudaMemcpy(Lv.cscale, &one, sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpy");
@@ -416,9 +430,9 @@ hhg_status mixed_prepare(hhg_mesh_s* m, int storage) {
       cudaFree(Lv.c16);
       Lv.c16 = nullptr;
     }
-    cudaError_t e = cudaMalloc(&Lv.c16, esz * Lv.N);
+    cudaError_t e = cudaMalloc(&Lv.c16, esz * (Lv.N + kVecPad));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-    if ((e = cudaMemset(Lv.c16, 0, esz * Lv.N)) != cudaSuccess) return cuda_fail(e, "cudaMemset");
+    if ((e = cudaMemset(Lv.c16, 0, esz * (Lv.N + kVecPad))) != cudaSuccess) return cuda_fail(e, "cudaMemset");
   }
   m->mixed_alloc = true;
   m->last_storage = storage;

@@ -697,6 +697,41 @@ hhg_status build_mesh(hhg_mesh_s* m, const double* coords, const int* cells, con
         Lv.icol_off[g].push_back((int64_t)icol.size());
       }
     }
+    // plane-range tiles of the staged interior stage (3D): consecutive interior planes
+    // k = 1 .. n-3, as many per tile as keep its u window (planes k0-1 .. k1+1) within kTileNodes
+    Lv.tile_off.assign(m->groups.size(), {});
+    std::vector<int4> tiles;
+    if (d == 3 && Lv.n >= 4) {
+      const int n = Lv.n;
+      auto P = [&](int k) { return tet_size(n) - tet_size(n - k); };
+      std::vector<std::pair<int, int>> ranges;
+      for (int k0 = 1; k0 <= n - 3;) {
+        int k1 = k0;
+        while (k1 + 1 <= n - 3 && P(k1 + 3) - P(k0 - 1) <= kTileNodes) ++k1;
+        ranges.push_back({k0, k1});
+        k0 = k1 + 1;
+      }
+      Lv.nranges = (int)ranges.size();
+      auto r16 = [](int64_t bytes) { return (size_t)((bytes + 32 + 15) & ~(int64_t)15); };
+      for (size_t g = 0; g < m->groups.size(); ++g)
+        for (int c = 0; c < m->groups[g].m; ++c) {
+          Lv.tile_off[g].push_back((int64_t)tiles.size());
+          auto b0 = icol.begin() + Lv.icol_off[g][c], b1 = icol.begin() + Lv.icol_off[g][c + 1];
+          auto by_q = [](const int2& e, int64_t q) { return (int64_t)e.x < q; };
+          for (auto& r : ranges) {
+            int64_t lo = std::lower_bound(b0, b1, P(r.first), by_q) - icol.begin();
+            int64_t hi = std::lower_bound(b0, b1, P(r.second + 1), by_q) - icol.begin();
+            tiles.push_back(make_int4(r.first, r.second, (int)lo, (int)hi));
+            size_t sm = 16 + r16(4 * (P(r.second + 2) - P(r.first - 1))) + r16(4 * (P(r.second + 1) - P(r.first))) +
+                        r16(8 * (hi - lo));
+            Lv.tile_smem4 = std::max(Lv.tile_smem4, sm);
+          }
+        }
+    }
+    if ((st = upload(m, &Lv.d_tiles, tiles)) != HHG_OK) return st;
+    // two spare entries: the staged stage copies 16-byte windows that may end past the last entry
+    icol.push_back(make_int2(0, 0));
+    icol.push_back(make_int2(0, 0));
     if ((st = upload(m, &Lv.d_icol, icol)) != HHG_OK) return st;
     // boundary-type nodes, sorted by type (stable: packed order inside a type)
     std::vector<std::pair<int, int64_t>> bt;
@@ -753,6 +788,7 @@ hhg_status build_mesh(hhg_mesh_s* m, const double* coords, const int* cells, con
   if ((st = dalloc(m, &m->d_part, (size_t)m->part_len)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->d_red, (size_t)nc * 4)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->d_flag, 4)) != HHG_OK) return st;
+  if ((st = dalloc(m, &m->d_err, 4)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->d_scal32, 64)) != HHG_OK) return st;
   {
     cudaError_t e = cudaMallocHost((void**)&m->h_red, sizeof(double) * (size_t)nc * 4 + 64);
@@ -789,10 +825,10 @@ void free_mesh(hhg_mesh_s* m) {
   for (auto& g : m->groups) F(g.d_cells);
   F(m->d_Ainv); F(m->d_cf_vert);
   for (auto& Lv : m->lv) {
-    F(Lv.d_ijk); F(Lv.d_icol); F(Lv.d_bnd); F(Lv.d_invl); F(Lv.d_invlf); F(Lv.d_fcol); F(Lv.d_frim); F(Lv.d_fin); F(Lv.u); F(Lv.b); F(Lv.rc); F(Lv.w); F(Lv.tmp);
+    F(Lv.d_ijk); F(Lv.d_icol); F(Lv.d_bnd); F(Lv.d_tiles); F(Lv.d_invl); F(Lv.d_invlf); F(Lv.d_fcol); F(Lv.d_frim); F(Lv.d_fin); F(Lv.u); F(Lv.b); F(Lv.rc); F(Lv.w); F(Lv.tmp);
     F(Lv.c16); F(Lv.r32); F(Lv.t32); F(Lv.cscale); F(Lv.x32); F(Lv.b32);
   }
-  F(m->fL); F(m->gL); F(m->d_part); F(m->d_red); F(m->d_flag); F(m->d_scal32);
+  F(m->fL); F(m->gL); F(m->d_part); F(m->d_red); F(m->d_flag); F(m->d_err); F(m->d_scal32);
   if (m->h_red) cudaFreeHost(m->h_red);
   if (m->cap) cudaStreamDestroy(m->cap);
   if (m->own) cudaStreamDestroy(m->own);

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libhhg.so")
 
 OK = 0
 STATUS = {0: "HHG_OK", 1: "HHG_ERR_ARG", 2: "HHG_ERR_MESH", 3: "HHG_ERR_CUDA", 4: "HHG_ERR_OOM",
-          5: "HHG_ERR_NOT_CONVERGED", 6: "HHG_ERR_DIVERGED", 7: "HHG_ERR_STATE"}
+          5: "HHG_ERR_NOT_CONVERGED", 6: "HHG_ERR_DIVERGED", 7: "HHG_ERR_STATE", 8: "HHG_ERR_TIMEOUT"}
 
 
 class HHGError(RuntimeError):
