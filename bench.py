@@ -49,7 +49,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel-only", type=int, default=0,
                     help="set up the workload, launch the dominant kernel this many times, exit (for ncu)")
-    ap.add_argument("--kernel-id", type=int, default=0, help="with --kernel-only: 0 interior stage, 1 face stage")
+    ap.add_argument("--kernel-id", type=int, default=0,
+                    help="with --kernel-only: 0 interior stage, 1 face stage, 2 prolongation-add, 3 residual, "
+                         "4 estimator mass form (2-4: level L, binary64)")
     return ap.parse_args()
 
 
@@ -153,7 +155,7 @@ def peaks():
 FP64_PEAK_TFLOPS = 1.205
 # DRAM bytes (read + write) of one launch of the roofline kernel on the 384-tet cube at L = 6, from
 # one ncu capture of that kernel (summarised under profiles/); None for other workloads
-TRAFFIC_BYTES = {("cube384_l6", "fp64"): 369.5e6, ("cube384_l6", "mixed"): 166.9e6}
+TRAFFIC_BYTES = {("cube384_l6", "fp64"): 369.5e6}
 
 
 # ----------------------------------------------------------------------------- arms

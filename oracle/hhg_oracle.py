@@ -29,7 +29,11 @@ What each part follows
       id); macro-cell interior nodes by colour (alpha . p) mod m with alpha, m
       chosen per macro from its interior stencil (red-black where the diagonal
       couplings vanish).  Inside one stage all nodes are updated from the values
-      at the start of the stage.
+      at the start of the stage.  The three face colours form one block in which
+      every macro face is smoothed on its own: Gauss-Seidel over the face's nodes
+      in colour order, with all nodes outside the face (including the nodes of
+      other faces next to a shared macro edge) at their values from the start of
+      the block.
     - Coarse solve: exact dense Cholesky solve (the limit of the paper's CG).
     - I = linear interpolation on the nested meshes, restriction = I^T.
 * Sec. 4.4, Alg. 4 (ErrorEstimate) and Eqs. (4.5), (4.6), (4.14): e~_l = u_L - I w_l,
@@ -177,6 +181,12 @@ class Level:
     stages: list = field(default_factory=list)
     stage_rows: list = field(default_factory=list)
     stage_diag: list = field(default_factory=list)
+    # 3D face block (stages face_first .. face_first+2): each face stage's rows split into the
+    # couplings to nodes of the same macro face (current values) and all others (values frozen
+    # at the start of the block)
+    face_first: int = -1
+    stage_rows_same: list = field(default_factory=list)
+    stage_rows_other: list = field(default_factory=list)
     P: sp.csr_matrix = None   # interpolation from level l-1 to l (l >= 1)
 
 
@@ -407,13 +417,29 @@ class Hierarchy:
             col = (np.einsum("nk,nk->n", p[c], self.alpha[macro[c]])) % self.mcol[macro[c]]
             stage_of[c] = base + col
         n_stages = base + int(self.mcol.max())
+        # macro face of each face-interior node (its three vertex ids), -1 elsewhere
+        face_of = np.full(len(keys), -1, dtype=np.int64)
+        if d == 3:
+            f = s == 3
+            if f.any():
+                _, fid = np.unique(np.sort(g[f][:, :3], axis=1), axis=0, return_inverse=True)
+                face_of[f] = fid.ravel()
+            lev.face_first = 3
         lev.stages = []
         diag = lev.A.diagonal()
         for st in range(n_stages):
             idx = np.nonzero((stage_of == st) & free)[0]
             lev.stages.append(idx)
-            lev.stage_rows.append(lev.A[idx])
+            rows = lev.A[idx]
+            lev.stage_rows.append(rows)
             lev.stage_diag.append(diag[idx])
+            if d == 3 and 3 <= st < 6:
+                coo = rows.tocoo()
+                same = face_of[coo.col] == face_of[idx[coo.row]]
+                shape = rows.shape
+                lev.stage_rows_same.append(sp.csr_matrix((coo.data[same], (coo.row[same], coo.col[same])), shape=shape))
+                lev.stage_rows_other.append(
+                    sp.csr_matrix((coo.data[~same], (coo.row[~same], coo.col[~same])), shape=shape))
 
 
 def _row_hash(keys):
@@ -486,16 +512,24 @@ class Problem:
 # Smoother, V-cycle, FMG (Alg. 4)
 # --------------------------------------------------------------------------------------
 
-def smooth(lev: Level, u: np.ndarray, rhs: np.ndarray, reverse: bool = False) -> None:
-    """One Gauss-Seidel sweep as the ordered stage list; Jacobi inside a stage (in place)."""
-    order = range(len(lev.stages))
-    if reverse:
-        order = reversed(order)
-    for s in order:
+def smooth(lev: Level, u: np.ndarray, rhs: np.ndarray) -> None:
+    """One Gauss-Seidel sweep as the ordered stage list; Jacobi inside a stage (in place).
+
+    3D face block: the three face colours update each macro face's nodes by Gauss-Seidel over the
+    face (its own nodes at their current values), with every node outside the face taken at its
+    value from the start of the block (the faces are independent of each other inside the block)."""
+    u0 = None
+    for s in range(len(lev.stages)):
         idx = lev.stages[s]
+        if lev.face_first >= 0 and s == lev.face_first:
+            u0 = u.copy()
         if len(idx) == 0:
             continue
-        r = rhs[idx] - lev.stage_rows[s] @ u
+        if lev.face_first >= 0 and lev.face_first <= s < lev.face_first + 3:
+            q = s - lev.face_first
+            r = rhs[idx] - lev.stage_rows_same[q] @ u - lev.stage_rows_other[q] @ u0
+        else:
+            r = rhs[idx] - lev.stage_rows[s] @ u
         u[idx] += r / lev.stage_diag[s]
 
 

@@ -17,6 +17,8 @@ void launch_restrict_rhs_chain(hhg_mesh_s* m, cudaStream_t s);
 hhg_status read_check(long long* out);
 hhg_status preload_kernels();
 void launch_profile_face(hhg_mesh_s* m, int reps, cudaStream_t s, long long* units);
+void launch_profile_level(hhg_mesh_s* m, int kernel, int reps, cudaStream_t s, long long* units, double* bytes,
+                          double* flops);
 hhg_status mixed_profile_interior(hhg_mesh_s* m, int reps, cudaStream_t s, long long* units, double* bytes,
                                   double* flops);
 hhg_status mixed_prepare(hhg_mesh_s* m, int storage);
@@ -105,13 +107,13 @@ void enqueue_vcycle(hhg_mesh_s* m, int l, const double* rhs, const hhg_solve_par
     launch_coarse_solve(m, rhs, s);
     return;
   }
-  for (int q = 0; q < p.pre; ++q) launch_sweep(m, l, rhs, s, false);
+  for (int q = 0; q < p.pre; ++q) launch_sweep(m, l, rhs, s);
   launch_residual_after(m, l, rhs, s, p.pre > 0);
   launch_restrict(m, l, m->lv[l].tmp, m->lv[l - 1].rc, s);
   cudaMemsetAsync(m->lv[l - 1].u, 0, sizeof(double) * (size_t)m->lv[l - 1].N, s);
   enqueue_vcycle(m, l - 1, m->lv[l - 1].rc, p, s);
   launch_prolong_add(m, l, s);
-  for (int q = 0; q < p.post; ++q) launch_sweep(m, l, rhs, s, false);
+  for (int q = 0; q < p.post; ++q) launch_sweep(m, l, rhs, s);
 }
 
 // Alg. 4 FMG.  adjoint = true: right-hand side given on level L in lv[L].b (restricted to the
@@ -217,6 +219,10 @@ hhg_status hhg_mesh_create(int dim, int n_verts, const double* coords, int n_cel
   m->nc = n_cells;
   m->nv = n_verts;
   m->device = dev;
+  {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) m->sm_count = sms;
+  }
   m->stream = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess && m->stream == nullptr) {
@@ -374,29 +380,34 @@ hhg_status hhg_estimate(hhg_mesh m, int j, double* eta_T, double* eta_jT, hhg_es
   CHECK_PTR(m->dM);
   CHECK_PTR(m->lv[L].d_ijk);
   CHECK_PTR(m->lv[L].tmp);
+  CHECK_PTR(m->lv[L].rc);
   const int jj = j;
+  // The differences are formed once into level-L scratch (rc is never a coarse-grid rhs on level L,
+  // tmp is free after the solve), so the mass form reads one vector.
+  double* xa = m->lv[L].rc;
+  double* xb = m->lv[L].tmp;
   hhg_status st = run_graph(m, "est:" + std::to_string(jj), [&](cudaStream_t cs) {
     // e~_{L-1} = u_L - w_{L-1} (eta_T)
-    launch_mass_norm_sq(m, uL, m->lv[L - 1].w, red, cs);
+    launch_sub(m, uL, m->lv[L - 1].w, xa, m->lv[L].N, cs);
+    launch_mass_norm_sq(m, xa, nullptr, red, cs);
     // e~_l = u_L - I w_l (w_l lives on level l+1); for j = 1 it is e~_{L-1} again
     if (l == L - 1) {
       cudaMemcpyAsync(red + nc, red, sizeof(double) * nc, cudaMemcpyDeviceToDevice, cs);
     } else {
       const double* v = m->lv[l].w;
       for (int q = l + 2; q <= L; ++q) {
-        launch_prolong(m, q, v, m->lv[q].tmp, cs);
+        launch_prolong(m, q, v, m->lv[q].tmp, cs, q == L ? uL : nullptr);
         v = m->lv[q].tmp;
       }
-      launch_mass_norm_sq(m, uL, v, red + nc, cs);
+      launch_mass_norm_sq(m, xb, nullptr, red + nc, cs);
     }
-    const double* v;
     // e~_{l-1} = u_L - I w_{l-1} (w_{l-1} lives on level l)
-    v = m->lv[l - 1].w;
+    const double* v = m->lv[l - 1].w;
     for (int q = l + 1; q <= L; ++q) {
-      launch_prolong(m, q, v, m->lv[q].tmp, cs);
+      launch_prolong(m, q, v, m->lv[q].tmp, cs, q == L ? uL : nullptr);
       v = m->lv[q].tmp;
     }
-    launch_mass_norm_sq(m, uL, v, red + 2 * nc, cs);
+    launch_mass_norm_sq(m, xb, nullptr, red + 2 * nc, cs);
   });
   if (st != HHG_OK) return st;
   DBG_SYNC("estimator graph");
@@ -485,7 +496,7 @@ hhg_status hhg_apply(hhg_mesh m, int level, int op, const double* in, double* ou
     // rhs = M in (partial), initial guess from out, sweeps in place on the level's u
     launch_apply_op(m, level, 1, din, Lv.b, s);
     cudaMemcpyAsync(Lv.u, out, sizeof(double) * Lv.N, cudaMemcpyDefault, s);
-    for (int q = 0; q < nsweeps; ++q) launch_sweep(m, level, Lv.b, s, false);
+    for (int q = 0; q < nsweeps; ++q) launch_sweep(m, level, Lv.b, s);
     cudaMemcpyAsync(dout, Lv.u, sizeof(double) * Lv.N, cudaMemcpyDeviceToDevice, s);
     m->solved = false;
   }
@@ -569,12 +580,16 @@ hhg_status hhg_adjoint_l2(hhg_mesh m, const hhg_solve_params* params, const unsi
 hhg_status hhg_profile_kernel(hhg_mesh m, int kernel, int precision, int reps, long long* units, double* bytes,
                               double* flops) {
   REQUIRE(m && units && bytes && flops, HHG_ERR_ARG, "NULL argument");
-  REQUIRE(kernel == 0 || kernel == 1, HHG_ERR_ARG, "kernel must be 0 or 1");
+  REQUIRE(kernel >= 0 && kernel <= 4, HHG_ERR_ARG, "kernel must be 0 .. 4");
   REQUIRE(precision == 0 || precision == 1, HHG_ERR_ARG, "precision must be 0 or 1");
   REQUIRE(reps >= 0 && reps <= 100000, HHG_ERR_ARG, "reps in [0, 100000]");
   DeviceGuard g(m->device);
   ENTER(m);
-  if (kernel == 1) {
+  if (kernel >= 2) {
+    REQUIRE(precision == 0, HHG_ERR_ARG, "the level probes 2 .. 4 are binary64");
+    REQUIRE(m->L >= 1, HHG_ERR_ARG, "the level probes need L >= 1");
+    launch_profile_level(m, kernel, reps, m->stream, units, bytes, flops);
+  } else if (kernel == 1) {
     REQUIRE(precision == 0, HHG_ERR_ARG, "the face-stage probe is binary64");
     launch_profile_face(m, reps, m->stream, units);
     *bytes = 0;

@@ -37,12 +37,15 @@ struct Prims {
   // per primitive: 1 / (assembled diagonal of its interior nodes) at unit level scale (0 if Dirichlet)
   double* d_pinv = nullptr;
   float* d_pinvf = nullptr;
+  // faces: in-plane couplings per face (8 slots, 6 used), unit level scale
+  double* d_fw = nullptr;
+  float* d_fwf = nullptr;
 };
 
 // nodes of the u window (planes k0-1 .. k1+1) of one staged interior tile, at most (a single plane
 // range may exceed it)
 constexpr int64_t kTileNodes = 8192;
-// dynamic shared memory a staged tile may use (tiles beyond it fall back to the list kernel)
+// dynamic shared memory a staged CTA may use (tiles beyond it fall back to the list kernel)
 constexpr size_t kMaxTileSmem = 200 * 1024;
 // spare values past the last node of every vector the staged kernel reads
 constexpr int64_t kVecPad = 16;
@@ -56,8 +59,8 @@ struct LevelData {
   std::vector<std::vector<int64_t>> icol_off;
   int2* d_icol = nullptr;
   // staged interior stage (3D): plane-range tiles {k0, k1, lo, hi} of group g, colour c at
-  // d_tiles[tile_off[g][c] .. + nranges); tile_smem4: largest dynamic shared memory of one tile
-  // with 4-byte values
+  // d_tiles[tile_off[g][c] .. + nranges); tile_smem4: largest shared memory (u and list windows) of
+  // one tile with 4-byte values
   std::vector<std::vector<int64_t>> tile_off;
   int nranges = 0;
   int4* d_tiles = nullptr;
@@ -70,10 +73,6 @@ struct LevelData {
   // face colour lists (3D): colour c entries [fcol_off[c], fcol_off[c+1]) of a | b << 16
   int64_t fcol_off[4] = {0, 0, 0, 0};
   int32_t* d_fcol = nullptr;
-  // the same split into rim (next to a face edge) and inner entries per colour
-  int64_t frim_off[4] = {0, 0, 0, 0}, fin_off[4] = {0, 0, 0, 0};
-  int32_t* d_frim = nullptr;
-  int32_t* d_fin = nullptr;
   // binary64 vectors
   double* u = nullptr;    // solution / correction
   double* b = nullptr;    // rhs M_l f_l (partial at interfaces)
@@ -93,6 +92,7 @@ struct LevelData {
 
 struct hhg_mesh_s {
   int dim = 2, L = 1, nc = 0, nv = 0, device = 0;
+  int sm_count = 152;  // streaming multiprocessors of the device (queried at creation)
   cudaStream_t stream = nullptr;  // caller's stream
   cudaStream_t cap = nullptr;     // internal stream used for graph capture
   cudaStream_t own = nullptr;     // stream owned by the mesh when the caller passes NULL
@@ -130,6 +130,7 @@ struct hhg_mesh_s {
   double* d_red = nullptr;        // per-cell reduction results (3 x n_cells)
   int* d_flag = nullptr;
   int* d_err = nullptr;  // sticky: set by a device-side bounded wait that ran out
+  void* d_face_work = nullptr;  // face-block scratch for levels whose faces exceed shared memory
   float* d_scal32 = nullptr;      // scratch scalars for the mixed path
   std::map<std::string, cudaGraphExec_t> graphs;
   std::map<std::string, long long> graph_kernels;  // kernel nodes per captured graph
@@ -155,7 +156,7 @@ enum class Prec { F64 = 0, F32 = 1, BF16 = 2, F16 = 3 };
 
 void launch_build_rhs(hhg_mesh_s* m, int l, cudaStream_t s);
 void launch_init_coarse(hhg_mesh_s* m, cudaStream_t s);
-void launch_sweep(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s, bool reverse);
+void launch_sweep(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s);
 void launch_residual(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s);
 // the same directly after a Gauss-Seidel sweep (last interior colour has zero residual)
 void launch_residual_after(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s, bool after_sweep);
@@ -163,7 +164,9 @@ void launch_restrict(hhg_mesh_s* m, int l, const double* fine, double* coarse, c
 void launch_prolong_add(hhg_mesh_s* m, int l, cudaStream_t s);
 void launch_fmg_prolong(hhg_mesh_s* m, int l, cudaStream_t s);
 void launch_coarse_solve(hhg_mesh_s* m, const double* rhs, cudaStream_t s);
-void launch_prolong(hhg_mesh_s* m, int l, const double* coarse, double* fine, cudaStream_t s);
+void launch_prolong(hhg_mesh_s* m, int l, const double* coarse, double* fine, cudaStream_t s,
+                    const double* minuend = nullptr);
+void launch_sub(hhg_mesh_s* m, const double* a, const double* b, double* x, int64_t n, cudaStream_t s);
 void launch_finite_check(hhg_mesh_s* m, const double* v, int64_t n, cudaStream_t s);
 // per-cell reductions on level L: out[T] = (a-b)^T M_T (a-b), b may be null
 void launch_mass_norm_sq(hhg_mesh_s* m, const double* a, const double* b, double* out, cudaStream_t s);

@@ -8,15 +8,15 @@
 
 namespace hhg {
 
-// One block per cell: deterministic shared-memory tree sum of the cell's node contributions.
-__global__ void __launch_bounds__(256) k_cell_sum(int64_t Nt, double scale, const double* __restrict__ contrib,
+// One block per cell: deterministic shared-memory tree sum of the cell's np partial sums.
+__global__ void __launch_bounds__(256) k_cell_sum(int64_t np, double scale, const double* __restrict__ part,
                                                   double* __restrict__ out) {
   grid_dependency_sync();
   __shared__ double sh[256];
   int T = blockIdx.x;
-  const double* c = contrib + (int64_t)T * Nt;
+  const double* c = part + (int64_t)T * np;
   double acc = 0;
-  for (int64_t q = threadIdx.x; q < Nt; q += 256) acc += c[q];
+  for (int64_t q = threadIdx.x; q < np; q += 256) acc += c[q];
   sh[threadIdx.x] = acc;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
@@ -24,6 +24,14 @@ __global__ void __launch_bounds__(256) k_cell_sum(int64_t Nt, double scale, cons
     __syncthreads();
   }
   if (threadIdx.x == 0) out[T] = scale * sh[0];
+}
+
+// x = a - b elementwise
+__global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ x,
+                      int64_t n) {
+  grid_dependency_sync();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = a[i] - b[i];
 }
 
 __global__ void k_finite(const double* __restrict__ v, int64_t n, int* __restrict__ flag) {
@@ -107,55 +115,51 @@ static void iface_stage(hhg_mesh_s* m, int l, const Prims& P, int nverts, int pa
   const LevelData& Lv = m->lv[l];
   double* du = Lv.tmp;  // residual scratch is free during a sweep (sized N_l >= the rim nodes)
   double ss = stiff_scale(DIM, Lv.n);
-  // Face stages with many nodes are DFMA-bound in binary64: one lane per node and only the nonzero
-  // stencil terms.  Smaller stages are latency-bound: copies spread over lanes, all loads together.
-  int64_t nodes = (int64_t)P.count * (cnt_rim + cnt_inner);
-  bool sparse = nverts == 3 && nodes >= kSparseFaceNodes;
-  int lanes = sparse ? 1 : iface_lanes(P.max_copies);
-  launch_iface<DIM, double, double, double>(lanes, sparse, P.count, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, nverts, parity,
+  // copies spread over lanes (the edge stages are latency-bound)
+  launch_iface<DIM, double, double, double>(iface_lanes(P.max_copies), P.count, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, nverts, parity,
                                             cnt_rim, cnt_inner, rim_list, inner_list, ctx(m, l), m->dS, ss, P.d_pinv,
                                             Vec<double, double>{u, nullptr}, CVec<double, double>{rhs, nullptr}, du,
                                             s);
 }
 
 template <int DIM>
-static void sweep_impl(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s, bool reverse) {
+static void sweep_impl(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s) {
   LevelData& Lv = m->lv[l];
   double* u = Lv.u;
   int n = Lv.n;
   double ss = stiff_scale(DIM, n);
-  // stage list: vertex, edge even, edge odd, [face colours], interior colours
-  int nst = 3 + (DIM == 3 ? 3 : 0) + m->n_colours;
-  for (int q = 0; q < nst; ++q) {
-    int st = reverse ? nst - 1 - q : q;
+  // stage list: vertex, edge even, edge odd, [face block], interior colours
+  const int nst = 3 + (DIM == 3 ? 1 : 0) + m->n_colours;
+  for (int st = 0; st < nst; ++st) {
     if (st == 0) {
       const Prims& P = m->verts;
       if (P.count)
-        hhg_launch(k_smooth_vertex<DIM, double, double, double>, blocks_for((int64_t)P.count * 32), kBlock, 0, s, 
-            P.count, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l), m->dS, ss, P.d_pinv, 1.0 / ss,
-            Vec<double, double>{u, nullptr}, CVec<double, double>{rhs, nullptr});
+        hhg_launch(k_smooth_vertex<DIM, double, double, double>, blocks_for((int64_t)P.count * 32), kBlock, 0, s,
+                   P.count, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l), m->dS, ss, P.d_pinv, 1.0 / ss,
+                   Vec<double, double>{u, nullptr}, CVec<double, double>{rhs, nullptr});
     } else if (st <= 2) {
       // stage 1: even local index (no coupling inside the stage); stage 2: odd, t = 1 and n-1 are rim
       int parity = (st == 2);
       int cnt_rim = parity ? (n == 2 ? 1 : 2) : 0;
       int cnt_inner = parity ? (n == 2 ? 0 : n / 2 - 2) : n / 2 - 1;
       iface_stage<DIM>(m, l, m->edges, 2, parity, cnt_rim, cnt_inner, nullptr, nullptr, u, rhs, s);
-    } else if (DIM == 3 && st <= 5) {
-      int c = st - 3;
-      iface_stage<DIM>(m, l, m->faces, 3, 0, (int)(Lv.frim_off[c + 1] - Lv.frim_off[c]),
-                       (int)(Lv.fin_off[c + 1] - Lv.fin_off[c]), Lv.d_frim + Lv.frim_off[c],
-                       Lv.d_fin + Lv.fin_off[c], u, rhs, s);
+    } else if (DIM == 3 && st == 3) {
+      // binary64 face-node pass over the outside couplings: sparse slot loop where DFMA-bound
+      bool sparse = (int64_t)m->faces.count * Lv.fcol_off[3] >= kSparseFaceNodes;
+      launch_face_block<double, double, double>(m->faces, Lv, ctx(m, l), m->dS, ss, m->faces.d_fw, m->faces.d_pinv,
+                                                Vec<double, double>{u, nullptr}, CVec<double, double>{rhs, nullptr},
+                                                Lv.tmp, (double*)m->d_face_work, sparse, s);
     } else {
-      int c = st - (DIM == 3 ? 6 : 3);
+      int c = st - (DIM == 3 ? 4 : 3);
       for (size_t gi = 0; gi < m->groups.size(); ++gi)
         if (c < m->groups[gi].m) interior_stage_dispatch<DIM>(m, l, (int)gi, c, u, rhs, s);
     }
   }
 }
 
-void launch_sweep(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s, bool reverse) {
-  if (m->dim == 2) sweep_impl<2>(m, l, rhs, s, reverse);
-  else sweep_impl<3>(m, l, rhs, s, reverse);
+void launch_sweep(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s) {
+  if (m->dim == 2) sweep_impl<2>(m, l, rhs, s);
+  else sweep_impl<3>(m, l, rhs, s);
 }
 
 template <int DIM, int PM>
@@ -223,10 +227,14 @@ void launch_fmg_prolong_g(hhg_mesh_s* m, int l, const double* g, double* w, cuda
 
 void launch_fmg_prolong(hhg_mesh_s* m, int l, cudaStream_t s) { launch_fmg_prolong_g(m, l, m->gL, m->lv[l].w, s); }
 
-void launch_prolong(hhg_mesh_s* m, int l, const double* coarse, double* fine, cudaStream_t s) {
+void launch_prolong(hhg_mesh_s* m, int l, const double* coarse, double* fine, cudaStream_t s, const double* minuend) {
   const LevelData& F = m->lv[l];
   dim3 grid(blocks_for(F.Nt), m->nc);
-  DISPATCH_DIM(m, k_prolong, grid, kBlock, 0, s, ctx(m, l), ctx(m, l - 1), coarse, fine);
+  DISPATCH_DIM(m, k_prolong, grid, kBlock, 0, s, ctx(m, l), ctx(m, l - 1), coarse, fine, minuend);
+}
+
+void launch_sub(hhg_mesh_s* m, const double* a, const double* b, double* x, int64_t n, cudaStream_t s) {
+  hhg_launch(k_sub, 4 * m->sm_count, kBlock, 0, s, a, b, x, n);
 }
 
 void launch_coarse_solve(hhg_mesh_s* m, const double* rhs, cudaStream_t s) {
@@ -249,13 +257,13 @@ void launch_coarse_solve(hhg_mesh_s* m, const double* rhs, cudaStream_t s) {
 }
 
 void launch_finite_check(hhg_mesh_s* m, const double* v, int64_t n, cudaStream_t s) {
-  hhg_launch(k_finite, 304, kBlock, 0, s, v, n, m->d_flag);
+  hhg_launch(k_finite, 2 * m->sm_count, kBlock, 0, s, v, n, m->d_flag);
 }
 
 static void cell_form(hhg_mesh_s* m, bool diff, const double* tab, double scale, const double* a, const double* b,
                       double* out, cudaStream_t s) {
   const LevelData& Lv = m->lv[m->L];
-  double* contrib = m->d_part;  // N_L doubles of scratch
+  double* contrib = m->d_part;  // per-block partial sums (cells x blocks <= N_L doubles)
   dim3 grid(blocks_for(Lv.Nt), m->nc);
   if (diff) {
     if (m->dim == 2) hhg_launch(k_node_form<2, true>, grid, kBlock, 0, s, ctx(m, m->L), tab, a, b, contrib);
@@ -264,7 +272,7 @@ static void cell_form(hhg_mesh_s* m, bool diff, const double* tab, double scale,
     if (m->dim == 2) hhg_launch(k_node_form<2, false>, grid, kBlock, 0, s, ctx(m, m->L), tab, a, b, contrib);
     else hhg_launch(k_node_form<3, false>, grid, kBlock, 0, s, ctx(m, m->L), tab, a, b, contrib);
   }
-  hhg_launch(k_cell_sum, m->nc, 256, 0, s, Lv.Nt, scale, contrib, out);
+  hhg_launch(k_cell_sum, m->nc, 256, 0, s, (int64_t)grid.x, scale, contrib, out);
 }
 
 void launch_mass_norm_sq(hhg_mesh_s* m, const double* a, const double* b, double* out, cudaStream_t s) {
@@ -321,11 +329,41 @@ void launch_restrict_rhs_chain(hhg_mesh_s* m, cudaStream_t s) {
 void launch_profile_face(hhg_mesh_s* m, int reps, cudaStream_t s, long long* units) {
   const int L = m->L;
   LevelData& Lv = m->lv[L];
-  *units = (long long)m->faces.count * (Lv.fcol_off[1] - Lv.fcol_off[0]);
+  *units = (long long)m->faces.count * Lv.fcol_off[3];
   if (m->dim != 3) return;
+  bool sparse = (int64_t)m->faces.count * Lv.fcol_off[3] >= kSparseFaceNodes;
   for (int r = 0; r < reps; ++r)
-    iface_stage<3>(m, L, m->faces, 3, 0, (int)(Lv.frim_off[1] - Lv.frim_off[0]), (int)(Lv.fin_off[1] - Lv.fin_off[0]),
-                   Lv.d_frim, Lv.d_fin, Lv.u, Lv.b, s);
+    launch_face_block<double, double, double>(m->faces, Lv, ctx(m, L), m->dS, stiff_scale(3, Lv.n), m->faces.d_fw,
+                                              m->faces.d_pinv, Vec<double, double>{Lv.u, nullptr},
+                                              CVec<double, double>{Lv.b, nullptr}, Lv.tmp, (double*)m->d_face_work,
+                                              sparse, s);
+}
+
+static int ndirs_of(int dim) { return dim == 2 ? 7 : 15; }
+
+// binary64 level-L probes: 2 prolongation-add, 3 residual (all nodes computed), 4 estimator mass form
+// of a difference vector (node form + per-cell sum)
+void launch_profile_level(hhg_mesh_s* m, int kernel, int reps, cudaStream_t s, long long* units, double* bytes,
+                          double* flops) {
+  const int L = m->L;
+  LevelData& Lv = m->lv[L];
+  const double N = (double)Lv.N, Nc = (double)m->lv[L - 1].N;
+  *units = (long long)Lv.N;
+  if (kernel == 2) {
+    *bytes = 8.0 * (2.0 * N + Nc);
+    *flops = 3.0 * N;
+  } else if (kernel == 3) {
+    *bytes = 8.0 * 3.0 * N;
+    *flops = (2.0 * (1 + 2 * __builtin_popcount(m->groups[0].pmask)) + 2.0) * N;
+  } else {
+    *bytes = 8.0 * 2.0 * N;
+    *flops = 2.0 * (ndirs_of(m->dim) + 1) / 2 * N + 2.0 * N;
+  }
+  for (int r = 0; r < reps; ++r) {
+    if (kernel == 2) launch_prolong_add(m, L, s);
+    else if (kernel == 3) launch_residual(m, L, Lv.b, s);
+    else launch_mass_norm_sq(m, Lv.u, nullptr, m->d_red, s);
+  }
 }
 
 void launch_profile_interior(hhg_mesh_s* m, int precision, int reps, cudaStream_t s, long long* units,
@@ -357,7 +395,7 @@ hhg_status preload_kernels() {
       (const void*)k_node_form<2, true>, (const void*)k_node_form<3, true>, (const void*)k_node_form<2, false>,
       (const void*)k_node_form<3, false>, (const void*)k_cell_sum, (const void*)k_apply_partial<2>,
       (const void*)k_apply_partial<3>, (const void*)k_sum_prims<2>, (const void*)k_sum_prims<3>,
-      (const void*)k_finite};
+      (const void*)k_finite, (const void*)k_sub};
   for (const void* f : fns) {
     cudaError_t e = cudaFuncGetAttributes(&fa, f);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");

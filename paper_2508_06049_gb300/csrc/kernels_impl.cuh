@@ -65,12 +65,9 @@ __device__ __forceinline__ void prim_position(int loc, int nverts, int n, int s,
 }
 
 // Stencil terms of one cell copy of an interface node (i,j,k): acc += sum_d S[t][d] u[g + off_d] over
-// the slots whose neighbour lies in the closure and whose entry is nonzero, bsum += rhs[g]; returns
-// g.  SPARSE: a loop over the set bits of that mask, so a warp whose lanes share the mask (nodes of
-// one primitive in one cell) issues only the nonzero terms (fewer binary64 instructions where the
-// stage is DFMA-bound, but one memory round trip per term).  Dense: all slots unrolled, loads issued
-// together (for latency-bound stages).
-template <int DIM, bool SPARSE, typename R, typename U, typename B>
+// the slots whose neighbour lies in the closure and whose entry is nonzero (all slots unrolled,
+// loads issued together), bsum += rhs[g]; returns g.
+template <int DIM, typename R, typename U, typename B>
 __device__ __forceinline__ int64_t copy_terms(const R* __restrict__ S, const uint16_t* __restrict__ nzs, int T, int n,
                                               int64_t Nt, int i, int j, int k, const CVec<R, U>& u,
                                               const CVec<R, B>& rhs, R& acc, R& bsum) {
@@ -81,22 +78,12 @@ __device__ __forceinline__ int64_t copy_terms(const R* __restrict__ S, const uin
   uint32_t vm = valid_dirs_tab(DIM, t) & nzs[T * kMaxTypes + t];
   const R* s = S + (size_t)T * kStencilStride + t * kMaxDirs;
   R a = s[0] * u.get(g);
-  if (SPARSE) {
-    PlaneBasis pb = plane_basis(DIM, n, k);
-    for (uint32_t mm = vm & ~1u; mm; mm &= mm - 1) {
-      int d = __ffs(mm) - 1;
-      int64_t o = dir_offset(DIM, d, pb.m, j, pb.Tm, pb.Tm1);
-      if (HHG_OOB(p + o, Nt, 32)) continue;
-      a += s[d] * u.get(g + o);
-    }
-  } else {
-    int64_t off[15];
-    neighbour_offsets(DIM, n, j, k, off);
-    mask_offsets(DIM, vm, off);
+  int64_t off[15];
+  neighbour_offsets(DIM, n, j, k, off);
+  mask_offsets(DIM, vm, off);
 #pragma unroll
-    for (int d = 1; d < ndirs<DIM>(); ++d)
-      if ((vm >> d & 1) && !HHG_OOB(p + off[d], Nt, 32)) a += s[d] * u.get(g + off[d]);
-  }
+  for (int d = 1; d < ndirs<DIM>(); ++d)
+    if ((vm >> d & 1) && !HHG_OOB(p + off[d], Nt, 32)) a += s[d] * u.get(g + off[d]);
   acc += a;
   bsum += rhs.get(g);
   return g;
@@ -123,15 +110,26 @@ __global__ void k_build_rhs(LevelCtx lc, int nL, int64_t NtL, int shift, const d
   }
   uint32_t vm = valid_dirs_tab(DIM, t);
   const double* s = Mst + (size_t)T * kStencilStride + t * kMaxDirs;
+  const double* f = fL + (int64_t)T * NtL;
   double acc = 0;
-  for (int d = 0; d < ndirs<DIM>(); ++d) {
-    if (!(vm >> d & 1)) continue;
-    int di, dj, dk;
-    dir_vec(DIM, d, di, dj, dk);
-    int64_t q = packed_index(DIM, nL, (int64_t)(i + di) << shift, (int64_t)(j + dj) << shift,
-                             (int64_t)(k + dk) << shift);
-    if (HHG_OOB(q, NtL, 71)) continue;
-    acc += s[d] * fL[(int64_t)T * NtL + q];
+  if (shift == 0) {  // level L itself: the level's own neighbour offsets
+    int64_t off[15];
+    neighbour_offsets(DIM, lc.n, j, k, off);
+    mask_offsets(DIM, vm, off);
+#pragma unroll
+    for (int d = 0; d < ndirs<DIM>(); ++d)
+      if ((vm >> d & 1) && !HHG_OOB(loc + off[d], NtL, 71)) acc += s[d] * f[loc + off[d]];
+  } else {
+#pragma unroll
+    for (int d = 0; d < ndirs<DIM>(); ++d) {
+      if (!(vm >> d & 1)) continue;
+      int di, dj, dk;
+      dir_vec(DIM, d, di, dj, dk);
+      int64_t q = packed_index(DIM, nL, (int64_t)(i + di) << shift, (int64_t)(j + dj) << shift,
+                               (int64_t)(k + dk) << shift);
+      if (HHG_OOB(q, NtL, 71)) continue;
+      acc += s[d] * f[q];
+    }
   }
   b[g] = mscale * acc;
 }
@@ -194,15 +192,16 @@ __global__ void __launch_bounds__(kBlock) k_smooth_interior(const int* __restric
   u.set(g, acc);
 }
 
-// The same interior colour stage (3D) with the cell's data staged in shared memory.  One CTA takes
-// one plane range [k0, k1] of one cell (tile = {k0, k1, lo, hi}): the u planes k0-1 .. k1+1 and
-// the b planes k0 .. k1 are contiguous in the packed layout, and the colour's list entries of those
-// planes are the contiguous list range [lo, hi); three bulk asynchronous copies (16-byte aligned
-// windows around them) bring them in, completing on one mbarrier, and the update then reads only
-// shared memory.  Neighbouring CTAs copy each other's boundary planes while those CTAs write
-// their own colour's nodes there; a proper colouring means such values are never used.
-// The vectors read here carry 16 bytes of padding past their last node.  A copy that does not
-// complete within the bounded wait sets *err and the CTA returns without updating.
+// The same interior colour stage (3D) with the cell's u values staged in shared memory.  One CTA
+// takes one plane range [k0, k1] of one cell (tile = {k0, k1, lo, hi}): the u planes k0-1 .. k1+1
+// are contiguous in the packed layout and the colour's list entries of those planes are the
+// contiguous list range [lo, hi); two bulk asynchronous copies (16-byte aligned windows around
+// them) bring both in, completing on one mbarrier, and the update reads its neighbours from shared
+// memory (b at the updated node from global memory).  Neighbouring CTAs copy each other's
+// boundary planes while those CTAs write their own colour's nodes there; a proper colouring means
+// such values are never used.  The vectors read here carry 16 bytes of padding past their last
+// node.  A copy that does not complete within the bounded wait sets *err and the CTA returns
+// without updating.
 constexpr int kBulkWaitTries = 1 << 20;
 
 template <int PM, typename R>
@@ -221,30 +220,28 @@ __global__ void __launch_bounds__(kBlock) k_smooth_interior_tiled(const int* __r
   const int64_t cell0 = (int64_t)T * lc.Nt;
   const int64_t tn = tet_size(n);
   const int64_t ua = tn - tet_size(n - tl.x + 1), ue = tn - tet_size(n - tl.y - 2);
-  const int64_t ba = tn - tet_size(n - tl.x), be = tn - tet_size(n - tl.y - 1);
-  const uintptr_t gu0 = (uintptr_t)(u + cell0 + ua), gb0 = (uintptr_t)(b + cell0 + ba), gl0 = (uintptr_t)(list + tl.z);
-  const uintptr_t au = gu0 & ~(uintptr_t)15, ab = gb0 & ~(uintptr_t)15, al = gl0 & ~(uintptr_t)15;
+  const uintptr_t gu0 = (uintptr_t)(u + cell0 + ua), gl0 = (uintptr_t)(list + tl.z);
+  const uintptr_t au = gu0 & ~(uintptr_t)15, al = gl0 & ~(uintptr_t)15;
   const uint32_t nu = (uint32_t)((((uintptr_t)(u + cell0 + ue) - au) + 15) & ~(uintptr_t)15);
-  const uint32_t nb = (uint32_t)((((uintptr_t)(b + cell0 + be) - ab) + 15) & ~(uintptr_t)15);
   const uint32_t nl = (uint32_t)((((uintptr_t)(list + tl.w) - al) + 15) & ~(uintptr_t)15);
   R* su = (R*)(smem + 16);
-  R* sb = (R*)(smem + 16 + nu);
-  int2* sl = (int2*)(smem + 16 + nu + nb);
+  int2* sl = (int2*)(smem + 16 + nu);
   const uint32_t bar = smem_addr(smem);
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
-    mbar_arrive_expect_tx(bar, nu + nb + nl);
+    mbar_arrive_expect_tx(bar, nu + nl);
     bulk_g2s(smem_addr(su), (const void*)au, nu, bar);
-    bulk_g2s(smem_addr(sb), (const void*)ab, nb, bar);
     bulk_g2s(smem_addr(sl), (const void*)al, nl, bar);
   }
   __syncthreads();
-  if (!mbar_wait_bounded(bar, 0, kBulkWaitTries)) {
+  // the outcome of the bounded wait is made uniform across the CTA before anyone acts on it
+  const int ok = __syncthreads_and(mbar_wait_bounded(bar, 0, kBulkWaitTries));
+  if (!ok) {
     if (threadIdx.x == 0) atomicOr(err, 1);
     mbar_wait_bounded(bar, 0, kBulkWaitTries);  // let copies in flight land before the CTA exits
     return;
   }
-  const int upad = (int)((gu0 - au) / sizeof(R)), bpad = (int)((gb0 - ab) / sizeof(R));
+  const int upad = (int)((gu0 - au) / sizeof(R));
   const int lpad = (int)((gl0 - al) / sizeof(int2));
   const R* t = tnorm + (size_t)T * 16;
   R tv[15];
@@ -263,7 +260,7 @@ __global__ void __launch_bounds__(kBlock) k_smooth_interior_tiled(const int* __r
       if ((PM >> ((d - 1) >> 1)) & 1) bad |= HHG_OOB(c + off[d], (int64_t)(nu / sizeof(R)), 44);
     if (bad) continue;
 #endif
-    R acc = sb[bpad + (int)(q - ba)] * il;
+    R acc = b[cell0 + q] * il;
 #pragma unroll
     for (int qq = 0; qq < 7; ++qq) {
       if (PM >> qq & 1) {
@@ -295,7 +292,7 @@ __global__ void k_smooth_vertex(int nprim, const int* __restrict__ ptr, const in
   for (int c = c0 + lane; c < c1; c += 32) {
     int i, j, k;
     prim_position(locv[c], 1, lc.n, 0, 0, i, j, k);
-    copy_terms<DIM, false>(S, lc.nzs, cell[c], lc.n, lc.Nt, i, j, k, uc, rhs, acc, bs);
+    copy_terms<DIM>(S, lc.nzs, cell[c], lc.n, lc.Nt, i, j, k, uc, rhs, acc, bs);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -313,14 +310,14 @@ __global__ void k_smooth_vertex(int nprim, const int* __restrict__ ptr, const in
   }
 }
 
-// Edge (parity) and face (colour) stages.  Every node of a stage is updated from the values at the
-// start of the stage.  Nodes of one stage can couple only next to a shared macro vertex (odd edge
-// nodes t = 1, n-1) or a shared macro edge (face nodes with a = 1, b = 1 or a + b = n-1): these "rim"
-// nodes are computed into du and applied by a second kernel.  All other ("inner") nodes of the stage
-// have no neighbour in the stage, so one pass updates them in place.
+// Edge stages (even, then odd edge-local index).  Every node of a stage is updated from the values
+// at the start of the stage.  Nodes of one stage can couple only next to a shared macro vertex (odd
+// edge nodes t = 1, n-1): these "rim" nodes are computed into du and applied by a second kernel.
+// All other ("inner") nodes of the stage have no neighbour in the stage, so one pass updates them
+// in place.  (The face stages are the face block further down.)
 //
-// Position of entry q of a stage: edges: rim q -> t in {1, n-1} (odd stage only), inner q ->
-// t = 2q+3 (odd) or 2q+2 (even); faces: (a, b) from the stage's rim or inner list.
+// Position of entry q of a stage: rim q -> t in {1, n-1} (odd stage only), inner q -> t = 2q+3
+// (odd) or 2q+2 (even); for a primitive with three vertices (a, b) from the given list.
 __device__ __forceinline__ void stage_position(int nverts, int parity, bool rim, int n, int q,
                                                const int32_t* __restrict__ list, int& s, int& t) {
   if (nverts == 2) {
@@ -334,12 +331,12 @@ __device__ __forceinline__ void stage_position(int nverts, int parity, bool rim,
   }
 }
 
-// One interface stage (edge parity or face colour) on the nodes of nprim primitives.  G lanes
+// One interface stage (edge parity) on the nodes of nprim primitives.  G lanes
 // (a power of two dividing 32) serve one node: lane r takes the copies ptr[e] + r, + r + G, ...,
 // and the partial residuals and diagonals are summed over the lanes by an xor butterfly, so every
 // lane holds the same sum.  Rim nodes (those that can neighbour another node of the same stage in
 // some cell) store their correction in du for k_iface_apply; inner nodes are updated in place.
-template <int DIM, int G, bool SPARSE, typename R, typename U, typename B>
+template <int DIM, int G, typename R, typename U, typename B>
 __global__ void k_iface_stage(int nprim, int nverts, int parity, int cnt_rim, int cnt_inner,
                               const int32_t* __restrict__ rim_list, const int32_t* __restrict__ inner_list,
                               const int* __restrict__ ptr, const int* __restrict__ cell, const int* __restrict__ locv,
@@ -373,7 +370,7 @@ __global__ void k_iface_stage(int nprim, int nverts, int parity, int cnt_rim, in
     for (int c = ptr[e] + lane; c < ptr[e + 1]; c += G) {
       int i, j, k;
       prim_position(locv[c], nverts, lc.n, s, t, i, j, k);
-      int64_t g = copy_terms<DIM, SPARSE>(S, lc.nzs, cell[c], lc.n, lc.Nt, i, j, k, uc, rhs, acc, bs);
+      int64_t g = copy_terms<DIM>(S, lc.nzs, cell[c], lc.n, lc.Nt, i, j, k, uc, rhs, acc, bs);
       if (g0 < 0) g0 = g;
     }
   }
@@ -429,8 +426,9 @@ __global__ void k_iface_apply(int nprim, int nverts, int parity, int cnt_rim, co
   }
 }
 
-// binary64 face stages with at least this many nodes run one lane per node with the sparse stencil
-// loop (the 384-tet cube has 5.6e5 face nodes per colour at level 6, 1.3e5 at 5, 3.0e4 at 4)
+// binary64 face blocks with at least this many face nodes visit only the nonzero outside couplings
+// (a loop over set bits: fewer DFMA instructions, one memory round trip per term); smaller ones
+// unroll all slots (the 384-tet cube has 1.7e6 face nodes at level 6, 4.0e5 at 5, 9.1e4 at 4)
 constexpr int64_t kSparseFaceNodes = 100000;
 
 // lanes per interface node: the copy count rounded up to a power of two, at most a warp
@@ -441,13 +439,13 @@ inline int iface_lanes(int max_copies) {
 }
 
 // launch one interface stage over the primitives of P, then (if it has rim nodes) its apply phase
-template <int DIM, int G, bool SPARSE, typename R, typename U, typename B>
+template <int DIM, int G, typename R, typename U, typename B>
 void launch_iface_g(int nprim, const int* ptr, const int* cell, const int* locv, const unsigned char* dir,
                     int nverts, int parity, int cnt_rim, int cnt_inner, const int32_t* rim_list,
                     const int32_t* inner_list, LevelCtx lc, const R* S, R ss, const R* pinv, Vec<R, U> u,
                     CVec<R, B> rhs, R* du, cudaStream_t s) {
   int64_t nodes = (int64_t)nprim * (cnt_rim + cnt_inner);
-  hhg_launch(k_iface_stage<DIM, G, SPARSE, R, U, B>, blocks_for(nodes * G), kBlock, 0, s, 
+  hhg_launch(k_iface_stage<DIM, G, R, U, B>, blocks_for(nodes * G), kBlock, 0, s, 
       nprim, nverts, parity, cnt_rim, cnt_inner, rim_list, inner_list, ptr, cell, locv, dir, lc, S, ss, pinv,
       (R)1 / ss, u, rhs, du);
   if (cnt_rim > 0)
@@ -456,26 +454,235 @@ void launch_iface_g(int nprim, const int* ptr, const int* cell, const int* locv,
 }
 
 template <int DIM, typename R, typename U, typename B>
-void launch_iface(int lanes, bool sparse, int nprim, const int* ptr, const int* cell, const int* locv,
-                  const unsigned char* dir, int nverts, int parity, int cnt_rim, int cnt_inner,
-                  const int32_t* rim_list, const int32_t* inner_list, LevelCtx lc, const R* S, R ss, const R* pinv,
-                  Vec<R, U> u, CVec<R, B> rhs, R* du, cudaStream_t s) {
-#define HHG_IFACE_G(GL, SP)                                                                                        \
-  launch_iface_g<DIM, GL, SP, R, U, B>(nprim, ptr, cell, locv, dir, nverts, parity, cnt_rim, cnt_inner, rim_list, \
-                                       inner_list, lc, S, ss, pinv, u, rhs, du, s)
-  if (sparse && lanes == 1) {
-    HHG_IFACE_G(1, true);
-    return;
-  }
+void launch_iface(int lanes, int nprim, const int* ptr, const int* cell, const int* locv, const unsigned char* dir,
+                  int nverts, int parity, int cnt_rim, int cnt_inner, const int32_t* rim_list,
+                  const int32_t* inner_list, LevelCtx lc, const R* S, R ss, const R* pinv, Vec<R, U> u,
+                  CVec<R, B> rhs, R* du, cudaStream_t s) {
+#define HHG_IFACE_G(GL)                                                                                          \
+  launch_iface_g<DIM, GL, R, U, B>(nprim, ptr, cell, locv, dir, nverts, parity, cnt_rim, cnt_inner, rim_list, \
+                                   inner_list, lc, S, ss, pinv, u, rhs, du, s)
   switch (lanes) {
-    case 1: HHG_IFACE_G(1, false); break;
-    case 2: HHG_IFACE_G(2, false); break;
-    case 4: HHG_IFACE_G(4, false); break;
-    case 8: HHG_IFACE_G(8, false); break;
-    case 16: HHG_IFACE_G(16, false); break;
-    default: HHG_IFACE_G(32, false); break;
+    case 1: HHG_IFACE_G(1); break;
+    case 2: HHG_IFACE_G(2); break;
+    case 4: HHG_IFACE_G(4); break;
+    case 8: HHG_IFACE_G(8); break;
+    case 16: HHG_IFACE_G(16); break;
+    default: HHG_IFACE_G(32); break;
   }
 #undef HHG_IFACE_G
+}
+
+// ---------------------------------------------------------------- face block (3D, row 3)
+//
+// The three face colours form one block: every macro face is smoothed on its own, Gauss-Seidel over
+// its interior nodes in colour order (a + 2b) mod 3, with every node outside the face (edges,
+// vertices, cell interiors, the nodes of other faces) at its value from the start of the block.
+// Two kernels: k_face_ext sums, per face node, b - A u over the couplings that leave the face
+// (over both cell copies), from the values at the start of the block; k_face_gs then runs the
+// colour sweeps of one face in one CTA on the face's own values held in shared memory, using the
+// face's in-plane couplings (summed over its copies), and writes the result to every copy.
+// Face-interior nodes (a, b >= 1, a + b <= n - 1) are indexed (a, b) -> face_pos in the
+// per-face vectors.
+
+__device__ __forceinline__ int face_pos(int n, int a, int b) {
+  return (b - 1) * (n - 2) - (b - 1) * (b - 2) / 2 + (a - 1);
+}
+
+__device__ __forceinline__ bool face_interior(int n, int a, int b) { return a >= 1 && b >= 1 && a + b <= n - 1; }
+
+// in-plane directions of a face in its local (a, b) coordinates
+__device__ __forceinline__ void face_dir(int q, int& da, int& db) {
+  da = (q == 0 || q == 4) ? 1 : ((q == 1 || q == 5) ? -1 : 0);
+  db = (q == 2 || q == 5) ? 1 : ((q == 3 || q == 4) ? -1 : 0);
+}
+
+// stencil slot of lattice vector v (0 if v is not a lattice direction)
+__device__ __forceinline__ int slot_of_vec(int di, int dj, int dk) {
+#pragma unroll
+  for (int s = 1; s < 15; ++s) {
+    int a, b, c;
+    dir_vec(3, s, a, b, c);
+    if (a == di && b == dj && c == dk) return s;
+  }
+  return 0;
+}
+
+// cell-local slot of face direction q for the copy whose local face vertices are packed in loc
+__device__ __forceinline__ int face_dir_slot(int loc, int q) {
+  int a0 = loc & 3, a1 = (loc >> 2) & 3, a2 = (loc >> 4) & 3;
+  int x0, y0, z0, x1, y1, z1, x2, y2, z2;
+  local_vertex_vec(a0, x0, y0, z0);
+  local_vertex_vec(a1, x1, y1, z1);
+  local_vertex_vec(a2, x2, y2, z2);
+  int da, db;
+  face_dir(q, da, db);
+  return slot_of_vec(da * (x1 - x0) + db * (x2 - x0), da * (y1 - y0) + db * (y2 - y0), da * (z1 - z0) + db * (z2 - z0));
+}
+
+template <int G, bool SPARSE, typename R, typename U, typename B>
+__global__ void k_face_ext(int nprim, int nf, const int32_t* __restrict__ fnodes, const int* __restrict__ ptr,
+                           const int* __restrict__ cell, const int* __restrict__ locv,
+                           const unsigned char* __restrict__ dir, LevelCtx lc, const R* __restrict__ S, R sscale,
+                           CVec<R, U> u, CVec<R, B> rhs, R* __restrict__ E) {
+  grid_dependency_sync();
+  int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int lane = (int)(gid & (G - 1));
+  int64_t tid = gid / G;
+  bool active = tid < (int64_t)nprim * nf;
+  int e = 0, a = 0, b = 0;
+  if (active) {
+    e = (int)(tid / nf);
+    int32_t ab = fnodes[tid % nf];
+    a = ab & 0xffff;
+    b = ab >> 16;
+    if (dir[e]) active = false;
+  }
+  R acc = 0, bs = 0;
+  if (active) {
+    const int n = lc.n;
+    for (int c = ptr[e] + lane; c < ptr[e + 1]; c += G) {
+      int loc = locv[c];
+      int i, j, k;
+      prim_position(loc, 3, n, a, b, i, j, k);
+      // leave out the node itself and its in-plane neighbours that are face-interior nodes
+      uint32_t excl = 1u;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        int da, db;
+        face_dir(q, da, db);
+        if (face_interior(n, a + da, b + db)) excl |= 1u << face_dir_slot(loc, q);
+      }
+      const int T = cell[c];
+      int t = boundary_type(3, n, i, j, k);
+      int64_t p = packed_index(3, n, i, j, k);
+      if (HHG_OOB(p, lc.Nt, 33)) continue;
+      int64_t g = (int64_t)T * lc.Nt + p;
+      uint32_t vm = valid_dirs_tab(3, t) & lc.nzs[T * kMaxTypes + t] & ~excl;
+      const R* s = S + (size_t)T * kStencilStride + t * kMaxDirs;
+      R x = 0;
+      if (SPARSE) {
+        PlaneBasis pb = plane_basis(3, n, k);
+        for (uint32_t mm = vm; mm; mm &= mm - 1) {
+          int d = __ffs(mm) - 1;
+          int64_t o = dir_offset(3, d, pb.m, j, pb.Tm, pb.Tm1);
+          if (HHG_OOB(p + o, lc.Nt, 34)) continue;
+          x += s[d] * u.get(g + o);
+        }
+      } else {
+        int64_t off[15];
+        neighbour_offsets(3, n, j, k, off);
+        mask_offsets(3, vm, off);
+#pragma unroll
+        for (int d = 1; d < 15; ++d)
+          if ((vm >> d & 1) && !HHG_OOB(p + off[d], lc.Nt, 34)) x += s[d] * u.get(g + off[d]);
+      }
+      acc += x;
+      bs += rhs.get(g);
+    }
+  }
+#pragma unroll
+  for (int w = 1; w < G; w <<= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, w);
+    bs += __shfl_xor_sync(0xffffffffu, bs, w);
+  }
+  if (active && lane == 0) E[(int64_t)e * nf + face_pos(lc.n, a, b)] = bs - sscale * acc;
+}
+
+// One CTA per face.  fcol: colour offsets of fnodes (colour c entries [fcol.c, fcol.c+1)); W: the
+// face's six in-plane couplings (unit level scale, summed over copies); pinv: 1 / diagonal (unit
+// scale); isscale = 1 / level scale.  work: 2 nf values of scratch per face when they do not fit
+// in shared memory (nullptr: shared memory).
+template <typename R, typename U>
+__global__ void __launch_bounds__(kBlock) k_face_gs(int nf, int4 fcol, const int32_t* __restrict__ fnodes,
+                                                    const int* __restrict__ ptr, const int* __restrict__ cell,
+                                                    const int* __restrict__ locv, const unsigned char* __restrict__ dir,
+                                                    LevelCtx lc, const R* __restrict__ W, const R* __restrict__ pinv,
+                                                    R isscale, Vec<R, U> u, const R* __restrict__ E, R* work) {
+  grid_dependency_sync();
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int e = blockIdx.x;
+  if (dir[e]) return;  // uniform across the CTA
+  const int n = lc.n;
+  R* uf = work ? work + (int64_t)e * 2 * nf : (R*)smem;
+  R* ef = uf + nf;
+  const int c0 = ptr[e];
+  const int loc0 = locv[c0];
+  const int64_t base0 = (int64_t)cell[c0] * lc.Nt;
+  for (int q = threadIdx.x; q < nf; q += blockDim.x) {
+    int32_t ab = fnodes[q];
+    int a = ab & 0xffff, b = ab >> 16;
+    int i, j, k;
+    prim_position(loc0, 3, n, a, b, i, j, k);
+    int pos = face_pos(n, a, b);
+    int64_t p = packed_index(3, n, i, j, k);
+    uf[pos] = HHG_OOB(p, lc.Nt, 35) ? (R)0 : u.get(base0 + p);
+    ef[pos] = E[(int64_t)e * nf + pos] * isscale;
+  }
+  R w[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) w[q] = W[(int64_t)e * 8 + q];
+  const R pv = pinv[e];
+  __syncthreads();
+  const int cb[4] = {fcol.x, fcol.y, fcol.z, fcol.w};
+  for (int col = 0; col < 3; ++col) {
+    for (int q = cb[col] + threadIdx.x; q < cb[col + 1]; q += blockDim.x) {
+      int32_t ab = fnodes[q];
+      int a = ab & 0xffff, b = ab >> 16;
+      int pos = face_pos(n, a, b);
+      R v = ef[pos];
+#pragma unroll
+      for (int d = 0; d < 6; ++d) {
+        int da, db;
+        face_dir(d, da, db);
+        if (face_interior(n, a + da, b + db)) v -= w[d] * uf[face_pos(n, a + da, b + db)];
+      }
+      uf[pos] = v * pv;
+    }
+    __syncthreads();
+  }
+  for (int c = c0; c < ptr[e + 1]; ++c) {
+    const int loc = locv[c];
+    const int64_t base = (int64_t)cell[c] * lc.Nt;
+    for (int q = threadIdx.x; q < nf; q += blockDim.x) {
+      int32_t ab = fnodes[q];
+      int a = ab & 0xffff, b = ab >> 16;
+      int i, j, k;
+      prim_position(loc, 3, n, a, b, i, j, k);
+      int64_t p = packed_index(3, n, i, j, k);
+      if (HHG_OOB(p, lc.Nt, 36)) continue;
+      u.set(base + p, uf[face_pos(n, a, b)]);
+    }
+  }
+}
+
+// Launch the face block on one level: E in `E` (P.count x nf values), the per-face sweeps in shared
+// memory when 2 nf values fit (else in `work`, P.count x 2 nf values).
+template <typename R, typename U, typename B>
+void launch_face_block(const Prims& P, const LevelData& Lv, LevelCtx lc, const R* S, R ss, const R* W,
+                       const R* pinv, Vec<R, U> u, CVec<R, B> rhs, R* E, R* work, bool sparse, cudaStream_t s) {
+  const int nf = (int)Lv.fcol_off[3];
+  if (P.count == 0 || nf == 0) return;
+  const int64_t nodes = (int64_t)P.count * nf;
+  CVec<R, U> uc{u.p, u.scale};
+  const int G = iface_lanes(P.max_copies);
+#define HHG_FACE_EXT(GL, SP)                                                                                       \
+  hhg_launch(k_face_ext<GL, SP, R, U, B>, blocks_for(nodes * GL), kBlock, 0, s, P.count, nf, Lv.d_fcol, P.d_ptr, \
+             P.d_cell, P.d_loc, P.d_dir, lc, S, ss, uc, rhs, E)
+  if (G == 1) {
+    if (sparse) HHG_FACE_EXT(1, true);
+    else HHG_FACE_EXT(1, false);
+  } else {
+    if (sparse) HHG_FACE_EXT(2, true);
+    else HHG_FACE_EXT(2, false);
+  }
+#undef HHG_FACE_EXT
+  const size_t smem = 2 * (size_t)nf * sizeof(R);
+  const bool fits = smem <= kMaxTileSmem;
+  if (fits && smem > 48 * 1024)
+    cudaFuncSetAttribute(k_face_gs<R, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxTileSmem);
+  int4 fcol = make_int4((int)Lv.fcol_off[0], (int)Lv.fcol_off[1], (int)Lv.fcol_off[2], (int)Lv.fcol_off[3]);
+  hhg_launch(k_face_gs<R, U>, (unsigned)P.count, kBlock, fits ? smem : 0, s, nf, fcol, Lv.d_fcol, P.d_ptr, P.d_cell,
+             P.d_loc, P.d_dir, lc, W, pinv, (R)1 / ss, u, (const R*)E, fits ? (R*)nullptr : work);
 }
 
 // ---------------------------------------------------------------- residual, restriction (row 4)
@@ -655,14 +862,18 @@ __global__ void k_fmg_prolong(LevelCtx fc, LevelCtx cc, int nL, int64_t NtL, int
 
 // plain interpolation v_f = I v_c (all nodes)
 template <int DIM>
-__global__ void k_prolong(LevelCtx fc, LevelCtx cc, const double* __restrict__ vc, double* __restrict__ vf) {
+// vf = I vc, or vf = minuend - I vc when minuend is given (the estimator's difference u_L - I w)
+__global__ void k_prolong(LevelCtx fc, LevelCtx cc, const double* __restrict__ vc, double* __restrict__ vf,
+                          const double* __restrict__ minuend) {
   grid_dependency_sync();
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (loc >= fc.Nt) return;
   int T = blockIdx.y;
   int i, j, k;
   decode(fc.ijk[loc], i, j, k);
-  vf[(int64_t)T * fc.Nt + loc] = interp<DIM, double>(cc, T, i, j, k, CVec<double, double>{vc, nullptr});
+  int64_t g = (int64_t)T * fc.Nt + loc;
+  double v = interp<DIM, double>(cc, T, i, j, k, CVec<double, double>{vc, nullptr});
+  vf[g] = minuend ? minuend[g] - v : v;
 }
 
 // ---------------------------------------------------------------- direct coarse solve (row 5)
@@ -688,7 +899,7 @@ __global__ void __launch_bounds__(1024) k_coarse(int n0f, const int* __restrict_
       for (int c = ptr[v] + lane; c < ptr[v + 1]; c += 32) {
         int i, j, k;
         prim_position(locv[c], 1, lc.n, 0, 0, i, j, k);
-        copy_terms<DIM, false>(S, lc.nzs, cell[c], lc.n, lc.Nt, i, j, k, uc, rc, acc, bs);
+        copy_terms<DIM>(S, lc.nzs, cell[c], lc.n, lc.Nt, i, j, k, uc, rc, acc, bs);
       }
       double res = bs - acc;  // level 0: unit stiffness scale
 #pragma unroll
@@ -704,73 +915,85 @@ __global__ void __launch_bounds__(1024) k_coarse(int n0f, const int* __restrict_
     for (int c = lane; c < n0f; c += 32) acc += a[c] * r[c];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      int v = cf[row];
-      for (int c = ptr[v]; c < ptr[v + 1]; ++c) {
-        int i, j, k;
-        prim_position(locv[c], 1, lc.n, 0, 0, i, j, k);
-        int64_t p = packed_index(DIM, lc.n, i, j, k);
-        if (HHG_OOB(p, lc.Nt, 93)) continue;
-        u[(int64_t)cell[c] * lc.Nt + p] += acc;
-      }
+    // every lane holds the sum: the lanes update the vertex's copies
+    int v = cf[row];
+    for (int c = ptr[v] + lane; c < ptr[v + 1]; c += 32) {
+      int i, j, k;
+      prim_position(locv[c], 1, lc.n, 0, 0, i, j, k);
+      int64_t p = packed_index(DIM, lc.n, i, j, k);
+      if (HHG_OOB(p, lc.Nt, 93)) continue;
+      u[(int64_t)cell[c] * lc.Nt + p] += acc;
     }
   }
 }
 
 // ---------------------------------------------------------------- reductions (row 8, row 11)
 
-// Per node p of a cell's closure, the symmetric-form contribution
+// Per node p of a cell's closure (one node per thread, one grid row per cell), the symmetric-form
+// contribution, summed over the block into part[cell][block]; the per-node form:
 //   c_p = S[t][0] x_p y_p + sum_{d positive, valid} S[t][d] (x_p y_{p+d} + x_{p+d} y_p),
 // with x = y = a - b (b may be null) for the mass form, or x = a, y = b for a bilinear form.  Summed
 // over the closure this is x^T S_T y, because the partial stencil of a cell is symmetric (the entry
 // p->p+d seen from p equals the entry p+d->p seen from p+d: both sum the cell's elements on that
-// edge), so each lattice edge is visited once.  Written to a level-L scratch vector; k_cell_sum adds
-// each cell's contributions in a fixed order.
+// edge), so each lattice edge is visited once.  The block sums land in a scratch vector (cells x
+// blocks); k_cell_sum adds each cell's block sums in a fixed order.
 template <int DIM, bool DIFF>
-__global__ void k_node_form(LevelCtx lc, const double* __restrict__ tab, const double* __restrict__ a,
-                            const double* __restrict__ b, double* __restrict__ contrib) {
+__global__ void __launch_bounds__(kBlock) k_node_form(LevelCtx lc, const double* __restrict__ tab,
+                                                      const double* __restrict__ a, const double* __restrict__ b,
+                                                      double* __restrict__ part) {
   grid_dependency_sync();
+  __shared__ double wsum[kBlock / 32];
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (loc >= lc.Nt) return;
   int T = blockIdx.y;
-  int i, j, k;
-  decode(lc.ijk[loc], i, j, k);
-  int t = boundary_type(DIM, lc.n, i, j, k);
-  if (HHG_OOB(t, kMaxTypes, 12)) return;
-  int64_t g = (int64_t)T * lc.Nt + loc;
-  int64_t off[15];
-  neighbour_offsets(DIM, lc.n, j, k, off);
-  uint32_t vm = valid_dirs_tab(DIM, t);
-  mask_offsets(DIM, vm, off);
-  const double* s = tab + (size_t)T * kStencilStride + t * kMaxDirs;
-  double xp, yp;
-  if (DIFF) {
-    xp = a[g];
-    if (b) xp -= b[g];
-    yp = xp;
-  } else {
-    xp = a[g];
-    yp = b[g];
-  }
-  // x_p (M y)_p restricted to the half stencil: s0 x_p y_p + sum_{+d} s_d (x_p y_q + x_q y_p),
-  // grouped as x_p (s0 y_p + sum s_d y_q) + y_p sum s_d x_q (one accumulator when x = y)
-  double ay = 0, ax = 0;
-#pragma unroll
-  for (int q = 0; q < npairs<DIM>(); ++q) {
-    int d = 2 * q + 1;
-    if (!(vm >> d & 1)) continue;
-    if (HHG_OOB(loc + off[d], lc.Nt, 13)) continue;
+  double sum = 0;
+  if (loc < lc.Nt) {
+    int i, j, k;
+    decode(lc.ijk[loc], i, j, k);
+    int t = boundary_type(DIM, lc.n, i, j, k);
+    int64_t g = (int64_t)T * lc.Nt + loc;
+    int64_t off[15];
+    neighbour_offsets(DIM, lc.n, j, k, off);
+    uint32_t vm = valid_dirs_tab(DIM, t);
+    mask_offsets(DIM, vm, off);
+    const double* s = tab + (size_t)T * kStencilStride + t * kMaxDirs;
+    double xp, yp;
     if (DIFF) {
-      double xq = a[g + off[d]];
-      if (b) xq -= b[g + off[d]];
-      ay += s[d] * xq;
+      xp = a[g];
+      if (b) xp -= b[g];
+      yp = xp;
     } else {
-      ay += s[d] * b[g + off[d]];
-      ax += s[d] * a[g + off[d]];
+      xp = a[g];
+      yp = b[g];
     }
+    // x_p (M y)_p restricted to the half stencil: s0 x_p y_p + sum_{+d} s_d (x_p y_q + x_q y_p),
+    // grouped as x_p (s0 y_p + sum s_d y_q) + y_p sum s_d x_q (one accumulator when x = y)
+    double ay = 0, ax = 0;
+#pragma unroll
+    for (int q = 0; q < npairs<DIM>(); ++q) {
+      int d = 2 * q + 1;
+      if (!(vm >> d & 1)) continue;
+      if (HHG_OOB(loc + off[d], lc.Nt, 13)) continue;
+      if (DIFF) {
+        double xq = a[g + off[d]];
+        if (b) xq -= b[g + off[d]];
+        ay += s[d] * xq;
+      } else {
+        ay += s[d] * b[g + off[d]];
+        ax += s[d] * a[g + off[d]];
+      }
+    }
+    sum = DIFF ? xp * (s[0] * xp + 2.0 * ay) : xp * (s[0] * yp + ay) + yp * ax;
   }
-  double sum = DIFF ? xp * (s[0] * xp + 2.0 * ay) : xp * (s[0] * yp + ay) + yp * ax;
-  contrib[g] = sum;
+  // deterministic block sum: warp butterflies, then the warp sums in order
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wsum[w];
+    part[(int64_t)T * gridDim.x + blockIdx.x] = tot;
+  }
 }
 
 // ---------------------------------------------------------------- operators for testing / adjoint

@@ -144,16 +144,15 @@ __global__ void __launch_bounds__(1024) k_coarse_mixed(int n0f, const int* __res
     for (int c = lane; c < n0f; c += 32) acc += a[c] * r[c];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      int v = cf[row];
-      for (int c = ptr[v]; c < ptr[v + 1]; ++c) {
-        int i, j, k;
-        prim_position(locv[c], 1, lc.n, 0, 0, i, j, k);
-        int64_t p = packed_index(DIM, lc.n, i, j, k);
-        if (HHG_OOB(p, lc.Nt, 96)) continue;
-        int64_t g = (int64_t)cell[c] * lc.Nt + p;
-        u.set(g, (float)((double)u.get(g) + acc));
-      }
+    // every lane holds the sum: the lanes update the vertex's copies
+    int v = cf[row];
+    for (int c = ptr[v] + lane; c < ptr[v + 1]; c += 32) {
+      int i, j, k;
+      prim_position(locv[c], 1, lc.n, 0, 0, i, j, k);
+      int64_t p = packed_index(DIM, lc.n, i, j, k);
+      if (HHG_OOB(p, lc.Nt, 96)) continue;
+      int64_t g = (int64_t)cell[c] * lc.Nt + p;
+      u.set(g, (float)((double)u.get(g) + acc));
     }
   }
 }
@@ -178,12 +177,12 @@ static void interior32(hhg_mesh_s* m, int l, int gi, int colour, U* u, const flo
   const Group& G = m->groups[gi];
   int64_t a = Lv.icol_off[gi][colour], b = Lv.icol_off[gi][colour + 1];
   if (b <= a || G.cells.empty()) return;
-  // 3D binary32 values: the stage staged through shared memory, one CTA per plane range and cell
-  if (DIM == 3 && std::is_same<U, float>::value && Lv.nranges > 0 && Lv.tile_smem4 <= kMaxTileSmem) {
+  // 3D binary32 values: the stage with u staged through shared memory, one CTA per plane range and cell
+  if (DIM == 3 && std::is_same<U, float>::value && Lv.nranges > 0 && Lv.tile_smem4 + 16 <= kMaxTileSmem) {
     cudaFuncSetAttribute(k_smooth_interior_tiled<PM, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kMaxTileSmem);
     dim3 grid((unsigned)Lv.nranges, (unsigned)G.cells.size());
-    hhg_launch(k_smooth_interior_tiled<PM, float>, grid, kBlock, Lv.tile_smem4, s, G.d_cells, ctx(m, l),
+    hhg_launch(k_smooth_interior_tiled<PM, float>, grid, kBlock, Lv.tile_smem4 + 16, s, G.d_cells, ctx(m, l),
                Lv.d_tiles + Lv.tile_off[gi][colour], Lv.d_icol, m->d_tnormf, Lv.d_invlf, (float*)u, rhs, m->d_err);
     return;
   }
@@ -215,7 +214,7 @@ static void iface32(hhg_mesh_s* m, int l, const Prims& P, int nverts, int parity
   if (P.count == 0 || (cnt_rim <= 0 && cnt_inner <= 0)) return;
   const LevelData& Lv = m->lv[l];
   float ss = (float)stiff_scale(DIM, Lv.n);
-  launch_iface<DIM, float, U, float>(iface_lanes(P.max_copies), false, P.count, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, nverts,
+  launch_iface<DIM, float, U, float>(iface_lanes(P.max_copies), P.count, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, nverts,
                                      parity, cnt_rim, cnt_inner, rim_list, inner_list, ctx(m, l), m->dS32, ss,
                                      P.d_pinvf, vec_of<U>(m, l, u), CVec<float, float>{rhs, nullptr}, Lv.t32, s);
 }
@@ -225,26 +224,25 @@ static void sweep32(hhg_mesh_s* m, int l, U* u, const float* rhs, cudaStream_t s
   LevelData& Lv = m->lv[l];
   int n = Lv.n;
   float ss = (float)stiff_scale(DIM, n);
-  int nst = 3 + (DIM == 3 ? 3 : 0) + m->n_colours;
+  const int nst = 3 + (DIM == 3 ? 1 : 0) + m->n_colours;
   for (int st = 0; st < nst; ++st) {
     if (st == 0) {
       const Prims& P = m->verts;
       if (P.count)
-        hhg_launch(k_smooth_vertex<DIM, float, U, float>, blocks_for((int64_t)P.count * 32), kBlock, 0, s, 
-            P.count, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l), m->dS32, ss, P.d_pinvf, 1.0f / ss,
-            vec_of<U>(m, l, u), CVec<float, float>{rhs, nullptr});
+        hhg_launch(k_smooth_vertex<DIM, float, U, float>, blocks_for((int64_t)P.count * 32), kBlock, 0, s, P.count,
+                   P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l), m->dS32, ss, P.d_pinvf, 1.0f / ss,
+                   vec_of<U>(m, l, u), CVec<float, float>{rhs, nullptr});
     } else if (st <= 2) {
       int parity = (st == 2);
       int cnt_rim = parity ? (n == 2 ? 1 : 2) : 0;
       int cnt_inner = parity ? (n == 2 ? 0 : n / 2 - 2) : n / 2 - 1;
       iface32<DIM, U>(m, l, m->edges, 2, parity, cnt_rim, cnt_inner, nullptr, nullptr, u, rhs, s);
-    } else if (DIM == 3 && st <= 5) {
-      int c = st - 3;
-      iface32<DIM, U>(m, l, m->faces, 3, 0, (int)(Lv.frim_off[c + 1] - Lv.frim_off[c]),
-                      (int)(Lv.fin_off[c + 1] - Lv.fin_off[c]), Lv.d_frim + Lv.frim_off[c], Lv.d_fin + Lv.fin_off[c],
-                      u, rhs, s);
+    } else if (DIM == 3 && st == 3) {
+      launch_face_block<float, U, float>(m->faces, Lv, ctx(m, l), m->dS32, ss, m->faces.d_fwf, m->faces.d_pinvf,
+                                         vec_of<U>(m, l, u), CVec<float, float>{rhs, nullptr}, Lv.t32,
+                                         (float*)m->d_face_work, false, s);
     } else {
-      int c = st - (DIM == 3 ? 6 : 3);
+      int c = st - (DIM == 3 ? 4 : 3);
       for (size_t gi = 0; gi < m->groups.size(); ++gi)
         if (c < m->groups[gi].m) interior32_dispatch<DIM, U>(m, l, (int)gi, c, u, rhs, s);
     }

@@ -62,11 +62,14 @@ HHG_HD int64_t tri_size(int64_t m) { return (m + 1) * (m + 2) / 2; }            
 HHG_HD int64_t tet_size(int64_t m) { return (m + 1) * (m + 2) * (m + 3) / 6; }  // nodes of a side-m tet
 HHG_HD int64_t closure_size(int dim, int64_t n) { return dim == 2 ? tri_size(n) : tet_size(n); }
 
-// packed index of lattice point (i, j, k) in the closure of side n
+// packed index of lattice point (i, j, k) in the closure of side n (32-bit arithmetic: exact for
+// n <= 1000, where every intermediate product stays below 2^31)
 HHG_HD int64_t packed_index(int dim, int64_t n, int64_t i, int64_t j, int64_t k) {
-  if (dim == 2) return j * (n + 1) - j * (j - 1) / 2 + i;
-  int64_t m = n - k;
-  return (tet_size(n) - tet_size(n - k)) + j * (m + 1) - j * (j - 1) / 2 + i;
+  const int nn = (int)n, ii = (int)i, jj = (int)j, kk = (int)k;
+  if (dim == 2) return (int64_t)(jj * (nn + 1) - jj * (jj - 1) / 2 + ii);
+  const int m = nn - kk;
+  const int tn = (nn + 1) * (nn + 2) * (nn + 3) / 6, tm = (m + 1) * (m + 2) * (m + 3) / 6;
+  return (int64_t)((tn - tm) + jj * (m + 1) - jj * (jj - 1) / 2 + ii);
 }
 
 HHG_HD int boundary_type(int dim, int n, int i, int j, int k) {
@@ -105,10 +108,12 @@ HHG_HD uint32_t valid_dirs_tab(int dim, int t) {
 
 // Packed-index offsets of all direction slots from the node at (j, k) (independent of i).
 // off[0] = 0.  Offsets of directions leaving the closure are meaningless and must be masked.
-HHG_HD void neighbour_offsets(int dim, int64_t n, int64_t j, int64_t k, int64_t* off) {
+HHG_HD void neighbour_offsets(int dim, int64_t n64, int64_t j64, int64_t k64, int64_t* off) {
+  // 32-bit arithmetic (exact for n <= 1000)
+  const int n = (int)n64, j = (int)j64, k = (int)k64;
   off[0] = 0;
   if (dim == 2) {
-    int64_t rl = n + 1 - j;  // length of row j
+    int rl = n + 1 - j;  // length of row j
     off[1] = 1;
     off[2] = -1;
     off[3] = rl;                 // +e2
@@ -117,8 +122,8 @@ HHG_HD void neighbour_offsets(int dim, int64_t n, int64_t j, int64_t k, int64_t*
     off[6] = -1 + rl;            // -e1+e2
     return;
   }
-  int64_t m = n - k;
-  int64_t Tm = tri_size(m), Tm1 = tri_size(m + 1);
+  const int m = n - k;
+  const int Tm = (m + 1) * (m + 2) / 2, Tm1 = (m + 2) * (m + 3) / 2;
   off[1] = 1;
   off[2] = -1;
   off[3] = m + 1 - j;            // +e2

@@ -365,6 +365,42 @@ hhg_status upload_coefficient(hhg_mesh_s* m) {
     CK(cudaMemcpy(P.d_pinv, pv.data(), pv.size() * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P.d_pinvf, pf.data(), pf.size() * sizeof(float), cudaMemcpyHostToDevice));
   }
+  // in-plane couplings of each macro face (face block of the smoother): for the six face-lattice
+  // directions (+a, -a, +b, -b, +a-b, -a+b) the stencil entries of the matching cell directions,
+  // summed over the face's copies (unit level scale)
+  if (m->dim == 3 && m->faces.count) {
+    Prims& P = m->faces;
+    std::vector<double> fw((size_t)P.count * 8, 0.0);
+    std::vector<float> fwf((size_t)P.count * 8, 0.0f);
+    static const int fda[6] = {1, -1, 0, 0, 1, -1}, fdb[6] = {0, 0, 1, -1, -1, 1};
+    for (int e = 0; e < P.count; ++e) {
+      if (P.dir[e]) continue;
+      for (int c = P.ptr[e]; c < P.ptr[e + 1]; ++c) {
+        int loc = P.loc[c];
+        int t = prim_interior_type(3, 3, loc);
+        int v[3][3];
+        for (int q = 0; q < 3; ++q) {
+          int a = (loc >> (2 * q)) & 3;
+          v[q][0] = a == 1;
+          v[q][1] = a == 2;
+          v[q][2] = a == 3;
+        }
+        for (int q = 0; q < 6; ++q) {
+          int dv[3];
+          for (int x = 0; x < 3; ++x) dv[x] = fda[q] * (v[1][x] - v[0][x]) + fdb[q] * (v[2][x] - v[0][x]);
+          int sl = slot_of(3, dv[0], dv[1], dv[2]);
+          if (sl <= 0) {
+            set_error("face direction is not a lattice direction (internal)");
+            return HHG_ERR_MESH;
+          }
+          fw[(size_t)e * 8 + q] += S[(size_t)P.cell[c] * NS + t * kMaxDirs + sl];
+        }
+      }
+      for (int q = 0; q < 8; ++q) fwf[(size_t)e * 8 + q] = (float)fw[(size_t)e * 8 + q];
+    }
+    CK(cudaMemcpy(P.d_fw, fw.data(), fw.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P.d_fwf, fwf.data(), fwf.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
   // coarse operator on the free macro vertices (level 0: n = 1, unit scale)
   int n0 = m->n0f;
   if (n0 > 0) {
@@ -409,6 +445,8 @@ static hhg_status upload_prims(hhg_mesh_s* m, Prims& P) {
   if ((st = upload(m, &P.d_dir, P.dir)) != HHG_OK) return st;
   if ((st = dalloc(m, &P.d_pinv, (size_t)P.count)) != HHG_OK) return st;
   if ((st = dalloc(m, &P.d_pinvf, (size_t)P.count)) != HHG_OK) return st;
+  if ((st = dalloc(m, &P.d_fw, (size_t)P.count * 8)) != HHG_OK) return st;
+  if ((st = dalloc(m, &P.d_fwf, (size_t)P.count * 8)) != HHG_OK) return st;
   for (int i = 0; i < P.count; ++i) P.max_copies = std::max(P.max_copies, P.ptr[i + 1] - P.ptr[i]);
   return HHG_OK;
 }
@@ -722,8 +760,7 @@ hhg_status build_mesh(hhg_mesh_s* m, const double* coords, const int* cells, con
             int64_t lo = std::lower_bound(b0, b1, P(r.first), by_q) - icol.begin();
             int64_t hi = std::lower_bound(b0, b1, P(r.second + 1), by_q) - icol.begin();
             tiles.push_back(make_int4(r.first, r.second, (int)lo, (int)hi));
-            size_t sm = 16 + r16(4 * (P(r.second + 2) - P(r.first - 1))) + r16(4 * (P(r.second + 1) - P(r.first))) +
-                        r16(8 * (hi - lo));
+            size_t sm = r16(4 * (P(r.second + 2) - P(r.first - 1))) + r16(8 * (hi - lo));
             Lv.tile_smem4 = std::max(Lv.tile_smem4, sm);
           }
         }
@@ -759,24 +796,11 @@ hhg_status build_mesh(hhg_mesh_s* m, const double* coords, const int* cells, con
     }
     Lv.fcol_off[3] = (int64_t)fcol.size();
     if ((st = upload(m, &Lv.d_fcol, fcol)) != HHG_OK) return st;
-    std::vector<int32_t> frim, fin;
-    for (int c = 0; c < 3; ++c) {
-      Lv.frim_off[c] = (int64_t)frim.size();
-      Lv.fin_off[c] = (int64_t)fin.size();
-      for (int64_t q = Lv.fcol_off[c]; q < Lv.fcol_off[c + 1]; ++q) {
-        int a = fcol[q] & 0xffff, b = fcol[q] >> 16;
-        bool rim = (a == 1) || (b == 1) || (a + b == Lv.n - 1);
-        (rim ? frim : fin).push_back(fcol[q]);
-      }
-    }
-    Lv.frim_off[3] = (int64_t)frim.size();
-    Lv.fin_off[3] = (int64_t)fin.size();
-    if ((st = upload(m, &Lv.d_frim, frim)) != HHG_OK) return st;
-    if ((st = upload(m, &Lv.d_fin, fin)) != HHG_OK) return st;
     // vectors
     if ((st = dalloc(m, &Lv.u, Lv.N)) != HHG_OK) return st;
     if ((st = dalloc(m, &Lv.b, Lv.N)) != HHG_OK) return st;
-    if (l < L && (st = dalloc(m, &Lv.rc, Lv.N)) != HHG_OK) return st;
+    // rc: coarse-grid rhs on levels < L; on level L the estimator's difference vector
+    if ((st = dalloc(m, &Lv.rc, Lv.N)) != HHG_OK) return st;
     if (l >= 1 && (st = dalloc(m, &Lv.tmp, Lv.N)) != HHG_OK) return st;
   }
   for (int l = 0; l < L; ++l)
@@ -789,6 +813,14 @@ hhg_status build_mesh(hhg_mesh_s* m, const double* coords, const int* cells, con
   if ((st = dalloc(m, &m->d_red, (size_t)nc * 4)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->d_flag, 4)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->d_err, 4)) != HHG_OK) return st;
+  if (d == 3 && m->faces.count) {  // face-block scratch where a face's values exceed shared memory
+    int64_t nfL = m->lv[L].fcol_off[3];
+    if (2 * nfL * (int64_t)sizeof(double) > (int64_t)kMaxTileSmem) {
+      double* wbuf = nullptr;
+      if ((st = dalloc(m, &wbuf, (size_t)m->faces.count * 2 * nfL)) != HHG_OK) return st;
+      m->d_face_work = wbuf;
+    }
+  }
   if ((st = dalloc(m, &m->d_scal32, 64)) != HHG_OK) return st;
   {
     cudaError_t e = cudaMallocHost((void**)&m->h_red, sizeof(double) * (size_t)nc * 4 + 64);
@@ -820,15 +852,15 @@ void free_mesh(hhg_mesh_s* m) {
   F(m->dS); F(m->dM); F(m->dS32); F(m->dM32); F(m->d_inv0); F(m->d_inv0f); F(m->d_tnorm); F(m->d_tnormf);
   F(m->d_dirmask); F(m->d_nzs);
   for (hhg::Prims* P : {&m->verts, &m->edges, &m->faces}) {
-    F(P->d_ptr); F(P->d_cell); F(P->d_loc); F(P->d_dir); F(P->d_pinv); F(P->d_pinvf);
+    F(P->d_ptr); F(P->d_cell); F(P->d_loc); F(P->d_dir); F(P->d_pinv); F(P->d_pinvf); F(P->d_fw); F(P->d_fwf);
   }
   for (auto& g : m->groups) F(g.d_cells);
   F(m->d_Ainv); F(m->d_cf_vert);
   for (auto& Lv : m->lv) {
-    F(Lv.d_ijk); F(Lv.d_icol); F(Lv.d_bnd); F(Lv.d_tiles); F(Lv.d_invl); F(Lv.d_invlf); F(Lv.d_fcol); F(Lv.d_frim); F(Lv.d_fin); F(Lv.u); F(Lv.b); F(Lv.rc); F(Lv.w); F(Lv.tmp);
+    F(Lv.d_ijk); F(Lv.d_icol); F(Lv.d_bnd); F(Lv.d_tiles); F(Lv.d_invl); F(Lv.d_invlf); F(Lv.d_fcol); F(Lv.u); F(Lv.b); F(Lv.rc); F(Lv.w); F(Lv.tmp);
     F(Lv.c16); F(Lv.r32); F(Lv.t32); F(Lv.cscale); F(Lv.x32); F(Lv.b32);
   }
-  F(m->fL); F(m->gL); F(m->d_part); F(m->d_red); F(m->d_flag); F(m->d_err); F(m->d_scal32);
+  F(m->fL); F(m->gL); F(m->d_part); F(m->d_red); F(m->d_flag); F(m->d_err); F(m->d_face_work); F(m->d_scal32);
   if (m->h_red) cudaFreeHost(m->h_red);
   if (m->cap) cudaStreamDestroy(m->cap);
   if (m->own) cudaStreamDestroy(m->own);

@@ -228,6 +228,53 @@ def test_smoother_stage_equals_true_gauss_seidel_when_colours_are_valid():
         assert np.abs(u1 - u2).max() < 1e-13
 
 
+def test_face_block_is_per_face_gauss_seidel_with_frozen_surroundings():
+    """3D face block, written out node by node: for every macro face, sequential Gauss-Seidel over
+    its nodes in colour order, reading its own nodes at their current values and every other node
+    at its value from the start of the block.  Face and colour are recomputed here from the node
+    keys (vertex ids and barycentric weights), not taken from the oracle's stage data."""
+    co, ce = W.cube_mesh(2)
+    h = O.Hierarchy(co, ce, 3, k=W.coeff_uniform(len(ce), seed=5))
+    lev = h.levels[3]
+    A = lev.A.tocsr()
+    keys = lev.keys
+    g, w = keys[:, 0::2], keys[:, 1::2]
+    nv = (w > 0).sum(axis=1)
+    face = {}
+    for i in np.nonzero((nv == 3) & lev.free)[0]:
+        fk = tuple(sorted(g[i, :3]))
+        col = (w[i, 1] + 2 * w[i, 2]) % 3
+        face.setdefault(fk, []).append((col, i))
+    assert len(face) > 4
+    rng = np.random.default_rng(2)
+    u = np.where(lev.dirichlet, 0.0, rng.standard_normal(len(keys)))
+    rhs = rng.standard_normal(len(keys))
+    # stages before the face block (vertices, edges), then the block literally
+    ref = u.copy()
+    for s in range(3):
+        idx = lev.stages[s]
+        ref[idx] += (rhs[idx] - A[idx] @ ref) / A.diagonal()[idx]
+    frozen = ref.copy()
+    for fk, nodes in face.items():
+        mine = np.zeros(len(keys), dtype=bool)
+        mine[[i for _, i in nodes]] = True
+        for col in range(3):
+            for c, i in nodes:
+                if c != col:
+                    continue
+                row = A.getrow(i)
+                vals = np.where(mine[row.indices], ref[row.indices], frozen[row.indices])
+                ref[i] += (rhs[i] - row.data @ vals) / A[i, i]
+    # the oracle's sweep, stopped after the face block
+    got = u.copy()
+    stages, lev.stages = lev.stages, lev.stages[:6]
+    try:
+        O.smooth(lev, got, rhs)
+    finally:
+        lev.stages = stages
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
 # ---------------------------------------------------------------- discretisation (Sec. 5)
 
 def _errors(name, Ls, fn=None):
