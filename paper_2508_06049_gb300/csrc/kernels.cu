@@ -132,17 +132,18 @@ static void sweep_impl(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s) 
   const int nst = 3 + (DIM == 3 ? 1 : 0) + m->n_colours;
   for (int st = 0; st < nst; ++st) {
     if (st == 0) {
-      const Prims& P = m->verts;
-      if (P.count)
-        hhg_launch(k_smooth_vertex<DIM, double, double, double>, blocks_for((int64_t)P.count * 32), kBlock, 0, s,
-                   P.count, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l), m->dS, ss, P.d_pinv, 1.0 / ss,
-                   Vec<double, double>{u, nullptr}, CVec<double, double>{rhs, nullptr});
-    } else if (st <= 2) {
-      // stage 1: even local index (no coupling inside the stage); stage 2: odd, t = 1 and n-1 are rim
-      int parity = (st == 2);
-      int cnt_rim = parity ? (n == 2 ? 1 : 2) : 0;
-      int cnt_inner = parity ? (n == 2 ? 0 : n / 2 - 2) : n / 2 - 1;
-      iface_stage<DIM>(m, l, m->edges, 2, parity, cnt_rim, cnt_inner, nullptr, nullptr, u, rhs, s);
+      // stages 0 and 1 (vertices, even edge nodes) do not couple: one launch
+      launch_vertex_edge_even<DIM, double, double, double>(m->verts, m->edges, n, ctx(m, l), m->dS, ss,
+                                                           m->verts.d_pinv, m->edges.d_pinv,
+                                                           Vec<double, double>{u, nullptr},
+                                                           CVec<double, double>{rhs, nullptr}, s);
+    } else if (st == 1) {
+      continue;
+    } else if (st == 2) {
+      // odd edge nodes: t = 1 and n-1 are rim
+      int cnt_rim = n == 2 ? 1 : 2;
+      int cnt_inner = n == 2 ? 0 : n / 2 - 2;
+      iface_stage<DIM>(m, l, m->edges, 2, 1, cnt_rim, cnt_inner, nullptr, nullptr, u, rhs, s);
     } else if (DIM == 3 && st == 3) {
       // binary64 face-node pass over the outside couplings: sparse slot loop where DFMA-bound
       bool sparse = (int64_t)m->faces.count * Lv.fcol_off[3] >= kSparseFaceNodes;

@@ -192,6 +192,47 @@ __global__ void __launch_bounds__(kBlock) k_smooth_interior(const int* __restric
   u.set(g, acc);
 }
 
+// The same stage with two cells per thread (grid.y = cell pairs): the list entry and its neighbour
+// offsets serve both cells, and the loads of both are in flight together.
+template <int DIM, int PM, typename R, typename U, typename B>
+__global__ void __launch_bounds__(kBlock) k_smooth_interior_x2(const int* __restrict__ gcells, int ncells,
+                                                               const int2* __restrict__ list, int64_t len, LevelCtx lc,
+                                                               const R* __restrict__ tnorm, const R* __restrict__ invl,
+                                                               Vec<R, U> u, CVec<R, B> rhs) {
+  grid_dependency_sync();
+  int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= len) return;
+  const int c0 = 2 * blockIdx.y;
+  const bool two = c0 + 1 < ncells;
+  const int T0 = gcells[c0], T1 = two ? gcells[c0 + 1] : T0;
+  int2 e = list[pos];
+  int loc = e.x;
+  if (HHG_OOB(loc, lc.Nt, 41)) return;
+  int j = e.y & 0xffff, k = e.y >> 16;
+  int64_t off[15];
+  neighbour_offsets(DIM, lc.n, j, k, off);
+#ifdef HHG_CHECK
+  for (int d = 1; d < ndirs<DIM>(); ++d)
+    if (HHG_OOB(loc + off[d], lc.Nt, 42)) return;
+#endif
+  const R* t0 = tnorm + (size_t)T0 * 16;
+  const R* t1 = tnorm + (size_t)T1 * 16;
+  const int64_t g0 = (int64_t)T0 * lc.Nt + loc, g1 = (int64_t)T1 * lc.Nt + loc;
+  R a0 = rhs.get(g0) * invl[T0];
+  R a1 = rhs.get(g1) * invl[T1];
+#pragma unroll
+  for (int q = 0; q < npairs<DIM>(); ++q) {
+    if (PM >> q & 1) {
+      a0 -= t0[2 * q + 1] * u.get(g0 + off[2 * q + 1]);
+      a1 -= t1[2 * q + 1] * u.get(g1 + off[2 * q + 1]);
+      a0 -= t0[2 * q + 2] * u.get(g0 + off[2 * q + 2]);
+      a1 -= t1[2 * q + 2] * u.get(g1 + off[2 * q + 2]);
+    }
+  }
+  u.set(g0, a0);
+  if (two) u.set(g1, a1);
+}
+
 // The same interior colour stage (3D) with the cell's u values staged in shared memory.  One CTA
 // takes one plane range [k0, k1] of one cell (tile = {k0, k1, lo, hi}): the u planes k0-1 .. k1+1
 // are contiguous in the packed layout and the colour's list entries of those planes are the
@@ -275,13 +316,11 @@ __global__ void __launch_bounds__(kBlock) k_smooth_interior_tiled(const int* __r
 // macro vertices: never coupled to each other on levels >= 1, so one pass.  One warp per vertex,
 // lanes over the vertex's cell copies (scattered loads in parallel), fixed-order shuffle sums.
 template <int DIM, typename R, typename U, typename B>
-__global__ void k_smooth_vertex(int nprim, const int* __restrict__ ptr, const int* __restrict__ cell,
-                                const int* __restrict__ locv, const unsigned char* __restrict__ dir, LevelCtx lc,
-                                const R* __restrict__ S, R sscale, const R* __restrict__ pinv, R isscale, Vec<R, U> u,
-                                CVec<R, B> rhs) {
-  grid_dependency_sync();
-  int v = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  int lane = threadIdx.x & 31;
+__device__ __forceinline__ void vertex_update(int v, int lane, int nprim, const int* __restrict__ ptr,
+                                              const int* __restrict__ cell, const int* __restrict__ locv,
+                                              const unsigned char* __restrict__ dir, const LevelCtx& lc,
+                                              const R* __restrict__ S, R sscale, const R* __restrict__ pinv,
+                                              R isscale, Vec<R, U> u, CVec<R, B> rhs) {
   if (v >= nprim || dir[v]) return;  // uniform across the warp
   CVec<R, U> uc{u.p, u.scale};
   R acc = 0, bs = 0;
@@ -308,6 +347,16 @@ __global__ void k_smooth_vertex(int nprim, const int* __restrict__ ptr, const in
     if (HHG_OOB(p, lc.Nt, 92)) continue;
     u.set((int64_t)cell[c] * lc.Nt + p, unew);
   }
+}
+
+template <int DIM, typename R, typename U, typename B>
+__global__ void k_smooth_vertex(int nprim, const int* __restrict__ ptr, const int* __restrict__ cell,
+                                const int* __restrict__ locv, const unsigned char* __restrict__ dir, LevelCtx lc,
+                                const R* __restrict__ S, R sscale, const R* __restrict__ pinv, R isscale, Vec<R, U> u,
+                                CVec<R, B> rhs) {
+  grid_dependency_sync();
+  int v = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  vertex_update<DIM>(v, threadIdx.x & 31, nprim, ptr, cell, locv, dir, lc, S, sscale, pinv, isscale, u, rhs);
 }
 
 // Edge stages (even, then odd edge-local index).  Every node of a stage is updated from the values
@@ -337,14 +386,13 @@ __device__ __forceinline__ void stage_position(int nverts, int parity, bool rim,
 // lane holds the same sum.  Rim nodes (those that can neighbour another node of the same stage in
 // some cell) store their correction in du for k_iface_apply; inner nodes are updated in place.
 template <int DIM, int G, typename R, typename U, typename B>
-__global__ void k_iface_stage(int nprim, int nverts, int parity, int cnt_rim, int cnt_inner,
-                              const int32_t* __restrict__ rim_list, const int32_t* __restrict__ inner_list,
-                              const int* __restrict__ ptr, const int* __restrict__ cell, const int* __restrict__ locv,
-                              const unsigned char* __restrict__ dir, LevelCtx lc, const R* __restrict__ S, R sscale,
-                              const R* __restrict__ pinv, R isscale, Vec<R, U> u, CVec<R, B> rhs,
-                              R* __restrict__ du) {
-  grid_dependency_sync();
-  int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void iface_update(int64_t gid, int nprim, int nverts, int parity, int cnt_rim, int cnt_inner,
+                                             const int32_t* __restrict__ rim_list,
+                                             const int32_t* __restrict__ inner_list, const int* __restrict__ ptr,
+                                             const int* __restrict__ cell, const int* __restrict__ locv,
+                                             const unsigned char* __restrict__ dir, const LevelCtx& lc,
+                                             const R* __restrict__ S, R sscale, const R* __restrict__ pinv,
+                                             R isscale, Vec<R, U> u, CVec<R, B> rhs, R* __restrict__ du) {
   int lane = (int)(gid & (G - 1));
   int64_t tid = gid / G;
   int64_t n_rim = (int64_t)nprim * cnt_rim;
@@ -398,6 +446,39 @@ __global__ void k_iface_stage(int nprim, int nverts, int parity, int cnt_rim, in
     int64_t p = packed_index(DIM, lc.n, i, j, k);
     if (HHG_OOB(p, lc.Nt, 91)) continue;
     u.set((int64_t)cell[c] * lc.Nt + p, unew);
+  }
+}
+
+template <int DIM, int G, typename R, typename U, typename B>
+__global__ void k_iface_stage(int nprim, int nverts, int parity, int cnt_rim, int cnt_inner,
+                              const int32_t* __restrict__ rim_list, const int32_t* __restrict__ inner_list,
+                              const int* __restrict__ ptr, const int* __restrict__ cell, const int* __restrict__ locv,
+                              const unsigned char* __restrict__ dir, LevelCtx lc, const R* __restrict__ S, R sscale,
+                              const R* __restrict__ pinv, R isscale, Vec<R, U> u, CVec<R, B> rhs,
+                              R* __restrict__ du) {
+  grid_dependency_sync();
+  iface_update<DIM, G>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, nprim, nverts, parity, cnt_rim, cnt_inner,
+                       rim_list, inner_list, ptr, cell, locv, dir, lc, S, sscale, pinv, isscale, u, rhs, du);
+}
+
+// The vertex stage and the even edge stage in one launch: no vertex neighbours an even edge node
+// (which sits at least two lattice steps from every macro vertex), so running them together gives
+// the results of the two stages in sequence.  Blocks [0, nbv) take the vertices (a warp each), the
+// others the even edge nodes (G lanes each, no rim nodes in the even stage).
+template <int DIM, int G, typename R, typename U, typename B>
+__global__ void k_vertex_edge_even(int nbv, int nv, const int* __restrict__ vptr, const int* __restrict__ vcell,
+                                   const int* __restrict__ vloc, const unsigned char* __restrict__ vdir,
+                                   const R* __restrict__ vpinv, int ne, int cnt_inner, const int* __restrict__ eptr,
+                                   const int* __restrict__ ecell, const int* __restrict__ eloc,
+                                   const unsigned char* __restrict__ edir, const R* __restrict__ epinv, LevelCtx lc,
+                                   const R* __restrict__ S, R sscale, R isscale, Vec<R, U> u, CVec<R, B> rhs) {
+  grid_dependency_sync();
+  if ((int)blockIdx.x < nbv) {
+    int v = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    vertex_update<DIM>(v, threadIdx.x & 31, nv, vptr, vcell, vloc, vdir, lc, S, sscale, vpinv, isscale, u, rhs);
+  } else {
+    iface_update<DIM, G>((int64_t)(blockIdx.x - nbv) * blockDim.x + threadIdx.x, ne, 2, 0, 0, cnt_inner, nullptr,
+                         nullptr, eptr, ecell, eloc, edir, lc, S, sscale, epinv, isscale, u, rhs, (R*)nullptr);
   }
 }
 
@@ -608,15 +689,33 @@ __global__ void __launch_bounds__(kBlock) k_face_gs(int nf, int4 fcol, const int
   const int c0 = ptr[e];
   const int loc0 = locv[c0];
   const int64_t base0 = (int64_t)cell[c0] * lc.Nt;
-  for (int q = threadIdx.x; q < nf; q += blockDim.x) {
-    int32_t ab = fnodes[q];
-    int a = ab & 0xffff, b = ab >> 16;
-    int i, j, k;
-    prim_position(loc0, 3, n, a, b, i, j, k);
-    int pos = face_pos(n, a, b);
-    int64_t p = packed_index(3, n, i, j, k);
-    uf[pos] = HHG_OOB(p, lc.Nt, 35) ? (R)0 : u.get(base0 + p);
-    ef[pos] = E[(int64_t)e * nf + pos] * isscale;
+  // gather the face's values (copy 0) and outside sums, four per thread in flight
+  constexpr int kUnroll = 4;
+  for (int q0 = threadIdx.x; q0 < nf; q0 += kUnroll * blockDim.x) {
+    R uv[kUnroll], ev[kUnroll];
+    int ps[kUnroll];
+#pragma unroll
+    for (int r = 0; r < kUnroll; ++r) {
+      int q = q0 + r * blockDim.x;
+      ps[r] = -1;
+      if (q < nf) {
+        int32_t ab = fnodes[q];
+        int a = ab & 0xffff, b = ab >> 16;
+        int i, j, k;
+        prim_position(loc0, 3, n, a, b, i, j, k);
+        int pos = face_pos(n, a, b);
+        int64_t p = packed_index(3, n, i, j, k);
+        ps[r] = pos;
+        uv[r] = HHG_OOB(p, lc.Nt, 35) ? (R)0 : u.get(base0 + p);
+        ev[r] = E[(int64_t)e * nf + pos];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kUnroll; ++r)
+      if (ps[r] >= 0) {
+        uf[ps[r]] = uv[r];
+        ef[ps[r]] = ev[r] * isscale;
+      }
   }
   R w[6];
 #pragma unroll
@@ -653,6 +752,31 @@ __global__ void __launch_bounds__(kBlock) k_face_gs(int nf, int4 fcol, const int
       u.set(base + p, uf[face_pos(n, a, b)]);
     }
   }
+}
+
+// Launch the vertex stage and the even edge stage together (k_vertex_edge_even).
+template <int DIM, typename R, typename U, typename B>
+void launch_vertex_edge_even(const Prims& V, const Prims& Ed, int n, LevelCtx lc, const R* S, R ss, const R* vpinv,
+                             const R* epinv, Vec<R, U> u, CVec<R, B> rhs, cudaStream_t s) {
+  const int cnt_inner = n / 2 - 1;  // even edge-local indices 2, 4, .., n-2
+  const unsigned nbv = blocks_for((int64_t)V.count * 32);
+  const int ne = cnt_inner > 0 ? Ed.count : 0;
+  const int G = iface_lanes(Ed.max_copies);
+  const unsigned nbe = blocks_for((int64_t)ne * (cnt_inner > 0 ? cnt_inner : 0) * G);
+  if (nbv + nbe == 0) return;
+#define HHG_VE(GL)                                                                                                    \
+  hhg_launch(k_vertex_edge_even<DIM, GL, R, U, B>, nbv + nbe, kBlock, 0, s, (int)nbv, V.count, V.d_ptr, V.d_cell,   \
+             V.d_loc, V.d_dir, vpinv, ne, cnt_inner, Ed.d_ptr, Ed.d_cell, Ed.d_loc, Ed.d_dir, epinv, lc, S, ss,     \
+             (R)1 / ss, u, rhs)
+  switch (G) {
+    case 1: HHG_VE(1); break;
+    case 2: HHG_VE(2); break;
+    case 4: HHG_VE(4); break;
+    case 8: HHG_VE(8); break;
+    case 16: HHG_VE(16); break;
+    default: HHG_VE(32); break;
+  }
+#undef HHG_VE
 }
 
 // Launch the face block on one level: E in `E` (P.count x nf values), the per-face sweeps in shared
@@ -942,7 +1066,7 @@ __global__ void __launch_bounds__(kBlock) k_node_form(LevelCtx lc, const double*
                                                       const double* __restrict__ a, const double* __restrict__ b,
                                                       double* __restrict__ part) {
   grid_dependency_sync();
-  __shared__ double wsum[kBlock / 32];
+  __shared__ double sh[kBlock];
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int T = blockIdx.y;
   double sum = 0;
@@ -984,16 +1108,14 @@ __global__ void __launch_bounds__(kBlock) k_node_form(LevelCtx lc, const double*
     }
     sum = DIFF ? xp * (s[0] * xp + 2.0 * ay) : xp * (s[0] * yp + ay) + yp * ax;
   }
-  // deterministic block sum: warp butterflies, then the warp sums in order
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = sum;
+  // deterministic block sum: shared-memory tree (one binary64 add per node in total)
+  sh[threadIdx.x] = sum;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double tot = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wsum[w];
-    part[(int64_t)T * gridDim.x + blockIdx.x] = tot;
+  for (int w = kBlock / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) part[(int64_t)T * gridDim.x + blockIdx.x] = sh[0];
 }
 
 // ---------------------------------------------------------------- operators for testing / adjoint

@@ -192,6 +192,19 @@ static void interior32(hhg_mesh_s* m, int l, int gi, int colour, U* u, const flo
       CVec<float, float>{rhs, nullptr});
 }
 
+// the two-cells-per-thread list kernel (profiling comparison with the staged kernel)
+template <int DIM, int PM, typename U>
+static void interior32_x2(hhg_mesh_s* m, int l, int gi, int colour, U* u, const float* rhs, cudaStream_t s) {
+  const LevelData& Lv = m->lv[l];
+  const Group& G = m->groups[gi];
+  int64_t a = Lv.icol_off[gi][colour], b = Lv.icol_off[gi][colour + 1];
+  if (b <= a || G.cells.empty()) return;
+  dim3 grid(blocks_for(b - a), (unsigned)((G.cells.size() + 1) / 2));
+  hhg_launch(k_smooth_interior_x2<DIM, PM, float, U, float>, grid, kBlock, 0, s, G.d_cells, (int)G.cells.size(),
+             Lv.d_icol + a, b - a, ctx(m, l), m->d_tnormf, Lv.d_invlf, vec_of<U>(m, l, u),
+             CVec<float, float>{rhs, nullptr});
+}
+
 template <int DIM, typename U>
 static void interior32_dispatch(hhg_mesh_s* m, int l, int gi, int colour, U* u, const float* rhs, cudaStream_t s) {
   int pm = m->groups[gi].pmask;
@@ -227,16 +240,16 @@ static void sweep32(hhg_mesh_s* m, int l, U* u, const float* rhs, cudaStream_t s
   const int nst = 3 + (DIM == 3 ? 1 : 0) + m->n_colours;
   for (int st = 0; st < nst; ++st) {
     if (st == 0) {
-      const Prims& P = m->verts;
-      if (P.count)
-        hhg_launch(k_smooth_vertex<DIM, float, U, float>, blocks_for((int64_t)P.count * 32), kBlock, 0, s, P.count,
-                   P.d_ptr, P.d_cell, P.d_loc, P.d_dir, ctx(m, l), m->dS32, ss, P.d_pinvf, 1.0f / ss,
-                   vec_of<U>(m, l, u), CVec<float, float>{rhs, nullptr});
-    } else if (st <= 2) {
-      int parity = (st == 2);
-      int cnt_rim = parity ? (n == 2 ? 1 : 2) : 0;
-      int cnt_inner = parity ? (n == 2 ? 0 : n / 2 - 2) : n / 2 - 1;
-      iface32<DIM, U>(m, l, m->edges, 2, parity, cnt_rim, cnt_inner, nullptr, nullptr, u, rhs, s);
+      // stages 0 and 1 (vertices, even edge nodes) do not couple: one launch
+      launch_vertex_edge_even<DIM, float, U, float>(m->verts, m->edges, n, ctx(m, l), m->dS32, ss, m->verts.d_pinvf,
+                                                    m->edges.d_pinvf, vec_of<U>(m, l, u),
+                                                    CVec<float, float>{rhs, nullptr}, s);
+    } else if (st == 1) {
+      continue;
+    } else if (st == 2) {
+      int cnt_rim = n == 2 ? 1 : 2;
+      int cnt_inner = n == 2 ? 0 : n / 2 - 2;
+      iface32<DIM, U>(m, l, m->edges, 2, 1, cnt_rim, cnt_inner, nullptr, nullptr, u, rhs, s);
     } else if (DIM == 3 && st == 3) {
       launch_face_block<float, U, float>(m->faces, Lv, ctx(m, l), m->dS32, ss, m->faces.d_fwf, m->faces.d_pinvf,
                                          vec_of<U>(m, l, u), CVec<float, float>{rhs, nullptr}, Lv.t32,
@@ -438,7 +451,7 @@ hhg_status mixed_prepare(hhg_mesh_s* m, int storage) {
 }
 
 hhg_status mixed_profile_interior(hhg_mesh_s* m, int reps, cudaStream_t s, long long* units, double* bytes,
-                                  double* flops) {
+                                  double* flops, bool x2) {
   const int L = m->L;
   LevelData& Lv = m->lv[L];
   const Group& G = m->groups[0];
@@ -449,8 +462,16 @@ hhg_status mixed_profile_interior(hhg_mesh_s* m, int reps, cudaStream_t s, long 
   *bytes = 4.0 * ((double)Lv.Nt * G.cells.size() + 2.0 * nodes);
   *flops = (4.0 * p + 1.0) * nodes;
   for (int r = 0; r < reps; ++r) {
-    if (m->dim == 2) interior32_dispatch<2, float>(m, L, 0, 0, Lv.x32, Lv.b32, s);
-    else interior32_dispatch<3, float>(m, L, 0, 0, Lv.x32, Lv.b32, s);
+    if (x2) {
+      // the two-cells-per-thread list kernel of the group's pattern
+      if (m->dim == 2) interior32_x2<2, 0x7, float>(m, L, 0, 0, Lv.x32, Lv.b32, s);
+      else if (G.pmask == 0x29) interior32_x2<3, 0x29, float>(m, L, 0, 0, Lv.x32, Lv.b32, s);
+      else interior32_x2<3, 0x7f, float>(m, L, 0, 0, Lv.x32, Lv.b32, s);
+    } else if (m->dim == 2) {
+      interior32_dispatch<2, float>(m, L, 0, 0, Lv.x32, Lv.b32, s);
+    } else {
+      interior32_dispatch<3, float>(m, L, 0, 0, Lv.x32, Lv.b32, s);
+    }
   }
   return HHG_OK;
 }
