@@ -155,7 +155,7 @@ def peaks():
 FP64_PEAK_TFLOPS = 1.205
 # DRAM bytes (read + write) of one launch of the roofline kernel on the 384-tet cube at L = 6, from
 # one ncu capture of that kernel (summarised under profiles/); None for other workloads
-TRAFFIC_BYTES = {("cube384_l6", "fp64"): 369.5e6, ("cube384_l6", "mixed"): 164.8e6}
+TRAFFIC_BYTES = {("cube384_l6", "fp64"): 369.5e6}
 
 
 # ----------------------------------------------------------------------------- arms

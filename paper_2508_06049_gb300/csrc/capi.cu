@@ -20,7 +20,7 @@ void launch_profile_face(hhg_mesh_s* m, int reps, cudaStream_t s, long long* uni
 void launch_profile_level(hhg_mesh_s* m, int kernel, int reps, cudaStream_t s, long long* units, double* bytes,
                           double* flops);
 hhg_status mixed_profile_interior(hhg_mesh_s* m, int reps, cudaStream_t s, long long* units, double* bytes,
-                                  double* flops, bool x2 = false);
+                                  double* flops, int variant = 0);
 hhg_status mixed_prepare(hhg_mesh_s* m, int storage);
 void mixed_enqueue_solve(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t s);
 }  // namespace hhg
@@ -580,16 +580,16 @@ hhg_status hhg_adjoint_l2(hhg_mesh m, const hhg_solve_params* params, const unsi
 hhg_status hhg_profile_kernel(hhg_mesh m, int kernel, int precision, int reps, long long* units, double* bytes,
                               double* flops) {
   REQUIRE(m && units && bytes && flops, HHG_ERR_ARG, "NULL argument");
-  REQUIRE(kernel >= 0 && kernel <= 5, HHG_ERR_ARG, "kernel must be 0 .. 5");
+  REQUIRE(kernel >= 0 && kernel <= 6, HHG_ERR_ARG, "kernel must be 0 .. 6");
   REQUIRE(precision == 0 || precision == 1, HHG_ERR_ARG, "precision must be 0 or 1");
   REQUIRE(reps >= 0 && reps <= 100000, HHG_ERR_ARG, "reps in [0, 100000]");
   DeviceGuard g(m->device);
   ENTER(m);
-  if (kernel == 5) {
-    REQUIRE(precision == 1, HHG_ERR_ARG, "probe 5 is the binary32 two-cells-per-thread interior stage");
+  if (kernel == 5 || kernel == 6) {
+    REQUIRE(precision == 1, HHG_ERR_ARG, "probes 5 and 6 are binary32 interior-stage variants");
     hhg_status st = mixed_prepare(m, m->mixed_alloc ? m->last_storage : 1);
     if (st != HHG_OK) return st;
-    st = mixed_profile_interior(m, reps, m->stream, units, bytes, flops, true);
+    st = mixed_profile_interior(m, reps, m->stream, units, bytes, flops, kernel - 4);
     if (st != HHG_OK) return st;
   } else if (kernel >= 2) {
     REQUIRE(precision == 0, HHG_ERR_ARG, "the level probes 2 .. 4 are binary64");

@@ -8,7 +8,7 @@
 
 namespace hhg {
 
-// One block per cell: deterministic shared-memory tree sum of the cell's np partial sums.
+// One block per cell: deterministic shared-memory tree sum of the cell's np node contributions.
 __global__ void __launch_bounds__(256) k_cell_sum(int64_t np, double scale, const double* __restrict__ part,
                                                   double* __restrict__ out) {
   grid_dependency_sync();
@@ -264,7 +264,7 @@ void launch_finite_check(hhg_mesh_s* m, const double* v, int64_t n, cudaStream_t
 static void cell_form(hhg_mesh_s* m, bool diff, const double* tab, double scale, const double* a, const double* b,
                       double* out, cudaStream_t s) {
   const LevelData& Lv = m->lv[m->L];
-  double* contrib = m->d_part;  // per-block partial sums (cells x blocks <= N_L doubles)
+  double* contrib = m->d_part;  // N_L doubles of scratch
   dim3 grid(blocks_for(Lv.Nt), m->nc);
   if (diff) {
     if (m->dim == 2) hhg_launch(k_node_form<2, true>, grid, kBlock, 0, s, ctx(m, m->L), tab, a, b, contrib);
@@ -273,7 +273,7 @@ static void cell_form(hhg_mesh_s* m, bool diff, const double* tab, double scale,
     if (m->dim == 2) hhg_launch(k_node_form<2, false>, grid, kBlock, 0, s, ctx(m, m->L), tab, a, b, contrib);
     else hhg_launch(k_node_form<3, false>, grid, kBlock, 0, s, ctx(m, m->L), tab, a, b, contrib);
   }
-  hhg_launch(k_cell_sum, m->nc, 256, 0, s, (int64_t)grid.x, scale, contrib, out);
+  hhg_launch(k_cell_sum, m->nc, 256, 0, s, Lv.Nt, scale, contrib, out);
 }
 
 void launch_mass_norm_sq(hhg_mesh_s* m, const double* a, const double* b, double* out, cudaStream_t s) {

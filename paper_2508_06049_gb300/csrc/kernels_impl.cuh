@@ -192,19 +192,18 @@ __global__ void __launch_bounds__(kBlock) k_smooth_interior(const int* __restric
   u.set(g, acc);
 }
 
-// The same stage with two cells per thread (grid.y = cell pairs): the list entry and its neighbour
-// offsets serve both cells, and the loads of both are in flight together.
-template <int DIM, int PM, typename R, typename U, typename B>
-__global__ void __launch_bounds__(kBlock) k_smooth_interior_x2(const int* __restrict__ gcells, int ncells,
-                                                               const int2* __restrict__ list, int64_t len, LevelCtx lc,
-                                                               const R* __restrict__ tnorm, const R* __restrict__ invl,
-                                                               Vec<R, U> u, CVec<R, B> rhs) {
+// The same stage with CPB cells per thread (grid.y = groups of CPB cells): the list entry and its
+// neighbour offsets serve all of them, and their loads are in flight together.
+template <int DIM, int PM, int CPB, typename R, typename U, typename B>
+__global__ void __launch_bounds__(kBlock) k_smooth_interior_multi(const int* __restrict__ gcells, int ncells,
+                                                                  const int2* __restrict__ list, int64_t len,
+                                                                  LevelCtx lc, const R* __restrict__ tnorm,
+                                                                  const R* __restrict__ invl, Vec<R, U> u,
+                                                                  CVec<R, B> rhs) {
   grid_dependency_sync();
   int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (pos >= len) return;
-  const int c0 = 2 * blockIdx.y;
-  const bool two = c0 + 1 < ncells;
-  const int T0 = gcells[c0], T1 = two ? gcells[c0 + 1] : T0;
+  const int c0 = CPB * blockIdx.y;
   int2 e = list[pos];
   int loc = e.x;
   if (HHG_OOB(loc, lc.Nt, 41)) return;
@@ -215,22 +214,28 @@ __global__ void __launch_bounds__(kBlock) k_smooth_interior_x2(const int* __rest
   for (int d = 1; d < ndirs<DIM>(); ++d)
     if (HHG_OOB(loc + off[d], lc.Nt, 42)) return;
 #endif
-  const R* t0 = tnorm + (size_t)T0 * 16;
-  const R* t1 = tnorm + (size_t)T1 * 16;
-  const int64_t g0 = (int64_t)T0 * lc.Nt + loc, g1 = (int64_t)T1 * lc.Nt + loc;
-  R a0 = rhs.get(g0) * invl[T0];
-  R a1 = rhs.get(g1) * invl[T1];
+  int64_t g[CPB];
+  const R* t[CPB];
+  R acc[CPB];
+#pragma unroll
+  for (int c = 0; c < CPB; ++c) {
+    const int T = gcells[min(c0 + c, ncells - 1)];  // a short last group repeats its last cell
+    g[c] = (int64_t)T * lc.Nt + loc;
+    t[c] = tnorm + (size_t)T * 16;
+    acc[c] = rhs.get(g[c]) * invl[T];
+  }
 #pragma unroll
   for (int q = 0; q < npairs<DIM>(); ++q) {
     if (PM >> q & 1) {
-      a0 -= t0[2 * q + 1] * u.get(g0 + off[2 * q + 1]);
-      a1 -= t1[2 * q + 1] * u.get(g1 + off[2 * q + 1]);
-      a0 -= t0[2 * q + 2] * u.get(g0 + off[2 * q + 2]);
-      a1 -= t1[2 * q + 2] * u.get(g1 + off[2 * q + 2]);
+#pragma unroll
+      for (int c = 0; c < CPB; ++c) acc[c] -= t[c][2 * q + 1] * u.get(g[c] + off[2 * q + 1]);
+#pragma unroll
+      for (int c = 0; c < CPB; ++c) acc[c] -= t[c][2 * q + 2] * u.get(g[c] + off[2 * q + 2]);
     }
   }
-  u.set(g0, a0);
-  if (two) u.set(g1, a1);
+#pragma unroll
+  for (int c = 0; c < CPB; ++c)
+    if (c0 + c < ncells) u.set(g[c], acc[c]);
 }
 
 // The same interior colour stage (3D) with the cell's u values staged in shared memory.  One CTA
@@ -1054,19 +1059,18 @@ __global__ void __launch_bounds__(1024) k_coarse(int n0f, const int* __restrict_
 // ---------------------------------------------------------------- reductions (row 8, row 11)
 
 // Per node p of a cell's closure (one node per thread, one grid row per cell), the symmetric-form
-// contribution, summed over the block into part[cell][block]; the per-node form:
+// contribution (written to part[cell][node]):
 //   c_p = S[t][0] x_p y_p + sum_{d positive, valid} S[t][d] (x_p y_{p+d} + x_{p+d} y_p),
 // with x = y = a - b (b may be null) for the mass form, or x = a, y = b for a bilinear form.  Summed
 // over the closure this is x^T S_T y, because the partial stencil of a cell is symmetric (the entry
 // p->p+d seen from p equals the entry p+d->p seen from p+d: both sum the cell's elements on that
-// edge), so each lattice edge is visited once.  The block sums land in a scratch vector (cells x
-// blocks); k_cell_sum adds each cell's block sums in a fixed order.
+// edge), so each lattice edge is visited once.  k_cell_sum adds each cell's contributions in a fixed
+// order.
 template <int DIM, bool DIFF>
 __global__ void __launch_bounds__(kBlock) k_node_form(LevelCtx lc, const double* __restrict__ tab,
                                                       const double* __restrict__ a, const double* __restrict__ b,
                                                       double* __restrict__ part) {
   grid_dependency_sync();
-  __shared__ double sh[kBlock];
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int T = blockIdx.y;
   double sum = 0;
@@ -1107,15 +1111,8 @@ __global__ void __launch_bounds__(kBlock) k_node_form(LevelCtx lc, const double*
       }
     }
     sum = DIFF ? xp * (s[0] * xp + 2.0 * ay) : xp * (s[0] * yp + ay) + yp * ax;
+    part[(int64_t)T * lc.Nt + loc] = sum;
   }
-  // deterministic block sum: shared-memory tree (one binary64 add per node in total)
-  sh[threadIdx.x] = sum;
-  __syncthreads();
-  for (int w = kBlock / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) part[(int64_t)T * gridDim.x + blockIdx.x] = sh[0];
 }
 
 // ---------------------------------------------------------------- operators for testing / adjoint

@@ -177,32 +177,38 @@ static void interior32(hhg_mesh_s* m, int l, int gi, int colour, U* u, const flo
   const Group& G = m->groups[gi];
   int64_t a = Lv.icol_off[gi][colour], b = Lv.icol_off[gi][colour + 1];
   if (b <= a || G.cells.empty()) return;
-  // 3D binary32 values: the stage with u staged through shared memory, one CTA per plane range and cell
-  if (DIM == 3 && std::is_same<U, float>::value && Lv.nranges > 0 && Lv.tile_smem4 + 16 <= kMaxTileSmem) {
-    cudaFuncSetAttribute(k_smooth_interior_tiled<PM, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kMaxTileSmem);
-    dim3 grid((unsigned)Lv.nranges, (unsigned)G.cells.size());
-    hhg_launch(k_smooth_interior_tiled<PM, float>, grid, kBlock, Lv.tile_smem4 + 16, s, G.d_cells, ctx(m, l),
-               Lv.d_tiles + Lv.tile_off[gi][colour], Lv.d_icol, m->d_tnormf, Lv.d_invlf, (float*)u, rhs, m->d_err);
-    return;
-  }
-  dim3 grid(blocks_for(b - a), (unsigned)G.cells.size());
-  hhg_launch(k_smooth_interior<DIM, PM, float, U, float>, grid, kBlock, 0, s, 
-      G.d_cells, Lv.d_icol + a, b - a, ctx(m, l), m->d_tnormf, Lv.d_invlf, vec_of<U>(m, l, u),
-      CVec<float, float>{rhs, nullptr});
+  // two cells per thread: the list entry and offsets shared, both cells' loads in flight together
+  constexpr int CPB = 2;
+  dim3 grid(blocks_for(b - a), (unsigned)((G.cells.size() + CPB - 1) / CPB));
+  hhg_launch(k_smooth_interior_multi<DIM, PM, CPB, float, U, float>, grid, kBlock, 0, s, G.d_cells,
+             (int)G.cells.size(), Lv.d_icol + a, b - a, ctx(m, l), m->d_tnormf, Lv.d_invlf, vec_of<U>(m, l, u),
+             CVec<float, float>{rhs, nullptr});
 }
 
-// the two-cells-per-thread list kernel (profiling comparison with the staged kernel)
-template <int DIM, int PM, typename U>
-static void interior32_x2(hhg_mesh_s* m, int l, int gi, int colour, U* u, const float* rhs, cudaStream_t s) {
+// the list kernel with four cells per thread, for comparison in profiling
+template <int DIM, int PM>
+static void interior32_x4(hhg_mesh_s* m, int l, int gi, int colour, float* u, const float* rhs, cudaStream_t s) {
   const LevelData& Lv = m->lv[l];
   const Group& G = m->groups[gi];
   int64_t a = Lv.icol_off[gi][colour], b = Lv.icol_off[gi][colour + 1];
   if (b <= a || G.cells.empty()) return;
-  dim3 grid(blocks_for(b - a), (unsigned)((G.cells.size() + 1) / 2));
-  hhg_launch(k_smooth_interior_x2<DIM, PM, float, U, float>, grid, kBlock, 0, s, G.d_cells, (int)G.cells.size(),
-             Lv.d_icol + a, b - a, ctx(m, l), m->d_tnormf, Lv.d_invlf, vec_of<U>(m, l, u),
+  dim3 grid(blocks_for(b - a), (unsigned)((G.cells.size() + 3) / 4));
+  hhg_launch(k_smooth_interior_multi<DIM, PM, 4, float, float, float>, grid, kBlock, 0, s, G.d_cells,
+             (int)G.cells.size(), Lv.d_icol + a, b - a, ctx(m, l), m->d_tnormf, Lv.d_invlf, vec_of<float>(m, l, u),
              CVec<float, float>{rhs, nullptr});
+}
+
+// the staged (shared-memory) variant of the 3D binary32 interior stage, for comparison in profiling
+template <int PM>
+static void interior32_tiled(hhg_mesh_s* m, int l, int gi, int colour, float* u, const float* rhs, cudaStream_t s) {
+  const LevelData& Lv = m->lv[l];
+  const Group& G = m->groups[gi];
+  if (Lv.nranges == 0 || Lv.tile_smem4 + 16 > kMaxTileSmem || G.cells.empty()) return;
+  cudaFuncSetAttribute(k_smooth_interior_tiled<PM, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kMaxTileSmem);
+  dim3 grid((unsigned)Lv.nranges, (unsigned)G.cells.size());
+  hhg_launch(k_smooth_interior_tiled<PM, float>, grid, kBlock, Lv.tile_smem4 + 16, s, G.d_cells, ctx(m, l),
+             Lv.d_tiles + Lv.tile_off[gi][colour], Lv.d_icol, m->d_tnormf, Lv.d_invlf, u, rhs, m->d_err);
 }
 
 template <int DIM, typename U>
@@ -451,7 +457,7 @@ hhg_status mixed_prepare(hhg_mesh_s* m, int storage) {
 }
 
 hhg_status mixed_profile_interior(hhg_mesh_s* m, int reps, cudaStream_t s, long long* units, double* bytes,
-                                  double* flops, bool x2) {
+                                  double* flops, int variant) {
   const int L = m->L;
   LevelData& Lv = m->lv[L];
   const Group& G = m->groups[0];
@@ -462,11 +468,14 @@ hhg_status mixed_profile_interior(hhg_mesh_s* m, int reps, cudaStream_t s, long 
   *bytes = 4.0 * ((double)Lv.Nt * G.cells.size() + 2.0 * nodes);
   *flops = (4.0 * p + 1.0) * nodes;
   for (int r = 0; r < reps; ++r) {
-    if (x2) {
-      // the two-cells-per-thread list kernel of the group's pattern
-      if (m->dim == 2) interior32_x2<2, 0x7, float>(m, L, 0, 0, Lv.x32, Lv.b32, s);
-      else if (G.pmask == 0x29) interior32_x2<3, 0x29, float>(m, L, 0, 0, Lv.x32, Lv.b32, s);
-      else interior32_x2<3, 0x7f, float>(m, L, 0, 0, Lv.x32, Lv.b32, s);
+    if (variant == 1) {
+      // the staged variant (3D)
+      if (m->dim == 3 && G.pmask == 0x29) interior32_tiled<0x29>(m, L, 0, 0, Lv.x32, Lv.b32, s);
+      else if (m->dim == 3) interior32_tiled<0x7f>(m, L, 0, 0, Lv.x32, Lv.b32, s);
+    } else if (variant == 2) {
+      // four cells per thread (3D)
+      if (m->dim == 3 && G.pmask == 0x29) interior32_x4<3, 0x29>(m, L, 0, 0, Lv.x32, Lv.b32, s);
+      else if (m->dim == 3) interior32_x4<3, 0x7f>(m, L, 0, 0, Lv.x32, Lv.b32, s);
     } else if (m->dim == 2) {
       interior32_dispatch<2, float>(m, L, 0, 0, Lv.x32, Lv.b32, s);
     } else {
