@@ -171,7 +171,7 @@ int hhg_lattice_selfcheck(int dim, int n);
  * kernels 2, 3, 4 (binary64): the level-L prolongation-add, residual (every node computed) and
  * estimator mass form of one vector (units = level-L nodes); kernel 5 (binary32, 3D): the interior
  * stage of kernel 0 staged through shared memory by bulk copies; kernel 6 (binary32, 3D): the same
- * stage with four cells per thread (both for comparison with the two-cells-per-thread kernel).
+ * stage with two cells per thread (both for comparison with the four-cells-per-thread kernel).
  * precision 0: the binary64 kernel; 1: the binary32 kernel of the mixed path (its buffers are
  * allocated on first use).  units: nodes updated per launch; bytes / flops: algorithmic bytes and floating-point
  * operations of one launch (the model is stated in the library's design notes).  The launches

@@ -169,10 +169,10 @@ static void residual_group(hhg_mesh_s* m, int l, int gi, const double* rhs, cuda
   const Group& G = m->groups[gi];
   ResidualSegments rs = residual_segments(Lv, G, gi, after_sweep);
   dim3 grid(rs.bcomp + rs.bzero + blocks_for(Lv.nbnd), (unsigned)G.cells.size());
-  hhg_launch(k_residual_list<DIM, PM, double, double, double, double>, grid, kBlock, 0, s, 
-      G.d_cells, ctx(m, l), m->dS, m->d_dirmask, stiff_scale(DIM, Lv.n), CVec<double, double>{Lv.u, nullptr},
-      CVec<double, double>{rhs, nullptr}, Lv.tmp, rs.ilist, rs.ncomp, rs.nzero, Lv.d_bnd, Lv.nbnd, rs.bcomp,
-      rs.bzero);
+  hhg_launch(k_residual_list<DIM, PM, 1, true, double, double, double, double>, grid, kBlock, 0, s, G.d_cells,
+             (int)G.cells.size(), ctx(m, l), m->dS, m->d_dirmask, stiff_scale(DIM, Lv.n),
+             CVec<double, double>{Lv.u, nullptr}, CVec<double, double>{rhs, nullptr}, Lv.tmp, rs.ilist, rs.ncomp,
+             rs.nzero, Lv.d_bnd, Lv.nbnd, rs.bcomp, rs.bzero);
 }
 
 void launch_residual_after(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s, bool after_sweep);

@@ -840,42 +840,56 @@ inline ResidualSegments residual_segments(const LevelData& Lv, const Group& G, i
 // pattern PM; blocks [bcomp, bcomp + bzero) write 0 at entries [ncomp, ncomp + nzero) (the interior
 // colour updated last, directly after a sweep); the remaining blocks take the boundary-type nodes
 // (list sorted by type, so a warp mostly shares one slot mask), zero on Dirichlet types.
-template <int DIM, int PM, typename R, typename U, typename B, typename O>
-__global__ void __launch_bounds__(kBlock) k_residual_list(const int* __restrict__ gcells, LevelCtx lc,
+template <int DIM, int PM, int CPB, bool SPARSE, typename R, typename U, typename B, typename O>
+__global__ void __launch_bounds__(kBlock) k_residual_list(const int* __restrict__ gcells, int ncells, LevelCtx lc,
                                                           const R* __restrict__ S, const uint16_t* __restrict__ dirmask,
                                                           R sscale, CVec<R, U> u, CVec<R, B> rhs, O* __restrict__ out,
                                                           const int2* __restrict__ ilist, int64_t ncomp, int64_t nzero,
                                                           const int2* __restrict__ blist, int64_t nbnd, unsigned bcomp,
                                                           unsigned bzero) {
   grid_dependency_sync();
-  int T = gcells[blockIdx.y];
+  const int c0 = CPB * blockIdx.y;
+  int Ts[CPB];
+#pragma unroll
+  for (int c = 0; c < CPB; ++c) Ts[c] = gcells[min(c0 + c, ncells - 1)];  // a short last group repeats
   unsigned bx = blockIdx.x;
-  const int64_t cell0 = (int64_t)T * lc.Nt;
   if (bx < bcomp) {
     int64_t pos = (int64_t)bx * blockDim.x + threadIdx.x;
     if (pos >= ncomp) return;
     int2 e = ilist[pos];
     if (HHG_OOB(e.x, lc.Nt, 52)) return;
     int j = e.y & 0xffff, k = e.y >> 16;
-    int64_t g = cell0 + e.x;
     int64_t off[15];
     neighbour_offsets(DIM, lc.n, j, k, off);
-    const R* s = S + (size_t)T * kStencilStride;  // interior type 0
-    R acc = s[0] * u.get(g);
+    int64_t g[CPB];
+    const R* st[CPB];
+    R acc[CPB];
+#pragma unroll
+    for (int c = 0; c < CPB; ++c) {
+      g[c] = (int64_t)Ts[c] * lc.Nt + e.x;
+      st[c] = S + (size_t)Ts[c] * kStencilStride;  // interior type 0
+      acc[c] = st[c][0] * u.get(g[c]);
+    }
 #pragma unroll
     for (int q = 0; q < npairs<DIM>(); ++q) {
       if (PM >> q & 1) {
-        acc += s[2 * q + 1] * u.get(g + off[2 * q + 1]);
-        acc += s[2 * q + 2] * u.get(g + off[2 * q + 2]);
+#pragma unroll
+        for (int c = 0; c < CPB; ++c) acc[c] += st[c][2 * q + 1] * u.get(g[c] + off[2 * q + 1]);
+#pragma unroll
+        for (int c = 0; c < CPB; ++c) acc[c] += st[c][2 * q + 2] * u.get(g[c] + off[2 * q + 2]);
       }
     }
-    out[g] = (dirmask[T] & 1) ? (O)0 : (O)(rhs.get(g) - sscale * acc);
+#pragma unroll
+    for (int c = 0; c < CPB; ++c)
+      if (c0 + c < ncells) out[g[c]] = (dirmask[Ts[c]] & 1) ? (O)0 : (O)(rhs.get(g[c]) - sscale * acc[c]);
   } else if (bx < bcomp + bzero) {
     int64_t pos = (int64_t)(bx - bcomp) * blockDim.x + threadIdx.x;
     if (pos >= nzero) return;
     int loc = ilist[ncomp + pos].x;
     if (HHG_OOB(loc, lc.Nt, 53)) return;
-    out[cell0 + loc] = (O)0;
+#pragma unroll
+    for (int c = 0; c < CPB; ++c)
+      if (c0 + c < ncells) out[(int64_t)Ts[c] * lc.Nt + loc] = (O)0;
   } else {
     int64_t pos = (int64_t)(bx - bcomp - bzero) * blockDim.x + threadIdx.x;
     if (pos >= nbnd) return;
@@ -883,23 +897,37 @@ __global__ void __launch_bounds__(kBlock) k_residual_list(const int* __restrict_
     if (HHG_OOB(e.x, lc.Nt, 54)) return;
     int i, j, k;
     decode(e.y, i, j, k);
-    int t = boundary_type(DIM, lc.n, i, j, k);
-    int64_t g = cell0 + e.x;
-    if (dirmask[T] >> t & 1) {
-      out[g] = (O)0;
-      return;
+    const int t = boundary_type(DIM, lc.n, i, j, k);
+#pragma unroll
+    for (int c = 0; c < CPB; ++c) {
+      if (c0 + c >= ncells) continue;
+      const int T = Ts[c];
+      const int64_t g = (int64_t)T * lc.Nt + e.x;
+      if (dirmask[T] >> t & 1) {
+        out[g] = (O)0;
+        continue;
+      }
+      uint32_t vm = valid_dirs_tab(DIM, t) & lc.nzs[T * kMaxTypes + t];
+      const R* s = S + (size_t)T * kStencilStride + t * kMaxDirs;
+      R acc = s[0] * u.get(g);
+      if (SPARSE) {  // binary64: only the nonzero terms (DFMA-bound)
+        PlaneBasis pb = plane_basis(DIM, lc.n, k);
+        for (uint32_t mm = vm & ~1u; mm; mm &= mm - 1) {
+          int d = __ffs(mm) - 1;
+          int64_t o = dir_offset(DIM, d, pb.m, j, pb.Tm, pb.Tm1);
+          if (HHG_OOB(e.x + o, lc.Nt, 55)) continue;
+          acc += s[d] * u.get(g + o);
+        }
+      } else {  // binary32: every slot unrolled, the loads issued together
+        int64_t off[15];
+        neighbour_offsets(DIM, lc.n, j, k, off);
+        mask_offsets(DIM, vm, off);
+#pragma unroll
+        for (int d = 1; d < ndirs<DIM>(); ++d)
+          if ((vm >> d & 1) && !HHG_OOB(e.x + off[d], lc.Nt, 55)) acc += s[d] * u.get(g + off[d]);
+      }
+      out[g] = (O)(rhs.get(g) - sscale * acc);
     }
-    uint32_t vm = valid_dirs_tab(DIM, t) & lc.nzs[T * kMaxTypes + t];
-    PlaneBasis pb = plane_basis(DIM, lc.n, k);
-    const R* s = S + (size_t)T * kStencilStride + t * kMaxDirs;
-    R acc = s[0] * u.get(g);
-    for (uint32_t mm = vm & ~1u; mm; mm &= mm - 1) {
-      int d = __ffs(mm) - 1;
-      int64_t o = dir_offset(DIM, d, pb.m, j, pb.Tm, pb.Tm1);
-      if (HHG_OOB(e.x + o, lc.Nt, 55)) continue;
-      acc += s[d] * u.get(g + o);
-    }
-    out[g] = (O)(rhs.get(g) - sscale * acc);
   }
 }
 
