@@ -78,7 +78,8 @@ def allmax(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -155,7 +156,7 @@ def peaks():
 FP64_PEAK_TFLOPS = 1.205
 # DRAM bytes (read + write) of one launch of the roofline kernel on the 384-tet cube at L = 6, from
 # one ncu capture of that kernel (summarised under profiles/); None for other workloads
-TRAFFIC_BYTES = {("cube384_l6", "fp64"): 369.5e6}
+TRAFFIC_BYTES = {("cube384_l6", "fp64"): 369.5e6, ("cube384_l6", "mixed"): 165.6e6}
 
 
 # ----------------------------------------------------------------------------- arms

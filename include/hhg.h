@@ -58,8 +58,14 @@ typedef enum {
  * precision = 1 (mixed, no counterpart in the paper): iterative refinement whose residual
  *   r = b - A u and update u += c are binary64 on level L; the correction c solves A c = r with
  *   FMG (first step) or ir_vcycles V-cycles (later steps) computed in binary32, with the level
- *   vectors of the correction stored as `storage` (0 = binary32, 1 = bfloat16, 2 = binary16)
- *   and accumulated in binary32.  ir_steps refinement steps follow the first one. */
+ *   vectors of the correction stored as `storage` (0 = binary32, 1 = bfloat16; 2 = binary16 is
+ *   rejected with HHG_ERR_ARG) and accumulated in binary32.  ir_steps refinement steps follow the
+ *   first one.
+ * One Gauss-Seidel sweep updates, in this order: the macro vertices together with the even
+ * edge-local nodes, the odd edge nodes, (3D) the face block - every macro face by Gauss-Seidel
+ * over its colours (a + 2b) mod 3 with all nodes outside the face at their values from the start
+ * of the block - and the macro-cell interiors by colours (alpha . p) mod m.  Nodes of one stage
+ * are updated from the values at the start of the stage. */
 typedef struct {
   int nu, pre, post, n_extra;
   int precision;
