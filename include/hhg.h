@@ -38,6 +38,7 @@ extern "C" {
 
 typedef struct hhg_mesh_s* hhg_mesh;
 typedef struct hhg_rg2d_s* hhg_rg2d;
+typedef struct hhg_rg3d_s* hhg_rg3d;
 
 typedef enum {
   HHG_OK = 0,
@@ -156,6 +157,25 @@ hhg_status hhg_rg2d_mesh(hhg_rg2d rg, int* n_verts, double* coords, int* n_cells
 hhg_status hhg_rg2d_destroy(hhg_rg2d rg);
 /* Marking + one red-green step: marked (host, n_cells of the current mesh, may be NULL). */
 hhg_status hhg_mark_refine(hhg_rg2d rg, const double* eta_T, double fraction, unsigned char* marked);
+
+/* 3D red-green refinement of a tetrahedral macro mesh (Alg. 3, Sec. 3), the k-step of the 3D
+ * kl loop (host, sequential).  One step: revert the green families of the previous step (a
+ * marked green child marks its parent); red-refine the marked tets (Bey's eight children, all
+ * with the parent's orientation); repeat { split the third edge of every face with two split
+ * edges; red-refine every tet with more than three split edges, a split edge whose half is split
+ * again, or a fully split face with a split midline } until nothing changes; then close each tet
+ * with one to three split edges by one of three green types (one edge: 2 children; two opposite
+ * edges: 4; the three edges of one face: 4).  New vertices are edge midpoints numbered in
+ * creation order; refined tets are replaced in place by their children.  coords: host,
+ * n_verts*3; cells: host, n_cells*4, 0-based.  Errors: HHG_ERR_ARG (sizes, vertex ids),
+ * HHG_ERR_STATE (corrupt state), HHG_ERR_OOM. */
+hhg_status hhg_rg3d_create(int n_verts, const double* coords, int n_cells, const int* cells, hhg_rg3d* out);
+hhg_status hhg_rg3d_refine(hhg_rg3d rg, const unsigned char* marked /* host, one flag per current cell */);
+/* Current conforming mesh; pass NULL arrays to query the sizes first. */
+hhg_status hhg_rg3d_mesh(hhg_rg3d rg, int* n_verts, double* coords, int* n_cells, int* cells);
+hhg_status hhg_rg3d_destroy(hhg_rg3d rg);
+/* Marking (hhg_mark) + one 3D red-green step: marked (host, n_cells of the current mesh, may be NULL). */
+hhg_status hhg_rg3d_mark_refine(hhg_rg3d rg, const double* eta_T, double fraction, unsigned char* marked);
 
 /* Adjoint of the discrete solve (no counterpart in the paper): for J(u) = u^T M_S u with
  * M_S the mass matrix of the micro elements inside the macro cells flagged in in_S, on the

@@ -800,6 +800,166 @@ class RG2D:
         self.tris = out
 
 
+_TET_EDGES = ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))
+_TET_FACES = ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3))
+
+
+class RG3D:
+    """Red-green refinement of a tetrahedral mesh following Alg. 3 (Sec. 3).
+
+    A tet is stored by its four vertex ids (its slots 0..3); an edge (a,b) is split when its
+    midpoint vertex exists.  One step (marked = flags on the current conforming mesh):
+      1. revert every green family to its parent; a marked green child marks the parent;
+      2. repeat: red-refine the flagged tets (Bey's eight children, x_ab = midpoint of slots a, b:
+         (x0,x01,x02,x03), (x01,x1,x12,x13), (x02,x12,x2,x23), (x03,x13,x23,x3), (x01,x02,x03,x13),
+         (x02,x01,x12,x13), (x02,x03,x13,x23), (x12,x02,x13,x23) -- the sixth and eighth with two
+         slots swapped so that every child keeps the parent's orientation); then split the third
+         edge of every face with exactly two split edges, until no such face is left; flag the
+         tets with more than three split edges, or a split edge whose half is split again, or a
+         fully split face one of whose midlines is split -- until nothing is flagged;
+      3. green closure of every tet with one to three split edges (after step 2 these are one
+         edge, two opposite edges, or the three edges of one face):
+           one edge (slots i<j, midpoint m): T with slot j := m, T with slot i := m;
+           two opposite edges: the one-edge rule on the first (in edge order
+             01,02,03,12,13,23), then on the second inside each half (four children);
+           one face (slots a<b<c, midpoints m_ab, m_bc, m_ca): T with (b, c) := (m_ab, m_ca),
+             T with (a, c) := (m_ab, m_bc), T with (a, b) := (m_ca, m_bc), and T with
+             (a, b, c) := (m_bc, m_ca, m_ab) (four children; all keep the orientation).
+    New vertices are numbered in creation order: tets in list order, edges in the order above,
+    faces in the order 012, 013, 023, 123.  Refined tets are replaced in place by their children.
+    """
+
+    def __init__(self, coords, cells):
+        self.coords = [tuple(float(c) for c in p) for p in np.asarray(coords, dtype=np.float64)]
+        # entries: (vertex 4-tuple, green parent 4-tuple or None, child index, children in family)
+        self.tets = [(tuple(int(v) for v in c), None, -1, 0) for c in np.asarray(cells)]
+        self.mid = {}
+
+    def mesh(self):
+        return (np.array(self.coords, dtype=np.float64),
+                np.array([t[0] for t in self.tets], dtype=np.int32).reshape(-1, 4))
+
+    def _midpoint(self, a, b, create):
+        key = (min(a, b), max(a, b))
+        m = self.mid.get(key)
+        if m is None and create:
+            pa, pb = self.coords[a], self.coords[b]
+            self.coords.append(((pa[0] + pb[0]) * 0.5, (pa[1] + pb[1]) * 0.5, (pa[2] + pb[2]) * 0.5))
+            m = len(self.coords) - 1
+            self.mid[key] = m
+        return m
+
+    def _red(self, t):
+        x = {}
+        for a, b in _TET_EDGES:
+            x[(a, b)] = self._midpoint(t[a], t[b], True)
+        x0, x1, x2, x3 = t
+        x01, x02, x03, x12, x13, x23 = (x[e] for e in _TET_EDGES)
+        return [(x0, x01, x02, x03), (x01, x1, x12, x13), (x02, x12, x2, x23), (x03, x13, x23, x3),
+                (x01, x02, x03, x13), (x02, x01, x12, x13), (x02, x03, x13, x23), (x12, x02, x13, x23)]
+
+    def _split_edges(self, t):
+        return [e for e, (a, b) in enumerate(_TET_EDGES) if self._midpoint(t[a], t[b], False) is not None]
+
+    def _over(self, t):
+        for a, b in _TET_EDGES:
+            m = self._midpoint(t[a], t[b], False)
+            if m is not None and (self._midpoint(t[a], m, False) is not None or
+                                  self._midpoint(m, t[b], False) is not None):
+                return True
+        for f in _TET_FACES:
+            ms = [self._midpoint(t[f[0]], t[f[1]], False), self._midpoint(t[f[1]], t[f[2]], False),
+                  self._midpoint(t[f[2]], t[f[0]], False)]
+            if all(m is not None for m in ms):
+                for i in range(3):
+                    if self._midpoint(ms[i], ms[(i + 1) % 3], False) is not None:
+                        return True
+        return False
+
+    def _close_faces(self, tets):
+        changed = True
+        while changed:
+            changed = False
+            for t in tets:
+                for f in _TET_FACES:
+                    edges = [(t[f[0]], t[f[1]]), (t[f[1]], t[f[2]]), (t[f[0]], t[f[2]])]
+                    have = [self._midpoint(a, b, False) is not None for a, b in edges]
+                    if sum(have) == 2:
+                        a, b = edges[have.index(False)]
+                        self._midpoint(a, b, True)
+                        changed = True
+
+    def _green(self, t, split):
+        def sub(tt, slot, v):
+            tt = list(tt)
+            tt[slot] = v
+            return tuple(tt)
+        if len(split) == 1:
+            i, j = _TET_EDGES[split[0]]
+            m = self._midpoint(t[i], t[j], False)
+            return [sub(t, j, m), sub(t, i, m)]
+        if len(split) == 2:
+            (i, j), (k, l) = _TET_EDGES[split[0]], _TET_EDGES[split[1]]
+            m1 = self._midpoint(t[i], t[j], False)
+            m2 = self._midpoint(t[k], t[l], False)
+            out = []
+            for half in (sub(t, j, m1), sub(t, i, m1)):
+                out.extend([sub(half, l, m2), sub(half, k, m2)])
+            return out
+        # three edges of one face
+        for f in _TET_FACES:
+            fe = {_TET_EDGES.index((f[0], f[1])), _TET_EDGES.index((f[1], f[2])), _TET_EDGES.index((f[0], f[2]))}
+            if fe == set(split):
+                a, b, c = f
+                mab = self._midpoint(t[a], t[b], False)
+                mbc = self._midpoint(t[b], t[c], False)
+                mca = self._midpoint(t[c], t[a], False)
+                return [sub(sub(t, b, mab), c, mca), sub(sub(t, a, mab), c, mbc), sub(sub(t, a, mca), b, mbc),
+                        sub(sub(sub(t, a, mbc), b, mca), c, mab)]
+        raise AssertionError("split pattern is not a green type")
+
+    def refine(self, marked):
+        marked = np.asarray(marked).astype(bool)
+        if len(marked) != len(self.tets):
+            raise ValueError("one flag per current cell")
+        # 1. revert greens
+        R, flags = [], []
+        i = 0
+        while i < len(self.tets):
+            v, parent, ci, nch = self.tets[i]
+            if parent is not None:
+                fam = self.tets[i:i + nch]
+                if ci != 0 or len(fam) != nch or any(f[1] != parent or f[2] != q for q, f in enumerate(fam)):
+                    raise AssertionError("green family not contiguous")
+                R.append(parent)
+                flags.append(bool(marked[i:i + nch].any()))
+                i += nch
+            else:
+                R.append(v)
+                flags.append(bool(marked[i]))
+                i += 1
+        # 2. red refinement and closure
+        while True:
+            newR = []
+            for t, fl in zip(R, flags):
+                newR.extend(self._red(t) if fl else [t])
+            R = newR
+            self._close_faces(R)
+            flags = [len(self._split_edges(t)) > 3 or self._over(t) for t in R]
+            if not any(flags):
+                break
+        # 3. green closure
+        out = []
+        for t in R:
+            split = self._split_edges(t)
+            if split:
+                ch = self._green(t, split)
+                out.extend((c, t, q, len(ch)) for q, c in enumerate(ch))
+            else:
+                out.append((t, None, -1, 0))
+        self.tets = out
+
+
 # --------------------------------------------------------------------------------------
 # Adjoint of the discrete solve: gradients of J(u) = u^T M_S u (no counterpart in the paper)
 # --------------------------------------------------------------------------------------

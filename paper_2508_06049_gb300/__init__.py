@@ -6,5 +6,5 @@ adjoint solve.
 """
 
 from .hhg import (  # noqa: F401
-    HHGError, Mesh, RG2D, SolveParams, lattice_selfcheck, lib, mark, solve_params,
+    HHGError, Mesh, RG2D, RG3D, SolveParams, lattice_selfcheck, lib, mark, solve_params,
 )

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIBNAME = "libhhg.so"
 
 CUDA_SOURCES = ["setup.cu", "kernels.cu", "kernels_mixed.cu", "kernels_noalloc.cu", "capi.cu"]
-CXX_SOURCES = ["rg2d.cpp"]
+CXX_SOURCES = ["rg2d.cpp", "rg3d.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -72,6 +72,11 @@ def lib():
         "hhg_rg2d_mesh": [vp, C.POINTER(i), vp, C.POINTER(i), vp],
         "hhg_rg2d_destroy": [vp],
         "hhg_mark_refine": [vp, vp, d, u8],
+        "hhg_rg3d_create": [i, vp, i, vp, C.POINTER(vp)],
+        "hhg_rg3d_refine": [vp, u8],
+        "hhg_rg3d_mesh": [vp, C.POINTER(i), vp, C.POINTER(i), vp],
+        "hhg_rg3d_destroy": [vp],
+        "hhg_rg3d_mark_refine": [vp, vp, d, u8],
         "hhg_adjoint_l2": [vp, C.POINTER(SolveParams), u8, C.POINTER(d), vp, vp],
         "hhg_lattice_selfcheck": [i, i],
         "hhg_debug_check": [vp],
@@ -262,6 +267,42 @@ class RG2D:
         eta = _f64(eta)
         marked = np.zeros(len(eta), dtype=np.uint8)
         _check(lib().hhg_mark_refine(self._h, _ptr(eta), float(fraction), _ptr(marked)))
+        return marked.astype(bool)
+
+
+class RG3D:
+    """Host 3D red-green refinement object (hhg_rg3d_*)."""
+
+    def __init__(self, coords, cells):
+        co = _f64(coords)
+        ce = np.ascontiguousarray(np.asarray(cells, dtype=np.int32))
+        h = C.c_void_p()
+        _check(lib().hhg_rg3d_create(len(co), _ptr(co), len(ce), _ptr(ce), C.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        try:
+            if self._h:
+                lib().hhg_rg3d_destroy(self._h)
+        except Exception:
+            pass
+
+    def mesh(self):
+        nv, nc = C.c_int(), C.c_int()
+        _check(lib().hhg_rg3d_mesh(self._h, C.byref(nv), None, C.byref(nc), None))
+        co = np.empty((nv.value, 3), dtype=np.float64)
+        ce = np.empty((nc.value, 4), dtype=np.int32)
+        _check(lib().hhg_rg3d_mesh(self._h, C.byref(nv), _ptr(co), C.byref(nc), _ptr(ce)))
+        return co, ce
+
+    def refine(self, marked):
+        m = np.ascontiguousarray(np.asarray(marked, dtype=np.uint8))
+        _check(lib().hhg_rg3d_refine(self._h, _ptr(m)))
+
+    def mark_refine(self, eta, fraction):
+        eta = _f64(eta)
+        marked = np.zeros(len(eta), dtype=np.uint8)
+        _check(lib().hhg_rg3d_mark_refine(self._h, _ptr(eta), float(fraction), _ptr(marked)))
         return marked.astype(bool)
 
 
