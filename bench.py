@@ -39,10 +39,14 @@ MIXED_DEFAULT = dict(storage=0, ir_steps=2, ir_vcycles=2)
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 50; --program alg5: 3)")
+    ap.add_argument("--warmup", type=int, default=None, help="warm-up steps (default 5; --program alg5: 1)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="cube384_l6")
+    ap.add_argument("--program", default="step", choices=["step", "alg5"],
+                    help="step: the FMG + estimator + marking step (default); alg5: the scaling program "
+                         "of Sec. 5.4 (solve, estimate, 3D red-green refinement of 12.5 %%, rebuild, solve)")
+    ap.add_argument("--workload", default=None, help="default cube384_l6 (step) or waves3d_l8 (alg5)")
+    ap.add_argument("--level", type=int, default=None, help="--program alg5: override the workload's finest level L")
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
     ap.add_argument("--storage", type=int, default=None, help="mixed arm: 0 binary32, 1 bfloat16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -52,7 +56,15 @@ def parse():
     ap.add_argument("--kernel-id", type=int, default=0,
                     help="with --kernel-only: 0 interior stage, 1 face stage, 2 prolongation-add, 3 residual, "
                          "4 estimator mass form (2-4: level L, binary64)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    alg5 = args.program == "alg5"
+    if args.workload is None:
+        args.workload = "waves3d_l8" if alg5 else "cube384_l6"
+    if args.steps is None:
+        args.steps = 3 if alg5 else 50
+    if args.warmup is None:
+        args.warmup = 1 if alg5 else 5
+    return args
 
 
 # ----------------------------------------------------------------------------- distributed
@@ -380,8 +392,104 @@ def kernel_only(args):
           % (args.kernel_only, args.kernel_id, units, b, fl))
 
 
+def alg5(args):
+    """The scaling program of Sec. 5.4 (Alg. 5) on one GPU, timed phase by phase (wall clock after
+    a device synchronisation): create the hierarchy on T^0 and its data, FMG solve, ErrorEstimate,
+    3D red-green refinement (Alg. 3) of the 12.5 % largest eta_T on the host, create the hierarchy
+    on T^1 and its data, FMG solve.  FMG as in Sec. 5.4: nu = 2 V-cycles per level with two
+    Gauss-Seidel sweeps before and after (V(2,2)), binary64.  The source and the Dirichlet values
+    are evaluated on the device from the level-L coordinates."""
+    import torch
+
+    import paper_2508_06049_gb300 as P
+    co0, ce0, L, f, g, k, ue = make_problem(args.workload, args.level)
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    s = torch.cuda.Stream()
+    prm = P.solve_params(nu=2, pre=2, post=2, n_extra=0, precision=0)
+    chunk = 1 << 25
+
+    def now():
+        torch.cuda.synchronize()
+        return time.perf_counter()
+
+    def setup(co, ce, T, key):
+        t0 = now()
+        mesh = P.Mesh(co, ce, L, stream=s)
+        if k is not None:
+            mesh.set_coefficient(k)
+        t1 = now()
+        N = mesh.n_nodes(L)
+        x = torch.empty((N, co.shape[1]), dtype=torch.float64, device="cuda")
+        mesh.level_coords(L, out=x)
+        fd = torch.empty(N, dtype=torch.float64, device="cuda")
+        gd = torch.empty_like(fd)
+        for a in range(0, N, chunk):
+            fd[a:a + chunk] = f(x[a:a + chunk])
+            gd[a:a + chunk] = g(x[a:a + chunk])
+        del x
+        torch.cuda.synchronize()
+        mesh.set_data(fd, gd)
+        t2 = now()
+        T["create_" + key] = t1 - t0
+        T["data_" + key] = t2 - t1
+        return mesh, fd, gd
+
+    def run():
+        T = {}
+        mesh0, f0, g0 = setup(co0, ce0, T, "T0")
+        u0 = torch.empty_like(f0)
+        t0 = now()
+        mesh0.solve(prm, out=u0)
+        t1 = now()
+        est = mesh0.estimate(1)
+        t2 = now()
+        rg = P.RG3D(co0, ce0)
+        marked = rg.mark_refine(est["eta_T"], 0.125)
+        co1, ce1 = rg.mesh()
+        t3 = now()
+        T.update(solve_T0=t1 - t0, estimate_T0=t2 - t1, refine=t3 - t2)
+        n0 = mesh0.info.n_unknowns
+        mesh0.close()
+        del u0, f0, g0
+        mesh1, f1, g1 = setup(co1, ce1, T, "T1")
+        u1 = torch.empty_like(f1)
+        t4 = now()
+        mesh1.solve(prm, out=u1)
+        T["solve_T1"] = now() - t4
+        err = float((u1 - g1).abs().max()) if ue is g else None
+        info = dict(cells_T0=len(ce0), cells_T1=len(ce1), marked=int(marked.sum()), unknowns_T0=int(n0),
+                    unknowns_T1=int(mesh1.info.n_unknowns), max_nodal_error_T1=err)
+        mesh1.close()
+        del u1, f1, g1
+        return T, info
+
+    for _ in range(args.warmup):
+        run()
+    clk = ClockSampler(dev)
+    clk.start()
+    runs = [run() for _ in range(args.steps)]
+    clocks = clk.stop()
+    tot = [sum(T.values()) for T, _ in runs]
+    phases = {key: statistics.mean(T[key] for T, _ in runs) for key in runs[0][0]}
+    info = runs[-1][1]
+    line = {"program": "alg5", "metric": "Alg. 5 total time (T^0 setup, FMG, eta_T, 3D red-green 12.5 %, "
+                                         "T^1 setup, FMG)",
+            "value": statistics.mean(tot), "unit": "s", "higher_is_better": False, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "runs_s": tot, "phases_s": phases,
+            "solve_T1_dof_per_s": info["unknowns_T1"] / phases["solve_T1"], "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "L": L, "fmg": "nu=2 V(2,2), estimator j=1, marking 12.5%",
+                       "coarse": "dense Cholesky", **info},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.program == "alg5":
+        alg5(args)
+        return
     if args.kernel_only:
         kernel_only(args)
         return

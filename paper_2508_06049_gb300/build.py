@@ -1,6 +1,9 @@
 """Build libhhg.so (the C-ABI library) in-tree for sm_103a with nvcc.
 
-Translation units are compiled in parallel; the result goes to paper_2508_06049_gb300/lib/.
+Translation units are compiled in parallel; the result goes to paper_2508_06049_gb300/lib/.  Host
+code is compiled with -ffp-contract=off: without it GCC fuses multiply-adds on Arm but not on x86,
+and host results (stencils, coordinates, refined meshes) would differ between the two in the last
+bit.
 Usage: python -m paper_2508_06049_gb300.build [--debug]
 """
 
@@ -42,7 +45,7 @@ def build(debug: bool = False, verbose: bool = False, check: bool = False) -> st
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     opt = ["-O0", "-g"] if debug else ["-O3"]
-    common = opt + ["-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSRC]
+    common = opt + ["-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-pthread,-ffp-contract=off", "-I", CSRC]
     if check or os.environ.get("HHG_CHECK"):
         common += ["-DHHG_CHECK=1"]
     jobs = []
@@ -52,7 +55,7 @@ def build(debug: bool = False, verbose: bool = False, check: bool = False) -> st
     cxx = shutil.which("g++") or "g++"
     for src in CXX_SOURCES:
         obj = os.path.join(BUILD, src + ".o")
-        jobs.append([cxx] + opt + ["-std=c++17", "-fPIC", "-c", os.path.join(CSRC, src), "-o", obj])
+        jobs.append([cxx] + opt + ["-std=c++17", "-fPIC", "-ffp-contract=off", "-c", os.path.join(CSRC, src), "-o", obj])
     with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
         for r in ex.map(_run, jobs):
             if verbose and (r.stdout or r.stderr):
@@ -60,7 +63,7 @@ def build(debug: bool = False, verbose: bool = False, check: bool = False) -> st
     objs = [os.path.join(BUILD, s + ".o") for s in CUDA_SOURCES + CXX_SOURCES]
     out = os.path.join(LIBDIR, LIBNAME)
     tmp = out + ".tmp"
-    _run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
+    _run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"])
     os.replace(tmp, out)
     return out
 

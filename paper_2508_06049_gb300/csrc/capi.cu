@@ -1,10 +1,13 @@
 // C ABI entry points: mesh life cycle, data, the FMG solve (Alg. 4) captured into CUDA graphs,
 // the error estimator (Alg. 4 ErrorEstimate), test operators and the adjoint.
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -279,26 +282,75 @@ hhg_status hhg_level_coords(hhg_mesh m, int level, double* xyz) {
   DeviceGuard g(m->device);
   const int d = m->dim;
   const LevelData& Lv = m->lv[level];
-  std::vector<double> x((size_t)Lv.N * d);
-  for (int c = 0; c < m->nc; ++c) {
-    const int* cv = &m->cells[(size_t)c * (d + 1)];
-    const double* x0 = &m->coords[(size_t)cv[0] * d];
-    double J[3][3] = {{0}};
-    for (int r = 0; r < d; ++r)
-      for (int q = 0; q < d; ++q) J[r][q] = m->coords[(size_t)cv[q + 1] * d + r] - x0[r];
-    for (int k = 0; k <= (d == 3 ? Lv.n : 0); ++k)
-      for (int j = 0; j <= Lv.n - k; ++j)
-        for (int i = 0; i <= Lv.n - k - j; ++i) {
-          int64_t idx = (int64_t)c * Lv.Nt + packed_index(d, Lv.n, i, j, k);
-          int p[3] = {i, j, k};
-          for (int r = 0; r < d; ++r) {
-            double v = 0;
-            for (int q = 0; q < d; ++q) v += J[r][q] * p[q];
-            x[(size_t)idx * d + r] = x0[r] + v / Lv.n;
-          }
-        }
+  cudaPointerAttributes pa;
+  const bool on_device = cudaPointerGetAttributes(&pa, xyz) == cudaSuccess &&
+                         (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) &&
+                         pa.device == m->device;
+  cudaGetLastError();  // an unregistered host pointer may leave an error behind
+  if (on_device) {
+    // device memory of the mesh's device: one kernel from the per-cell x_0 and J
+    std::vector<double> geom((size_t)m->nc * 12, 0.0);
+    for (int c = 0; c < m->nc; ++c) {
+      const int* cv = &m->cells[(size_t)c * (d + 1)];
+      const double* x0 = &m->coords[(size_t)cv[0] * d];
+      double* G = &geom[(size_t)c * 12];
+      for (int r = 0; r < d; ++r) {
+        G[r] = x0[r];
+        for (int q = 0; q < d; ++q) G[3 + 3 * r + q] = m->coords[(size_t)cv[q + 1] * d + r] - x0[r];
+      }
+    }
+    double* dg = nullptr;
+    CK(cudaMalloc(&dg, geom.size() * sizeof(double)));
+    cudaError_t e = cudaMemcpy(dg, geom.data(), geom.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      launch_level_coords(m, level, dg, xyz, m->stream);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    cudaFree(dg);
+    CK(e);
+    return HHG_OK;
   }
-  CK(cudaMemcpy(xyz, x.data(), x.size() * sizeof(double), cudaMemcpyDefault));
+  const int planes = d == 3 ? Lv.n + 1 : 1;
+  const int64_t per = Lv.Nt * d;  // doubles per cell
+  // cells are filled in batches of at most 2^26 doubles (512 MB) by host threads, one (cell,
+  // plane) pair per work item, and each batch is copied to xyz (host or device) in one piece
+  const int batch = (int)std::max<int64_t>(1, std::min<int64_t>(m->nc, ((int64_t)1 << 26) / per));
+  std::vector<double> buf((size_t)batch * per);
+  const int nthr = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  for (int c0 = 0; c0 < m->nc; c0 += batch) {
+    const int c1 = std::min(m->nc, c0 + batch);
+    std::atomic<int64_t> next(0);
+    const int64_t items = (int64_t)(c1 - c0) * planes;
+    auto work = [&]() {
+      for (int64_t it; (it = next.fetch_add(1)) < items;) {
+        const int c = c0 + (int)(it / planes), k = (int)(it % planes);
+        const int* cv = &m->cells[(size_t)c * (d + 1)];
+        const double* x0 = &m->coords[(size_t)cv[0] * d];
+        double J[3][3] = {{0}};
+        for (int r = 0; r < d; ++r)
+          for (int q = 0; q < d; ++q) J[r][q] = m->coords[(size_t)cv[q + 1] * d + r] - x0[r];
+        double* out = buf.data() + (size_t)(c - c0) * per;
+        for (int j = 0; j <= Lv.n - k; ++j)
+          for (int i = 0; i <= Lv.n - k - j; ++i) {
+            const int64_t q = packed_index(d, Lv.n, i, j, k);
+            const int p[3] = {i, j, k};
+            for (int r = 0; r < d; ++r) {
+              double v = 0;
+              for (int a = 0; a < d; ++a) v += J[r][a] * p[a];
+              out[(size_t)q * d + r] = x0[r] + v / Lv.n;
+            }
+          }
+      }
+    };
+    const int nt = (int)std::min<int64_t>(nthr, items);
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+    work();
+    for (auto& th : pool) th.join();
+    CK(cudaMemcpy(xyz + (size_t)c0 * per, buf.data(), (size_t)(c1 - c0) * per * sizeof(double),
+                  cudaMemcpyDefault));
+  }
   return HHG_OK;
 }
 

@@ -167,6 +167,9 @@ void launch_coarse_solve(hhg_mesh_s* m, const double* rhs, cudaStream_t s);
 void launch_prolong(hhg_mesh_s* m, int l, const double* coarse, double* fine, cudaStream_t s,
                     const double* minuend = nullptr);
 void launch_sub(hhg_mesh_s* m, const double* a, const double* b, double* x, int64_t n, cudaStream_t s);
+// coordinates of the level-l nodes into device memory xyz (N_l * dim doubles); geom: device, per cell
+// x_0 (3 doubles) and J row-major (9 doubles)
+void launch_level_coords(hhg_mesh_s* m, int l, const double* geom, double* xyz, cudaStream_t s);
 void launch_finite_check(hhg_mesh_s* m, const double* v, int64_t n, cudaStream_t s);
 // per-cell reductions on level L: out[T] = (a-b)^T M_T (a-b), b may be null
 void launch_mass_norm_sq(hhg_mesh_s* m, const double* a, const double* b, double* out, cudaStream_t s);

@@ -34,6 +34,25 @@ __global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b
     x[i] = a[i] - b[i];
 }
 
+// Level-l node coordinates x = x_0 + J p / n of every cell's closure lattice (hhg_level_coords into
+// device memory).  geom: per cell x_0 (3) and J row-major (3 x 3).  The products and sums are
+// rounded separately, in the host path's order, so both paths give the same bits.
+__global__ void k_level_coords(int dim, int n, int64_t Nt, int64_t N, const int32_t* __restrict__ ijk,
+                               const double* __restrict__ geom, double* __restrict__ xyz) {
+  grid_dependency_sync();
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = idx / Nt;
+    const int32_t e = ijk[idx - c * Nt];
+    const double p[3] = {(double)(e & 1023), (double)((e >> 10) & 1023), (double)(e >> 20)};
+    const double* G = geom + c * 12;
+    for (int r = 0; r < dim; ++r) {
+      double v = 0;
+      for (int a = 0; a < dim; ++a) v = __dadd_rn(v, __dmul_rn(G[3 + 3 * r + a], p[a]));
+      xyz[idx * dim + r] = __dadd_rn(G[r], v / (double)n);
+    }
+  }
+}
+
 __global__ void k_finite(const double* __restrict__ v, int64_t n, int* __restrict__ flag) {
   grid_dependency_sync();
   int bad = 0;
@@ -236,6 +255,11 @@ void launch_prolong(hhg_mesh_s* m, int l, const double* coarse, double* fine, cu
 
 void launch_sub(hhg_mesh_s* m, const double* a, const double* b, double* x, int64_t n, cudaStream_t s) {
   hhg_launch(k_sub, 4 * m->sm_count, kBlock, 0, s, a, b, x, n);
+}
+
+void launch_level_coords(hhg_mesh_s* m, int l, const double* geom, double* xyz, cudaStream_t s) {
+  const LevelData& Lv = m->lv[l];
+  hhg_launch(k_level_coords, 8 * m->sm_count, kBlock, 0, s, m->dim, Lv.n, Lv.Nt, Lv.N, Lv.d_ijk, geom, xyz);
 }
 
 void launch_coarse_solve(hhg_mesh_s* m, const double* rhs, cudaStream_t s) {

@@ -288,3 +288,22 @@ def test_full_size_cube384_l6_properties(P):
         assert mesh.info.n_unknowns == (4 * 2 ** L - 1) ** 3
         mesh.close()
     assert 3.5 < errs[0] / errs[1] < 4.5, errs
+
+
+@pytest.mark.parametrize("name", ["lshape", "cube"])
+def test_level_coords_device_path_matches_host_path(P, name):
+    """hhg_level_coords into device memory (one kernel) gives the host path's coordinates bit for
+    bit, on every level of a general mesh; both match the oracle's node coordinates."""
+    import torch
+    co, ce = perturbed(name)
+    L = 4 if name == "lshape" else 3
+    mesh = P.Mesh(co, ce, L)
+    h = O.Hierarchy(co, ce, L)
+    for lev in range(L + 1):
+        xh = mesh.level_coords(lev)
+        xd = torch.empty((mesh.n_nodes(lev), co.shape[1]), dtype=torch.float64, device="cuda")
+        mesh.level_coords(lev, out=xd)
+        assert np.array_equal(xd.cpu().numpy(), xh)
+        dist, _ = cKDTree(h.levels[lev].x).query(xh)
+        assert dist.max() < 1e-12
+    mesh.close()

@@ -164,21 +164,37 @@ def lshape_g(x: np.ndarray) -> np.ndarray:
     return np.power(r, 2.0 / 3.0) * np.sin(2.0 * phi / 3.0)
 
 
+def _fns(x):
+    """(exp, cos, sin) for a numpy array or a torch tensor (device inputs of large workloads)."""
+    if isinstance(x, np.ndarray):
+        return np.exp, np.cos, np.sin
+    import torch
+    return torch.exp, torch.cos, torch.sin
+
+
 def _waves_w(t, omega, alpha):
-    return 1.0 - np.cos(np.exp(alpha * (t - 1.0)) * omega * t)
+    exp, cos, _ = _fns(t)
+    return 1.0 - cos(exp(alpha * (t - 1.0)) * omega * t)
 
 
 def _waves_w2(t, omega, alpha):
     # second derivative of 1 - cos(s(t)), s = exp(alpha (t-1)) omega t
-    e = np.exp(alpha * (t - 1.0))
+    exp, cos, sin = _fns(t)
+    e = exp(alpha * (t - 1.0))
     s = e * omega * t
     ds = omega * e * (1.0 + alpha * t)
     d2s = omega * e * (2.0 * alpha + alpha * alpha * t)
-    return np.cos(s) * ds * ds + np.sin(s) * d2s
+    return cos(s) * ds * ds + sin(s) * d2s
 
 
 def waves_u(x, omega=16 * np.pi, alpha=10.0):
-    return np.prod(_waves_w(x, omega, alpha), axis=1)
+    """u = prod_i w(x_i), w(t) = 1 - cos(exp(alpha (t - 1)) omega t) (Example 5.1, extended to d
+    dims as in the scaling study of Sec. 5.4); x: (N, d) numpy array or torch tensor."""
+    w = _waves_w(x, omega, alpha)
+    u = w[:, 0]
+    for i in range(1, x.shape[1]):
+        u = u * w[:, i]
+    return u
 
 
 def waves_f(x, omega=16 * np.pi, alpha=10.0):
@@ -186,13 +202,13 @@ def waves_f(x, omega=16 * np.pi, alpha=10.0):
     w = _waves_w(x, omega, alpha)
     w2 = _waves_w2(x, omega, alpha)
     d = x.shape[1]
-    f = np.zeros(x.shape[0])
+    f = 0.0 * w[:, 0]
     for i in range(d):
-        t = w2[:, i].copy()
+        t = w2[:, i]
         for j in range(d):
             if j != i:
                 t = t * w[:, j]
-        f -= t
+        f = f - t
     return f
 
 
@@ -215,6 +231,9 @@ WORKLOADS = {
     # unit cube, 3072 Kuhn tets, L=7, f=1, k log-uniform in [1e-2,1e2] (SplitMix64 seed 0)
     "cube3072_l7": dict(mesh=lambda: cube_mesh(8), L=7, f=_one, g=_zero,
                         k=lambda n: coeff_loguniform(n, seed=0), u=None),
+    # unit cube, 3^3 cubes x 6 Kuhn tets = 162 tets, L=8, waves solution (omega = 16 pi, alpha = 10):
+    # the one-node size of the scaling program of Sec. 5.4 (Alg. 5, refinement of 12.5 %)
+    "waves3d_l8": dict(mesh=lambda: cube_mesh(3), L=8, f=waves_f, g=waves_u, k=None, u=waves_u),
     # Fichera corner, 336 tets, L=6, f=1, k uniform in [0.5,2] (SplitMix64 seed 1)
     "fichera336_l6": dict(mesh=fichera_mesh, L=6, f=_one, g=_zero,
                           k=lambda n: coeff_uniform(n, seed=1), u=None),
