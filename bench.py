@@ -42,11 +42,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=None, help="timed steps (default 50; --program alg5: 3)")
     ap.add_argument("--warmup", type=int, default=None, help="warm-up steps (default 5; --program alg5: 1)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--program", default="step", choices=["step", "alg5"],
+    ap.add_argument("--program", default="step", choices=["step", "alg5", "effectivity"],
                     help="step: the FMG + estimator + marking step (default); alg5: the scaling program "
-                         "of Sec. 5.4 (solve, estimate, 3D red-green refinement of 12.5 %%, rebuild, solve)")
+                         "of Sec. 5.4 (solve, estimate, 3D red-green refinement of 12.5 %%, rebuild, solve); "
+                         "effectivity: the estimator study of Sec. 5.3 (kl loops with K = 10, j = 1..4, nu = 6 and 2)")
     ap.add_argument("--workload", default=None, help="default cube384_l6 (step) or waves3d_l8 (alg5)")
-    ap.add_argument("--level", type=int, default=None, help="--program alg5: override the workload's finest level L")
+    ap.add_argument("--level", type=int, default=None, help="--program alg5 / effectivity: override the finest level L")
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
     ap.add_argument("--storage", type=int, default=None, help="mixed arm: 0 binary32, 1 bfloat16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -491,10 +492,157 @@ def alg5(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- effectivity study
+
+# worst-case effectivity indices eta_j / ||e_L||, j = 1..4, printed in Table 1 (nu = 6) and Table 2
+# (nu = 2) of Sec. 5.3 for the waves problem (Example 5.1) and the L-shape (Example 5.2)
+PAPER_WORST_EFFECTIVITY = {("waves2d", 6): [0.64, 0.87, 1.47, 8.92], ("lshape", 6): [0.43, 0.57, 0.52, 0.43],
+                           ("waves2d", 2): [0.68, 1.28, 1.67, 7.82], ("lshape", 2): [0.51, 0.74, 0.69, 0.53]}
+
+
+def theorem_bounds(theta, j):
+    """Idealised constants C_1, C_2 of Theorem 4.1 (epsilon = 0) for convergence factor theta."""
+    return ((1 - theta ** j) ** (j + 1) / (1 + theta ** (j + 1)) ** j,
+            (1 + theta ** j) ** (j + 1) / (1 - theta ** (j + 1)) ** j)
+
+
+def radon7():
+    """Radon's seven-point rule on a triangle (exact for polynomials of degree 5): barycentric
+    points and weights relative to the triangle's area."""
+    r = math.sqrt(15.0)
+    a, b = (6 - r) / 21, (6 + r) / 21
+    pts = [(1 / 3, 1 / 3, 1 / 3), (a, a, 1 - 2 * a), (a, 1 - 2 * a, a), (1 - 2 * a, a, a),
+           (b, b, 1 - 2 * b), (b, 1 - 2 * b, b), (1 - 2 * b, b, b)]
+    w = [9 / 40] + [(155 - r) / 1200] * 3 + [(155 + r) / 1200] * 3
+    return pts, w
+
+
+def micro_triangles(n):
+    """The n^2 micro triangles of a macro triangle refined uniformly to side n, as triples of packed
+    closure indices (row j, i fastest: q = j (n + 1) - j (j - 1) / 2 + i), counter-clockwise in
+    lattice coordinates: (i, j), (i+1, j), (i, j+1) for i + j <= n - 1 and (i+1, j), (i+1, j+1),
+    (i, j+1) for i + j <= n - 2."""
+    import numpy as np
+    ii, jj = np.meshgrid(np.arange(n + 1), np.arange(n + 1), indexing="ij")
+
+    def q(i, j):
+        return j * (n + 1) - j * (j - 1) // 2 + i
+
+    up = (ii + jj) <= n - 1
+    dn = (ii + jj) <= n - 2
+    iu, ju, idn, jdn = ii[up], jj[up], ii[dn], jj[dn]
+    tri_up = np.stack([q(iu, ju), q(iu + 1, ju), q(iu, ju + 1)], 1)
+    tri_dn = np.stack([q(idn + 1, jdn), q(idn + 1, jdn + 1), q(idn, jdn + 1)], 1)
+    return np.concatenate([tri_up, tri_dn]).astype(np.int64)
+
+
+def local_l2_errors_sq(x, u, u_exact, tri, Nt, n_cells, chunk_cells=32):
+    """Per macro triangle, the squared L2 norm of u_exact - u_h over the triangle, u_h the piecewise
+    linear function on its micro triangles with nodal values u (Radon's rule on every micro
+    triangle).  x (N, 2) and u (N,): torch tensors in the per-cell packed closure layout."""
+    import torch
+    pts, w = radon7()
+    t = torch.as_tensor(tri, device=x.device)
+    out = torch.empty(n_cells, dtype=torch.float64, device=x.device)
+    for c0 in range(0, n_cells, chunk_cells):
+        c1 = min(n_cells, c0 + chunk_cells)
+        idx = t[None] + (torch.arange(c0, c1, device=x.device) * Nt)[:, None, None]
+        X = x[idx]
+        U = u[idx]
+        d1 = X[:, :, 1] - X[:, :, 0]
+        d2 = X[:, :, 2] - X[:, :, 0]
+        area = 0.5 * (d1[..., 0] * d2[..., 1] - d1[..., 1] * d2[..., 0]).abs()
+        acc = torch.zeros_like(area)
+        for (l0, l1, l2), wq in zip(pts, w):
+            xq = l0 * X[:, :, 0] + l1 * X[:, :, 1] + l2 * X[:, :, 2]
+            uh = l0 * U[:, :, 0] + l1 * U[:, :, 1] + l2 * U[:, :, 2]
+            e = u_exact(xq.reshape(-1, 2)).reshape(uh.shape) - uh
+            acc += wq * e * e
+        out[c0:c1] = (acc * area).sum(1)
+    return out
+
+
+def effectivity_study(P, device, L=8, K=10, nus=(6, 2), fraction=0.10, names=("waves2d", "lshape"), log=None):
+    """Sec. 5.3: kl-refinement (Alg. 2) with K steps, each marking the given fraction of macro
+    triangles with the largest actual local L2 errors for red refinement (Sec. 5 drives refinement
+    by the true errors), and at every grid T^k_L the global estimates eta_j, j = 1..4, of the FMG
+    with nu V(2,2)-cycles per level against ||u - u_L||.  Returns per problem and nu the rows
+    (cells, unknowns, ||e||, eta_j, eta_j / ||e||) and the worst case per j (largest |log|)."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    problems = {"waves2d": (lambda: W.square_mesh(4), W.waves_f, W.waves_u, 2.0),
+                "lshape": (W.lshape_mesh, lambda x: x.new_zeros(x.shape[0]), W.lshape_g, 4.0 / 3.0)}
+    tri = micro_triangles(1 << L)
+    out = {}
+    for name in names:
+        mk, f, uex, q = problems[name]
+        for nu in nus:
+            prm = P.solve_params(nu=nu, pre=2, post=2, n_extra=0, precision=0)
+            co, ce = mk()
+            rg = P.RG2D(co, ce)
+            rows = []
+            for k in range(K + 1):
+                c, e = rg.mesh()
+                mesh = P.Mesh(c, e, L)
+                N = mesh.n_nodes(L)
+                x = torch.empty((N, 2), dtype=torch.float64, device=device)
+                mesh.level_coords(L, out=x)
+                fd = f(x).contiguous()
+                gd = uex(x).contiguous()
+                if device != "cpu":
+                    torch.cuda.synchronize()
+                mesh.set_data(fd, gd)
+                u = torch.empty(N, dtype=torch.float64, device=device)
+                mesh.solve(prm, out=u)
+                if device != "cpu":
+                    torch.cuda.synchronize()
+                etas = [mesh.estimate(j, want_local=False)["eta_j"] for j in (1, 2, 3, 4)]
+                e2 = local_l2_errors_sq(x, u, uex, tri, N // len(e), len(e))
+                err = math.sqrt(float(e2.sum()))
+                rows.append({"k": k, "cells": int(len(e)), "unknowns": int(mesh.info.n_unknowns), "l2_error": err,
+                             "eta": etas, "effectivity": [h / err for h in etas]})
+                if log:
+                    log("%s nu=%d k=%d cells=%d err=%.4e eff=%s" % (name, nu, k, len(e), err,
+                                                                    " ".join("%.3f" % g for g in rows[-1]["effectivity"])))
+                mesh.close()
+                del x, fd, gd, u
+                if k < K:
+                    rg.refine(P.mark(np.sqrt(e2.cpu().numpy()), fraction))
+            worst = []
+            for jj in range(4):
+                g = max((r["effectivity"][jj] for r in rows), key=lambda v: abs(math.log(v)))
+                worst.append(g)
+            theta = 2.0 ** (-q)
+            out["%s_nu%d" % (name, nu)] = {
+                "rows": rows, "worst_effectivity": worst,
+                "paper_worst_effectivity": PAPER_WORST_EFFECTIVITY.get((name, nu)),
+                "C1_C2": [theorem_bounds(theta, j) for j in (1, 2, 3, 4)]}
+    return out
+
+
+def effectivity(args):
+    import torch
+
+    import paper_2508_06049_gb300 as P
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    t0 = time.perf_counter()
+    res = effectivity_study(P, "cuda", L=args.level or 8, K=10,
+                            log=lambda m: print(m, file=sys.stderr, flush=True))
+    line = {"program": "effectivity", "metric": "worst-case effectivity eta_j / ||u - u_L|| over the kl steps",
+            "unit": "ratio", "L": args.level or 8, "K": 10, "marking": "top 10 % of actual local L2 errors",
+            "fmg": "nu V(2,2) binary64", "wall_s": time.perf_counter() - t0, "results": res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.program == "alg5":
         alg5(args)
+        return
+    if args.program == "effectivity":
+        effectivity(args)
         return
     if args.kernel_only:
         kernel_only(args)

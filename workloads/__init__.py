@@ -156,12 +156,17 @@ def sin_product_f(x: np.ndarray) -> np.ndarray:
     return d * np.pi ** 2 * np.prod(np.sin(np.pi * x), axis=1)
 
 
-def lshape_g(x: np.ndarray) -> np.ndarray:
-    """r^(2/3) sin(2 phi / 3) with phi in [0, 2 pi) measured from the +x axis."""
-    r = np.hypot(x[:, 0], x[:, 1])
-    phi = np.arctan2(x[:, 1], x[:, 0])
-    phi = np.where(phi < 0.0, phi + 2.0 * np.pi, phi)
-    return np.power(r, 2.0 / 3.0) * np.sin(2.0 * phi / 3.0)
+def lshape_g(x):
+    """r^(2/3) sin(2 phi / 3) with phi in [0, 2 pi) measured from the +x axis (numpy or torch)."""
+    if isinstance(x, np.ndarray):
+        hypot, atan2, where, sin = np.hypot, np.arctan2, np.where, np.sin
+    else:
+        import torch
+        hypot, atan2, where, sin = torch.hypot, torch.atan2, torch.where, torch.sin
+    r = hypot(x[:, 0], x[:, 1])
+    phi = atan2(x[:, 1], x[:, 0])
+    phi = where(phi < 0.0, phi + 2.0 * np.pi, phi)
+    return r ** (2.0 / 3.0) * sin(2.0 * phi / 3.0)
 
 
 def _fns(x):
@@ -213,7 +218,9 @@ def waves_f(x, omega=16 * np.pi, alpha=10.0):
 
 
 def _zero(x):
-    return np.zeros(x.shape[0])
+    if isinstance(x, np.ndarray):
+        return np.zeros(x.shape[0])
+    return x.new_zeros(x.shape[0])
 
 
 def _one(x):
