@@ -42,10 +42,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=None, help="timed steps (default 50; --program alg5: 3)")
     ap.add_argument("--warmup", type=int, default=None, help="warm-up steps (default 5; --program alg5: 1)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--program", default="step", choices=["step", "alg5", "effectivity"],
+    ap.add_argument("--program", default="step", choices=["step", "alg5", "effectivity", "kl_compare"],
                     help="step: the FMG + estimator + marking step (default); alg5: the scaling program "
                          "of Sec. 5.4 (solve, estimate, 3D red-green refinement of 12.5 %%, rebuild, solve); "
-                         "effectivity: the estimator study of Sec. 5.3 (kl loops with K = 10, j = 1..4, nu = 6 and 2)")
+                         "effectivity: the estimator study of Sec. 5.3 (kl loops with K = 10, j = 1..4, nu = 6 and 2); "
+                         "kl_compare: uniform vs Alg. 1 vs Alg. 2 refinement (Sec. 5.1-5.2, final error and rho)")
     ap.add_argument("--workload", default=None, help="default cube384_l6 (step) or waves3d_l8 (alg5)")
     ap.add_argument("--level", type=int, default=None, help="--program alg5 / effectivity: override the finest level L")
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
@@ -562,24 +563,38 @@ def local_l2_errors_sq(x, u, u_exact, tri, Nt, n_cells, chunk_cells=32):
     return out
 
 
-def effectivity_study(P, device, L=8, K=10, nus=(6, 2), fraction=0.10, names=("waves2d", "lshape"), log=None):
+# extra level-L V-cycles after the FMG in the studies of Sec. 5: the paper adds cycles until the
+# first two digits of ||u - u_L|| stop changing; 20 V(2,2)-cycles leave no visible change on the
+# waves and L-shape sequences (the coarse solutions w_l are not updated by them)
+STUDY_EXTRA_CYCLES = 20
+
+
+def study_problems():
+    """The two 2D problems of Sec. 5.1-5.3: (initial macro mesh, f, exact u = Dirichlet data, q) with
+    q the asymptotic convergence order of uniform refinement (theta = 2^-q)."""
+    import workloads as W
+    return {"waves2d": (lambda: W.square_mesh(4), W.waves_f, W.waves_u, 2.0),
+            "lshape": (W.lshape_mesh, lambda x: x.new_zeros(x.shape[0]), W.lshape_g, 4.0 / 3.0)}
+
+
+def effectivity_study(P, device, L=8, K=10, nus=(6, 2), fraction=0.10, names=("waves2d", "lshape"), log=None,
+                      n_extra=STUDY_EXTRA_CYCLES):
     """Sec. 5.3: kl-refinement (Alg. 2) with K steps, each marking the given fraction of macro
     triangles with the largest actual local L2 errors for red refinement (Sec. 5 drives refinement
     by the true errors), and at every grid T^k_L the global estimates eta_j, j = 1..4, of the FMG
-    with nu V(2,2)-cycles per level against ||u - u_L||.  Returns per problem and nu the rows
-    (cells, unknowns, ||e||, eta_j, eta_j / ||e||) and the worst case per j (largest |log|)."""
+    with nu V(2,2)-cycles per level (and n_extra further level-L cycles) against ||u - u_L||.
+    Returns per problem and nu the rows (cells, unknowns, ||e||, eta_j, eta_j / ||e||) and the
+    worst case per j (largest |log|)."""
     import numpy as np
     import torch
 
-    import workloads as W
-    problems = {"waves2d": (lambda: W.square_mesh(4), W.waves_f, W.waves_u, 2.0),
-                "lshape": (W.lshape_mesh, lambda x: x.new_zeros(x.shape[0]), W.lshape_g, 4.0 / 3.0)}
+    problems = study_problems()
     tri = micro_triangles(1 << L)
     out = {}
     for name in names:
         mk, f, uex, q = problems[name]
         for nu in nus:
-            prm = P.solve_params(nu=nu, pre=2, post=2, n_extra=0, precision=0)
+            prm = P.solve_params(nu=nu, pre=2, post=2, n_extra=n_extra, precision=0)
             co, ce = mk()
             rg = P.RG2D(co, ce)
             rows = []
@@ -622,6 +637,133 @@ def effectivity_study(P, device, L=8, K=10, nus=(6, 2), fraction=0.10, names=("w
     return out
 
 
+def coarse_errors_sq(P, device, c, e, f, uex, prm, n=256):
+    """Alg. 1's coarse step: the P1 solution u_0 on the macro mesh itself (the exact coarse-grid
+    solve inside the FMG of a one-level hierarchy, read back from w_0 at the macro vertices) and,
+    per macro triangle, the squared L2 norm of u - u_0 (u_0 interpolated linearly onto a side-n
+    lattice, Radon's rule on its micro triangles)."""
+    import torch
+    mesh = P.Mesh(c, e, 1)
+    N1 = mesh.n_nodes(1)
+    x1 = torch.empty((N1, 2), dtype=torch.float64, device=device)
+    mesh.level_coords(1, out=x1)
+    fd, gd = f(x1).contiguous(), uex(x1).contiguous()
+    if device != "cpu":
+        torch.cuda.synchronize()
+    mesh.set_data(fd, gd)
+    u1 = torch.empty(N1, dtype=torch.float64, device=device)
+    mesh.solve(prm, out=u1)
+    w0 = torch.empty(N1, dtype=torch.float64, device=device)
+    mesh.get_vector(1, 0, out=w0)
+    if device != "cpu":
+        torch.cuda.synchronize()
+    mesh.close()
+    # level-1 closure (side 2, packed): the macro vertices are nodes 0, 2 and 5
+    v = w0.view(len(e), 6)[:, [0, 2, 5]]
+    ii, jj = [], []
+    for j in range(n + 1):
+        for i in range(n + 1 - j):
+            ii.append(i)
+            jj.append(j)
+    a = torch.tensor(ii, dtype=torch.float64, device=device) / n
+    b = torch.tensor(jj, dtype=torch.float64, device=device) / n
+    cv = torch.as_tensor(c, dtype=torch.float64, device=device)[torch.as_tensor(e, dtype=torch.int64, device=device)]
+    X = (cv[:, None, 0] + a[None, :, None] * (cv[:, None, 1] - cv[:, None, 0])
+         + b[None, :, None] * (cv[:, None, 2] - cv[:, None, 0])).reshape(-1, 2)
+    U = ((1 - a - b)[None] * v[:, 0:1] + a[None] * v[:, 1:2] + b[None] * v[:, 2:3]).reshape(-1)
+    return local_l2_errors_sq(X, U, uex, micro_triangles(n), len(ii), len(e))
+
+
+def kl_compare_study(P, device, L=8, K=10, fraction=0.10, names=("waves2d", "lshape"), log=None,
+                     n_extra=STUDY_EXTRA_CYCLES):
+    """Sec. 5.1-5.2: uniform refinement, k+l-refinement (Alg. 1: K steps of solving on the coarse
+    grid and marking by its local errors, then L uniform levels) and kl-refinement (Alg. 2: marking
+    by the local errors of the level-L solution), each ending with a level-L solve on its final
+    grid.  Reports per scheme the final macro cells, unknowns and ||u - u_L||, and the mesh-quality
+    ratio rho = (H^2 ||e_h||) / (h^2 ||e_H||) (Eq. 5.3, d = 2) with H, e_H those of the initial
+    coarse grid and h = (|Omega| / #micro triangles)^(1/2)."""
+    import numpy as np
+    import torch
+    problems = study_problems()
+    prm = P.solve_params(nu=2, pre=2, post=2, n_extra=n_extra, precision=0)
+    tri = micro_triangles(1 << L)
+
+    def fine_error(c, e):
+        f_, uex = problems[name][1], problems[name][2]
+        mesh = P.Mesh(c, e, L)
+        N = mesh.n_nodes(L)
+        x = torch.empty((N, 2), dtype=torch.float64, device=device)
+        mesh.level_coords(L, out=x)
+        fd, gd = f_(x).contiguous(), uex(x).contiguous()
+        if device != "cpu":
+            torch.cuda.synchronize()
+        mesh.set_data(fd, gd)
+        u = torch.empty(N, dtype=torch.float64, device=device)
+        mesh.solve(prm, out=u)
+        if device != "cpu":
+            torch.cuda.synchronize()
+        e2 = local_l2_errors_sq(x, u, uex, tri, N // len(e), len(e))
+        unk = int(mesh.info.n_unknowns)
+        mesh.close()
+        return e2, unk
+
+    out = {}
+    for name in names:
+        mk, f, uex, q = problems[name]
+        co, ce = mk()
+        e2H = coarse_errors_sq(P, device, co, ce, f, uex, prm)
+        eH = math.sqrt(float(e2H.sum()))
+        res = {"coarse_cells": int(len(ce)), "coarse_error": eH}
+        # uniform
+        e2, unk = fine_error(co, ce)
+        res["uniform"] = {"cells": int(len(ce)), "unknowns": unk, "l2_error": math.sqrt(float(e2.sum()))}
+        # Alg. 1
+        rg = P.RG2D(co, ce)
+        for k in range(K):
+            c, e = rg.mesh()
+            e2c = e2H if k == 0 else coarse_errors_sq(P, device, c, e, f, uex, prm)
+            rg.refine(P.mark(np.sqrt(e2c.cpu().numpy()), fraction))
+        c, e = rg.mesh()
+        e2, unk = fine_error(c, e)
+        res["alg1"] = {"cells": int(len(e)), "unknowns": unk, "l2_error": math.sqrt(float(e2.sum()))}
+        # Alg. 2
+        rg = P.RG2D(co, ce)
+        hist = []
+        for k in range(K + 1):
+            c, e = rg.mesh()
+            e2, unk = fine_error(c, e)
+            hist.append((int(len(e)), unk, math.sqrt(float(e2.sum()))))
+            if k < K:
+                rg.refine(P.mark(np.sqrt(e2.cpu().numpy()), fraction))
+        res["alg2"] = {"cells": hist[-1][0], "unknowns": hist[-1][1], "l2_error": hist[-1][2],
+                       "history": [{"cells": a, "unknowns": b, "l2_error": g} for a, b, g in hist]}
+        for key in ("uniform", "alg1", "alg2"):
+            r = res[key]
+            r["rho"] = (r["cells"] * 4 ** L / len(ce)) * r["l2_error"] / eH
+        if log:
+            log("%s: coarse error %.4e; uniform %.4e (rho %.2f); alg1 %d cells %.4e (rho %.2f); alg2 %d cells %.4e (rho %.2f)"
+                % (name, eH, res["uniform"]["l2_error"], res["uniform"]["rho"], res["alg1"]["cells"],
+                   res["alg1"]["l2_error"], res["alg1"]["rho"], res["alg2"]["cells"], res["alg2"]["l2_error"],
+                   res["alg2"]["rho"]))
+        out[name] = res
+    return out
+
+
+def kl_compare(args):
+    import torch
+
+    import paper_2508_06049_gb300 as P
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    t0 = time.perf_counter()
+    res = kl_compare_study(P, "cuda", L=args.level or 8, K=10, log=lambda m: print(m, file=sys.stderr, flush=True))
+    line = {"program": "kl_compare", "metric": "final L2 error and rho of uniform, Alg. 1 and Alg. 2 refinement",
+            "unit": "1", "L": args.level or 8, "K": 10, "marking": "top 10 % of actual local L2 errors",
+            "fmg": "nu=2 V(2,2) + %d level-L cycles, binary64" % STUDY_EXTRA_CYCLES,
+            "paper_rho_waves2d": {"uniform": 9.8, "alg1": 1.5, "alg2": 0.9},
+            "wall_s": time.perf_counter() - t0, "results": res}
+    print(json.dumps(line), flush=True)
+
+
 def effectivity(args):
     import torch
 
@@ -632,7 +774,7 @@ def effectivity(args):
                             log=lambda m: print(m, file=sys.stderr, flush=True))
     line = {"program": "effectivity", "metric": "worst-case effectivity eta_j / ||u - u_L|| over the kl steps",
             "unit": "ratio", "L": args.level or 8, "K": 10, "marking": "top 10 % of actual local L2 errors",
-            "fmg": "nu V(2,2) binary64", "wall_s": time.perf_counter() - t0, "results": res}
+            "fmg": "nu V(2,2) + %d level-L cycles, binary64" % STUDY_EXTRA_CYCLES, "wall_s": time.perf_counter() - t0, "results": res}
     print(json.dumps(line), flush=True)
 
 
@@ -643,6 +785,9 @@ def main():
         return
     if args.program == "effectivity":
         effectivity(args)
+        return
+    if args.program == "kl_compare":
+        kl_compare(args)
         return
     if args.kernel_only:
         kernel_only(args)
