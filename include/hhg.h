@@ -106,7 +106,11 @@ hhg_status hhg_mesh_destroy(hhg_mesh mesh);
 hhg_status hhg_mesh_get_info(hhg_mesh mesh, hhg_mesh_info* info);
 
 /* Coordinates of the level-l nodes in the layout above (x = x_0 + J p / 2^l per cell).
- * xyz: host or device, N_l*dim doubles, node-major. */
+ * xyz: host or device, N_l*dim doubles, node-major.  Device memory of the mesh's device is written
+ * by one kernel on the mesh's stream (the call returns after it completes); any other pointer is
+ * filled from host threads in batches of cells.  Both paths round every product and sum
+ * separately and give the same bits.  Errors: HHG_ERR_ARG (NULL, level out of range),
+ * HHG_ERR_CUDA. */
 hhg_status hhg_level_coords(hhg_mesh mesh, int level, double* xyz);
 
 /* Piecewise-constant coefficient k_T > 0 per macro cell (Eq. 5.1 with k); NULL = 1. */
