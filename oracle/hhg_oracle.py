@@ -39,7 +39,9 @@ What each part follows
 * Sec. 4.4, Alg. 4 (ErrorEstimate) and Eqs. (4.5), (4.6), (4.14): e~_l = u_L - I w_l,
   theta~_l = ||e~_l|| / ||e~_{l-1}||, eta_j = theta~_l^j ||e~_l|| with l = L-j,
   L2 norms through the mass matrix; local eta_T = ||e~_{L-1}||_{L2(T)} over the
-  micro elements inside macro T.
+  micro elements inside macro T.  The Remark in Sec. 4: the energy norm (stiffness
+  matrix in place of the mass matrix) and a goal-oriented local seminorm
+  ||G(v|_T)||, here G(v|_T) = sqrt(w_T) v|_T with per-macro weights w_T.
 * Theorem 4.1 / Corollaries 4.3-4.4: effectivity constants.
 * Sec. 3 and Sec. 5.1: marking of a top fraction of macro elements; 2D red-green
   refinement with greens reverted before the next step.
@@ -604,6 +606,15 @@ def local_mass_sq(lev: Level, e: np.ndarray, n_cells: int) -> np.ndarray:
     return np.bincount(lev.emacro, weights=per_elem, minlength=n_cells)
 
 
+def local_energy_sq(lev: Level, e: np.ndarray, n_cells: int) -> np.ndarray:
+    """Per macro T: e^T A_{l,T} e = int_T k |grad e|^2, summing the element stiffness forms (with
+    k_T) of micro elements inside T, boundary nodes included (the energy norm of the Remark in
+    Sec. 4)."""
+    ee = e[lev.elems]
+    per_elem = np.einsum("ea,eab,eb->e", ee, lev.Ke, ee)
+    return np.bincount(lev.emacro, weights=per_elem, minlength=n_cells)
+
+
 def prolong_to_finest(h: Hierarchy, v: np.ndarray, l: int) -> np.ndarray:
     """I_l^L v for a level-l nodal vector."""
     for m in range(l + 1, h.L + 1):
@@ -611,8 +622,14 @@ def prolong_to_finest(h: Hierarchy, v: np.ndarray, l: int) -> np.ndarray:
     return v
 
 
-def estimate(h: Hierarchy, u_L: np.ndarray, ws, j: int = 1):
+def estimate(h: Hierarchy, u_L: np.ndarray, ws, j: int = 1, norm: str = "l2", weights=None):
     """Alg. 4 ErrorEstimate with offset j (l = L - j), plus the local indicators.
+
+    norm (Remark in Sec. 4): "l2" (the paper's choice, mass matrix), "energy" (the stiffness
+    matrix in place of the mass matrix: int_T k |grad v|^2), or "goal": the local seminorm
+    ||v||_T^2 = w_T ||v||_{L2(T)}^2 of the piecewise constant goal operator G(v|_T) = sqrt(w_T) v|_T
+    with per-macro weights w_T >= 0 (e.g. the indicator of a subregion made of macro cells); the
+    global values are the sums of the weighted local squares.
 
     Returns a dict with
       err_l, err_lm1  : ||e~_l||, ||e~_{l-1}|| (L2 via the mass matrix)
@@ -629,10 +646,14 @@ def estimate(h: Hierarchy, u_L: np.ndarray, ws, j: int = 1):
     levL = h.levels[L]
     e_l = u_L - prolong_to_finest(h, ws[l], l + 1)          # w_l lives on level l+1
     e_lm1 = u_L - prolong_to_finest(h, ws[l - 1], l)         # w_{l-1} lives on level l
-    sq_l = local_mass_sq(levL, e_l, h.n_cells)
-    sq_lm1 = local_mass_sq(levL, e_lm1, h.n_cells)
+    if norm not in ("l2", "energy", "goal"):
+        raise ValueError("norm must be l2, energy or goal")
+    form = local_energy_sq if norm == "energy" else local_mass_sq
+    wT = np.ones(h.n_cells) if norm != "goal" else np.asarray(weights, dtype=np.float64)
+    sq_l = wT * form(levL, e_l, h.n_cells)
+    sq_lm1 = wT * form(levL, e_lm1, h.n_cells)
     e_L1 = u_L - ws[L - 1]
-    sq_T = local_mass_sq(levL, e_L1, h.n_cells)
+    sq_T = wT * form(levL, e_L1, h.n_cells)
     err_l = math.sqrt(sq_l.sum())
     err_lm1 = math.sqrt(sq_lm1.sum())
     theta = err_l / err_lm1 if err_lm1 > 0 else 0.0
