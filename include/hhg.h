@@ -131,6 +131,17 @@ hhg_status hhg_fmg_solve(hhg_mesh mesh, const hhg_solve_params* params, double* 
  * scaled local estimate theta~_{l,T}^j ||e~_l||_T (Eq. 4.10).  out: host, global values. */
 hhg_status hhg_estimate(hhg_mesh mesh, int j, double* eta_T, double* eta_jT, hhg_estimate_out* out);
 
+/* hhg_estimate in another norm (Remark in Sec. 4).  norm 0: L2 (= hhg_estimate).  norm 1: energy,
+ * the stiffness matrix A_L (with k_T) in place of the mass matrix, ||v||_T^2 = int_T k |grad v|^2
+ * over the micro elements of T, boundary nodes included.  norm 2: goal-oriented local seminorm
+ * ||v||_T^2 = w_T ||v||_{L2(T)}^2 of the piecewise constant operator G(v|_T) = sqrt(w_T) v|_T,
+ * with cell_weights w_T (host, n_cells, finite, >= 0; e.g. the indicator of a subregion made of
+ * macro cells); global values are the sums of the weighted local squares.  cell_weights is read
+ * for norm 2 only.  Local squares are clamped at 0 before the square roots (the energy form is
+ * semidefinite).  Errors: as hhg_estimate, plus HHG_ERR_ARG for an unknown norm or bad weights. */
+hhg_status hhg_estimate_norm(hhg_mesh mesh, int j, int norm, const double* cell_weights, double* eta_T,
+                             double* eta_jT, hhg_estimate_out* out);
+
 /* Read an internal level vector of the last solve into `out` (host or device, N_l doubles):
  * which = 0: u_l after its FMG V-cycles (l = L: the solution, l < L: overwritten by later
  * corrections, so only l = L is meaningful after the solve), 1: w_l (l = 0..L-1, stored on

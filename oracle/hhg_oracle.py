@@ -650,10 +650,11 @@ def estimate(h: Hierarchy, u_L: np.ndarray, ws, j: int = 1, norm: str = "l2", we
         raise ValueError("norm must be l2, energy or goal")
     form = local_energy_sq if norm == "energy" else local_mass_sq
     wT = np.ones(h.n_cells) if norm != "goal" else np.asarray(weights, dtype=np.float64)
-    sq_l = wT * form(levL, e_l, h.n_cells)
-    sq_lm1 = wT * form(levL, e_lm1, h.n_cells)
+    # clamped at 0: the energy form is only semidefinite (constants are in the kernel of A_T)
+    sq_l = np.maximum(wT * form(levL, e_l, h.n_cells), 0.0)
+    sq_lm1 = np.maximum(wT * form(levL, e_lm1, h.n_cells), 0.0)
     e_L1 = u_L - ws[L - 1]
-    sq_T = wT * form(levL, e_L1, h.n_cells)
+    sq_T = np.maximum(wT * form(levL, e_L1, h.n_cells), 0.0)
     err_l = math.sqrt(sq_l.sum())
     err_lm1 = math.sqrt(sq_lm1.sum())
     theta = err_l / err_lm1 if err_lm1 > 0 else 0.0

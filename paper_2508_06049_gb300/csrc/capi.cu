@@ -411,7 +411,10 @@ hhg_status hhg_fmg_solve(hhg_mesh m, const hhg_solve_params* params, double* u_L
   return HHG_OK;
 }
 
-hhg_status hhg_estimate(hhg_mesh m, int j, double* eta_T, double* eta_jT, hhg_estimate_out* out) {
+// ErrorEstimate (Alg. 4) in the norm `norm`: 0 L2 (mass form), 1 energy (stiffness form),
+// 2 L2 with per-cell weights applied to the local squares on the host (goal-oriented seminorm)
+static hhg_status estimate_impl(hhg_mesh m, int j, int norm, const double* wts, double* eta_T, double* eta_jT,
+                                hhg_estimate_out* out) {
   REQUIRE(m, HHG_ERR_ARG, "mesh is NULL");
   REQUIRE(m->solved, HHG_ERR_STATE, "hhg_estimate needs a previous hhg_fmg_solve");
   const int L = m->L;
@@ -430,18 +433,24 @@ hhg_status hhg_estimate(hhg_mesh m, int j, double* eta_T, double* eta_jT, hhg_es
   CHECK_PTR(m->lv[l - 1].w);
   CHECK_PTR(m->d_part);
   CHECK_PTR(m->dM);
+  CHECK_PTR(m->dS);
   CHECK_PTR(m->lv[L].d_ijk);
   CHECK_PTR(m->lv[L].tmp);
   CHECK_PTR(m->lv[L].rc);
   const int jj = j;
+  const bool energy = norm == 1;
+  auto form = [&](const double* x, double* dst, cudaStream_t cs) {
+    if (energy) launch_energy_norm_sq(m, x, nullptr, dst, cs);
+    else launch_mass_norm_sq(m, x, nullptr, dst, cs);
+  };
   // The differences are formed once into level-L scratch (rc is never a coarse-grid rhs on level L,
-  // tmp is free after the solve), so the mass form reads one vector.
+  // tmp is free after the solve), so the per-cell form reads one vector.
   double* xa = m->lv[L].rc;
   double* xb = m->lv[L].tmp;
-  hhg_status st = run_graph(m, "est:" + std::to_string(jj), [&](cudaStream_t cs) {
+  hhg_status st = run_graph(m, "est:" + std::to_string(jj) + (energy ? ":energy" : ""), [&](cudaStream_t cs) {
     // e~_{L-1} = u_L - w_{L-1} (eta_T)
     launch_sub(m, uL, m->lv[L - 1].w, xa, m->lv[L].N, cs);
-    launch_mass_norm_sq(m, xa, nullptr, red, cs);
+    form(xa, red, cs);
     // e~_l = u_L - I w_l (w_l lives on level l+1); for j = 1 it is e~_{L-1} again
     if (l == L - 1) {
       cudaMemcpyAsync(red + nc, red, sizeof(double) * nc, cudaMemcpyDeviceToDevice, cs);
@@ -451,7 +460,7 @@ hhg_status hhg_estimate(hhg_mesh m, int j, double* eta_T, double* eta_jT, hhg_es
         launch_prolong(m, q, v, m->lv[q].tmp, cs, q == L ? uL : nullptr);
         v = m->lv[q].tmp;
       }
-      launch_mass_norm_sq(m, xb, nullptr, red + nc, cs);
+      form(xb, red + nc, cs);
     }
     // e~_{l-1} = u_L - I w_{l-1} (w_{l-1} lives on level l)
     const double* v = m->lv[l - 1].w;
@@ -459,28 +468,37 @@ hhg_status hhg_estimate(hhg_mesh m, int j, double* eta_T, double* eta_jT, hhg_es
       launch_prolong(m, q, v, m->lv[q].tmp, cs, q == L ? uL : nullptr);
       v = m->lv[q].tmp;
     }
-    launch_mass_norm_sq(m, xb, nullptr, red + 2 * nc, cs);
+    form(xb, red + 2 * nc, cs);
   });
   if (st != HHG_OK) return st;
   DBG_SYNC("estimator graph");
   CK(cudaMemcpyAsync(m->h_red, red, sizeof(double) * 3 * (size_t)nc, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
-  const double* h = m->h_red;
+  // local squares (weighted for the goal-oriented seminorm); clamped at 0: the energy form is only
+  // semidefinite (constants lie in the kernel of A_T), so a near-constant difference can round
+  // to a tiny negative square
+  std::vector<double> qT(nc), ql(nc), qlm1(nc);
+  for (int c = 0; c < nc; ++c) {
+    const double w = norm == 2 ? wts[c] : 1.0;
+    qT[c] = std::max(0.0, w * m->h_red[c]);
+    ql[c] = std::max(0.0, w * m->h_red[nc + c]);
+    qlm1[c] = std::max(0.0, w * m->h_red[2 * nc + c]);
+  }
   double sT = 0, sl = 0, slm1 = 0;
   for (int c = 0; c < nc; ++c) {
-    sT += h[c];
-    sl += h[nc + c];
-    slm1 += h[2 * nc + c];
+    sT += qT[c];
+    sl += ql[c];
+    slm1 += qlm1[c];
   }
   double err_l = std::sqrt(sl), err_lm1 = std::sqrt(slm1);
   double theta = err_lm1 > 0 ? err_l / err_lm1 : 0.0;
   if (eta_T)
-    for (int c = 0; c < nc; ++c) eta_T[c] = std::sqrt(h[c]);
+    for (int c = 0; c < nc; ++c) eta_T[c] = std::sqrt(qT[c]);
   if (eta_jT)
     for (int c = 0; c < nc; ++c) {
-      double th = h[2 * nc + c] > 0 ? std::sqrt(h[nc + c] / h[2 * nc + c]) : 0.0;
-      eta_jT[c] = std::pow(th, j) * std::sqrt(h[nc + c]);
+      double th = qlm1[c] > 0 ? std::sqrt(ql[c] / qlm1[c]) : 0.0;
+      eta_jT[c] = std::pow(th, j) * std::sqrt(ql[c]);
     }
   if (out) {
     out->eta_j = std::pow(theta, j) * err_l;
@@ -490,6 +508,23 @@ hhg_status hhg_estimate(hhg_mesh m, int j, double* eta_T, double* eta_jT, hhg_es
     out->err_Lm1 = std::sqrt(sT);
   }
   return HHG_OK;
+}
+
+hhg_status hhg_estimate(hhg_mesh m, int j, double* eta_T, double* eta_jT, hhg_estimate_out* out) {
+  return estimate_impl(m, j, 0, nullptr, eta_T, eta_jT, out);
+}
+
+hhg_status hhg_estimate_norm(hhg_mesh m, int j, int norm, const double* cell_weights, double* eta_T,
+                             double* eta_jT, hhg_estimate_out* out) {
+  REQUIRE(norm >= 0 && norm <= 2, HHG_ERR_ARG, "norm must be 0 (L2), 1 (energy) or 2 (weighted L2)");
+  if (norm == 2) {
+    REQUIRE(m, HHG_ERR_ARG, "mesh is NULL");
+    REQUIRE(cell_weights, HHG_ERR_ARG, "norm 2 needs cell_weights");
+    for (int c = 0; c < m->nc; ++c)
+      REQUIRE(std::isfinite(cell_weights[c]) && cell_weights[c] >= 0, HHG_ERR_ARG,
+              "cell_weights[%d] must be finite and >= 0", c);
+  }
+  return estimate_impl(m, j, norm, cell_weights, eta_T, eta_jT, out);
 }
 
 hhg_status hhg_get_vector(hhg_mesh m, int which, int level, double* out) {

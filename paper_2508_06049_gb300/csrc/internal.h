@@ -173,6 +173,8 @@ void launch_level_coords(hhg_mesh_s* m, int l, const double* geom, double* xyz, 
 void launch_finite_check(hhg_mesh_s* m, const double* v, int64_t n, cudaStream_t s);
 // per-cell reductions on level L: out[T] = (a-b)^T M_T (a-b), b may be null
 void launch_mass_norm_sq(hhg_mesh_s* m, const double* a, const double* b, double* out, cudaStream_t s);
+// out[T] = (a-b)^T A_T (a-b) with the cell's stiffness (k_T included), b may be null
+void launch_energy_norm_sq(hhg_mesh_s* m, const double* a, const double* b, double* out, cudaStream_t s);
 // out[T] = x^T A_T^(1) y (unit-coefficient partial stiffness of cell T), level L
 void launch_stiff_bilinear(hhg_mesh_s* m, const double* x, const double* y, double* out, cudaStream_t s);
 // operator application on all closure nodes (partial at interfaces), then interface sums

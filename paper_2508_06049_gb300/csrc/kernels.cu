@@ -304,6 +304,10 @@ void launch_mass_norm_sq(hhg_mesh_s* m, const double* a, const double* b, double
   cell_form(m, true, m->dM, mass_scale(m->dim, m->lv[m->L].n), a, b, out, s);
 }
 
+void launch_energy_norm_sq(hhg_mesh_s* m, const double* a, const double* b, double* out, cudaStream_t s) {
+  cell_form(m, true, m->dS, stiff_scale(m->dim, m->lv[m->L].n), a, b, out, s);
+}
+
 void launch_stiff_bilinear(hhg_mesh_s* m, const double* x, const double* y, double* out, cudaStream_t s) {
   cell_form(m, false, m->dS, stiff_scale(m->dim, m->lv[m->L].n), x, y, out, s);
 }

@@ -64,6 +64,7 @@ def lib():
         "hhg_set_data": [vp, vp, vp],
         "hhg_fmg_solve": [vp, C.POINTER(SolveParams), vp],
         "hhg_estimate": [vp, i, vp, vp, C.POINTER(EstimateOut)],
+        "hhg_estimate_norm": [vp, i, i, vp, vp, vp, C.POINTER(EstimateOut)],
         "hhg_get_vector": [vp, i, i, vp],
         "hhg_apply": [vp, i, i, vp, vp, i],
         "hhg_mark": [i, vp, d, u8, C.POINTER(i)],
@@ -174,11 +175,19 @@ class Mesh:
         _check(lib().hhg_fmg_solve(self._h, C.byref(p), _ptr(out)))
         return out
 
-    def estimate(self, j=1, want_local=True):
+    def estimate(self, j=1, want_local=True, norm=0, weights=None):
+        """ErrorEstimate of the last solve; norm 0 L2, 1 energy, 2 L2 weighted per cell (weights)."""
         eta = np.empty(self.n_cells) if want_local else None
         etaj = np.empty(self.n_cells) if want_local else None
         out = EstimateOut()
-        _check(lib().hhg_estimate(self._h, int(j), _ptr(eta), _ptr(etaj), C.byref(out)))
+        if norm == 0 and weights is None:
+            _check(lib().hhg_estimate(self._h, int(j), _ptr(eta), _ptr(etaj), C.byref(out)))
+        else:
+            w = None if weights is None else _f64(weights)
+            if w is not None and len(w) != self.n_cells:
+                raise ValueError("weights must have one entry per macro cell")
+            _check(lib().hhg_estimate_norm(self._h, int(j), int(norm), _ptr(w), _ptr(eta), _ptr(etaj),
+                                           C.byref(out)))
         return dict(eta_j=out.eta_j, theta=out.theta, err_l=out.err_l, err_lm1=out.err_lm1,
                     err_Lm1=out.err_Lm1, eta_T=eta, eta_jT=etaj)
 

@@ -172,6 +172,50 @@ def test_estimator_and_marking(P, name):
             assert np.array_equal(P.mark(eg["eta_T"], frac), O.mark_top_fraction(eo["eta_T"], frac))
 
 
+@pytest.mark.parametrize("name", list(CASES))
+def test_estimator_in_other_norms(P, name):
+    """The energy norm and the per-cell weighted L2 seminorm of the Remark in Sec. 4 against the
+    oracle.  Energy: u_L and the w_l agree to 1e-10 max|u| node by node (the FMG parity test), so
+    each difference vector agrees to twice that, and the seminorm of a nodal vector d on T is at most
+    max|d| sqrt(sum_pq |A_T,pq|): per-cell tolerance 1e-10 * 2 max|u| sqrt(sum |A_T|).  Weighted:
+    1e-10 sqrt(w_T) ||u||_{L2,T}, exact zeros where w_T = 0; norm 0 through the same entry point
+    gives hhg_estimate's values bit for bit."""
+    mesh, maps, h, u, uo, ws = run_both(P, name)
+    levL = h.levels[h.L]
+    uM = np.sqrt(O.local_mass_sq(levL, uo, h.n_cells))
+    absA_T = np.bincount(levL.emacro, weights=np.abs(levL.Ke).sum(axis=(1, 2)), minlength=h.n_cells)
+    sE_T = 2 * np.abs(uo).max() * np.sqrt(absA_T)
+    sE = math.sqrt(float((sE_T ** 2).sum()))
+    rng = np.random.default_rng(5)
+    w = rng.uniform(0, 2, h.n_cells)
+    w[::3] = 0.0
+    sW_T = np.sqrt(w) * uM
+    sW = math.sqrt(float((sW_T ** 2).sum()))
+    for j in range(1, h.L):
+        a = mesh.estimate(j)
+        b = mesh.estimate(j, norm=0, weights=np.ones(h.n_cells))
+        assert np.array_equal(a["eta_T"], b["eta_T"]) and a["eta_j"] == b["eta_j"]
+        for norm, key, s_T, s in ((1, "energy", sE_T, sE), (2, "goal", sW_T, sW)):
+            eg = mesh.estimate(j, norm=norm, weights=w if norm == 2 else None)
+            eo = O.estimate(h, uo, ws, j, norm=key, weights=w if norm == 2 else None)
+            assert np.all(np.abs(eg["eta_T"] - eo["eta_T"]) <= TOL * s_T), key
+            # eta_jT = theta_T^j ||e~_l||_T: first-order propagation of the per-cell norm errors
+            with np.errstate(divide="ignore", invalid="ignore"):
+                inv = 1 / np.sqrt(eo["sq_l_T"]) + 1 / np.sqrt(eo["sq_lm1_T"])
+                tol_jT = np.where(np.isfinite(inv), 4 * (j + 1) * TOL * s_T * inv * eo["eta_jT"], np.inf)
+            assert np.all(np.abs(eg["eta_jT"] - eo["eta_jT"]) <= tol_jT + 1e-300), key
+            for k in ("err_l", "err_lm1"):
+                assert abs(eg[k] - eo[k]) <= TOL * s, (key, k)
+            rel = TOL * s * (1 / eo["err_l"] + 1 / eo["err_lm1"])
+            assert abs(eg["theta"] - eo["theta"]) <= rel * eo["theta"], key
+            if norm == 2:
+                assert np.all(eg["eta_T"][w == 0] == 0)
+    with pytest.raises(P.HHGError):
+        mesh.estimate(1, norm=3)
+    with pytest.raises(P.HHGError):
+        mesh.estimate(1, norm=2, weights=-np.ones(h.n_cells))
+
+
 def test_estimate_before_solve_is_an_error(P):
     co, ce = W.square_mesh(2)
     m = P.Mesh(co, ce, 3)
