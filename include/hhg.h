@@ -164,7 +164,9 @@ hhg_status hhg_mark(int n, const double* eta, double fraction, unsigned char* ma
  * history so that green closures are reverted before the next step.  Rules: red = split
  * through the edge midpoints; closure: red-refine triangles with >= 2 split edges or a split
  * edge whose half is split again; green = bisect a triangle with one split edge from the
- * opposite vertex.  New vertices are appended in creation order. */
+ * opposite vertex.  New vertices are appended in creation order.  coords: host, n_verts*2;
+ * cells: host, n_cells*3, 0-based.  Errors: HHG_ERR_ARG (sizes, vertex ids), HHG_ERR_MESH (a cell
+ * with a repeated vertex or zero area), HHG_ERR_OOM. */
 hhg_status hhg_rg2d_create(int n_verts, const double* coords, int n_cells, const int* cells, hhg_rg2d* out);
 hhg_status hhg_rg2d_refine(hhg_rg2d rg, const unsigned char* marked /* host, one flag per current cell */);
 /* Current conforming mesh; pass NULL arrays to query the sizes first. */
@@ -183,7 +185,8 @@ hhg_status hhg_mark_refine(hhg_rg2d rg, const double* eta_T, double fraction, un
  * edges: 4; the three edges of one face: 4).  New vertices are edge midpoints numbered in
  * creation order; refined tets are replaced in place by their children.  coords: host,
  * n_verts*3; cells: host, n_cells*4, 0-based.  Errors: HHG_ERR_ARG (sizes, vertex ids),
- * HHG_ERR_STATE (corrupt state), HHG_ERR_OOM. */
+ * HHG_ERR_MESH (a cell with a repeated vertex or zero volume), HHG_ERR_STATE (corrupt state),
+ * HHG_ERR_OOM. */
 hhg_status hhg_rg3d_create(int n_verts, const double* coords, int n_cells, const int* cells, hhg_rg3d* out);
 hhg_status hhg_rg3d_refine(hhg_rg3d rg, const unsigned char* marked /* host, one flag per current cell */);
 /* Current conforming mesh; pass NULL arrays to query the sizes first. */

@@ -120,6 +120,17 @@ hhg_status hhg_rg2d_create(int n_verts, const double* coords, int n_cells, const
       rg->tris[c].parent[a] = -1;
     }
     rg->tris[c].child = -1;
+    // a cell must span a triangle: three distinct vertices, nonzero area
+    const int* v = rg->tris[c].v;
+    const double* p0 = &coords[2 * (size_t)v[0]];
+    const double* p1 = &coords[2 * (size_t)v[1]];
+    const double* p2 = &coords[2 * (size_t)v[2]];
+    const double det = (p1[0] - p0[0]) * (p2[1] - p0[1]) - (p1[1] - p0[1]) * (p2[0] - p0[0]);
+    if (v[0] == v[1] || v[0] == v[2] || v[1] == v[2] || det == 0.0) {
+      delete rg;
+      hhg::set_error("hhg_rg2d_create: cell %d is degenerate", c);
+      return HHG_ERR_MESH;
+    }
   }
   *out = rg;
   return HHG_OK;

@@ -208,6 +208,22 @@ hhg_status hhg_rg3d_create(int n_verts, const double* coords, int n_cells, const
         return HHG_ERR_ARG;
       }
     }
+    // a cell must span a tetrahedron: four distinct vertices, nonzero volume
+    const double* p0 = &coords[3 * (size_t)v[0]];
+    double e[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int r = 0; r < 3; ++r) e[a][r] = coords[3 * (size_t)v[a + 1] + r] - p0[r];
+    const double det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                       e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                       e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+    bool repeated = false;
+    for (int a = 0; a < 4; ++a)
+      for (int b = a + 1; b < 4; ++b) repeated |= v[a] == v[b];
+    if (repeated || det == 0.0) {
+      delete rg;
+      hhg::set_error("hhg_rg3d_create: cell %d is degenerate", c);
+      return HHG_ERR_MESH;
+    }
     rg->tets.push_back(plain(v[0], v[1], v[2], v[3]));
   }
   *out = rg;

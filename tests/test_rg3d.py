@@ -132,3 +132,43 @@ def test_rg3d_library_matches_oracle_bit_exactly():
             ca, ea = a.mesh()
             cb, eb = b.mesh()
             assert np.array_equal(ca, cb) and np.array_equal(ea, eb)
+
+
+def test_rg_libraries_reject_bad_meshes():
+    """hhg_rg2d_create / hhg_rg3d_create: vertex ids out of range -> HHG_ERR_ARG (1); a cell with a
+    repeated vertex or zero measure -> HHG_ERR_MESH (2); a refine step with a NULL mark array or a
+    size query without arrays behaves as declared."""
+    import paper_2508_06049_gb300 as P
+    try:
+        P.lib()
+    except ImportError:
+        pytest.skip("libhhg.so not built")
+    co3, ce3 = W.cube_mesh(1)
+    bad = ce3.copy()
+    bad[0, 3] = len(co3)
+    with pytest.raises(P.HHGError) as e:
+        P.RG3D(co3, bad)
+    assert e.value.status == 1
+    rep = ce3.copy()
+    rep[1, 2] = rep[1, 0]
+    with pytest.raises(P.HHGError) as e:
+        P.RG3D(co3, rep)
+    assert e.value.status == 2
+    flat = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0]], dtype=float)
+    with pytest.raises(P.HHGError) as e:
+        P.RG3D(flat, np.array([[0, 1, 2, 3]]))
+    assert e.value.status == 2
+    co2, ce2 = W.square_mesh(2)
+    rep2 = ce2.copy()
+    rep2[0, 1] = rep2[0, 2]
+    with pytest.raises(P.HHGError) as e:
+        P.RG2D(co2, rep2)
+    assert e.value.status == 2
+    line = np.array([[0, 0], [1, 0], [2, 0]], dtype=float)
+    with pytest.raises(P.HHGError) as e:
+        P.RG2D(line, np.array([[0, 1, 2]]))
+    assert e.value.status == 2
+    rg = P.RG3D(co3, ce3)
+    assert P.lib().hhg_rg3d_refine(rg._h, None) == 1
+    c, e3 = rg.mesh()
+    assert np.array_equal(c, co3) and np.array_equal(e3, ce3)
