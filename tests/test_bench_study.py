@@ -91,3 +91,95 @@ def test_theorem_bounds_reproduce_the_printed_constants():
         for j, (c1, c2) in enumerate(table, start=1):
             a, b = bench.theorem_bounds(theta, j)
             assert round(a, 2) == c1 and round(b, 2) == c2
+
+
+class _OracleMesh:
+    """Test double of the library's Mesh for the study programs' host logic: the same per-cell
+    closure layout (coordinates, solution, stored w_0), computed with the oracle."""
+
+    def __init__(self, c, e, L, stream=None):
+        from oracle import hhg_oracle as O
+        self.O = O
+        self.c, self.e, self.L = np.asarray(c, dtype=float), np.asarray(e), L
+        self.h = O.Hierarchy(self.c, self.e, L)
+        n = 1 << L
+        self.Nt = (n + 1) * (n + 2) // 2
+        self.info = type("Info", (), {"n_unknowns": int(self.h.levels[L].free.sum())})()
+
+    def n_nodes(self, level):
+        assert level == self.L
+        return self.Nt * len(self.e)
+
+    def level_coords(self, level, out):
+        n = 1 << level
+        ij = np.array([(i, j) for j in range(n + 1) for i in range(n + 1 - j)], dtype=float) / n
+        X0 = self.c[self.e[:, 0]]
+        J = np.stack([self.c[self.e[:, 1]] - X0, self.c[self.e[:, 2]] - X0], axis=2)
+        X = X0[:, None, :] + np.einsum("cra,pa->cpr", J, ij)
+        self.X = X.reshape(-1, 2)
+        out.copy_(torch.from_numpy(self.X))
+
+    def _to_closure(self, vals, level):
+        from scipy.spatial import cKDTree
+        d, idx = cKDTree(self.h.levels[level].x).query(self.X)
+        assert d.max() < 1e-12
+        return torch.from_numpy(vals[idx])
+
+    def set_data(self, f, g):
+        from scipy.spatial import cKDTree
+        tree = cKDTree(self.X)
+        fv, gv = f.numpy().copy(), g.numpy().copy()
+
+        def lookup(vals):
+            return lambda Y: vals[tree.query(Y)[1]]
+        self.prob = self.O.Problem(self.h, lookup(fv), lookup(gv))
+
+    def solve(self, prm, out):
+        self.uo, self.ws, _ = self.O.fmg(self.prob, prm.nu, prm.pre, prm.post, prm.n_extra)
+        out.copy_(self._to_closure(self.uo, self.L))
+
+    def estimate(self, j, want_local=True):
+        return self.O.estimate(self.h, self.uo, self.ws, j)
+
+    def get_vector(self, which, level, out):
+        assert which == 1 and level == self.L - 1
+        out.copy_(self._to_closure(self.ws[level], self.L))
+
+    def close(self):
+        pass
+
+
+def _stand_in():
+    import types
+    from oracle import hhg_oracle as O
+    return types.SimpleNamespace(solve_params=lambda **kw: types.SimpleNamespace(**kw), RG2D=O.RG2D,
+                                 Mesh=_OracleMesh, mark=O.mark_top_fraction)
+
+
+def test_effectivity_study_runs_end_to_end():
+    """Host logic of `--program effectivity` on a stand-in library: rows for every step, effectivity
+    = eta_j / ||e||, worst case = largest |log|, the paper's values and C_1, C_2 attached."""
+    res = bench.effectivity_study(_stand_in(), "cpu", L=5, K=1, nus=(2,), n_extra=2)
+    assert set(res) == {"waves2d_nu2", "lshape_nu2"}
+    for key, v in res.items():
+        assert [r["k"] for r in v["rows"]] == [0, 1]
+        assert v["rows"][1]["cells"] > v["rows"][0]["cells"]
+        for r in v["rows"]:
+            assert np.allclose(r["effectivity"], np.array(r["eta"]) / r["l2_error"])
+        for jj in range(4):
+            vals = [r["effectivity"][jj] for r in v["rows"]]
+            assert abs(math.log(v["worst_effectivity"][jj])) == max(abs(math.log(g)) for g in vals)
+        assert len(v["paper_worst_effectivity"]) == 4 and len(v["C1_C2"]) == 4
+
+
+def test_kl_compare_study_runs_end_to_end():
+    """Host logic of `--program kl_compare` on a stand-in library at L = 3, K = 2: the three schemes
+    report their final grids, Alg. 2 its history, and rho = (cells 4^L / cells_0) ||e_h|| / ||e_H||."""
+    res = bench.kl_compare_study(_stand_in(), "cpu", L=3, K=2, n_extra=2)
+    for name, r in res.items():
+        assert r["uniform"]["cells"] == r["coarse_cells"]
+        assert r["alg1"]["cells"] > r["coarse_cells"] and r["alg2"]["cells"] > r["coarse_cells"]
+        assert len(r["alg2"]["history"]) == 3
+        for key in ("uniform", "alg1", "alg2"):
+            s = r[key]
+            assert s["rho"] == pytest.approx(s["cells"] * 4 ** 3 / r["coarse_cells"] * s["l2_error"] / r["coarse_error"])
