@@ -265,16 +265,10 @@ void launch_level_coords(hhg_mesh_s* m, int l, const double* geom, double* xyz, 
 void launch_coarse_solve(hhg_mesh_s* m, const double* rhs, cudaStream_t s) {
   if (m->n0f == 0) return;
   size_t smem = (size_t)m->n0f * sizeof(double);
-  static bool attr_set[2] = {false, false};
+  // the attribute belongs to the current device, so it is set on every call that needs it
   if (smem > 48 * 1024) {
-    if (m->dim == 2 && !attr_set[0]) {
-      cudaFuncSetAttribute(k_coarse<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr_set[0] = true;
-    }
-    if (m->dim == 3 && !attr_set[1]) {
-      cudaFuncSetAttribute(k_coarse<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr_set[1] = true;
-    }
+    if (m->dim == 2) cudaFuncSetAttribute(k_coarse<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    else cudaFuncSetAttribute(k_coarse<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   }
   const Prims& P = m->verts;
   DISPATCH_DIM(m, k_coarse, 1, 1024, smem, s, m->n0f, m->d_cf_vert, P.d_ptr, P.d_cell, P.d_loc, ctx(m, 0), m->dS,
