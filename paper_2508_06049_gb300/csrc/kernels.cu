@@ -8,28 +8,22 @@
 
 namespace hhg {
 
-// One block of 256 threads per cell: the cell's np node contributions summed in a fixed order
-// (strided per-thread sums, an xor butterfly of warp shuffles inside each warp, then the eight warp
-// sums by a butterfly in warp 0), so the result is deterministic.
+// One block per cell: deterministic shared-memory tree sum of the cell's np node contributions.
 __global__ void __launch_bounds__(256) k_cell_sum(int64_t np, double scale, const double* __restrict__ part,
                                                   double* __restrict__ out) {
   grid_dependency_sync();
-  __shared__ double warp_sum[8];
-  const int T = blockIdx.x;
+  __shared__ double sh[256];
+  int T = blockIdx.x;
   const double* c = part + (int64_t)T * np;
   double acc = 0;
   for (int64_t q = threadIdx.x; q < np; q += 256) acc += c[q];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) warp_sum[warp] = acc;
+  sh[threadIdx.x] = acc;
   __syncthreads();
-  if (warp == 0) {
-    double v = lane < 8 ? warp_sum[lane] : 0.0;
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) out[T] = scale * v;
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) out[T] = scale * sh[0];
 }
 
 // x = a - b elementwise
