@@ -9,9 +9,10 @@
  *     constant on each macro element, Dirichlet data g.
  *   - Sec. 4.4, Alg. 4: FMG with nu V-cycles per level and Gauss-Seidel smoothing, storing the
  *     prolongated coarse solutions w_l; the ErrorEstimate procedure and the local indicators
- *     eta_T (Eq. 4.14, Sec. 4.4).
- *   - Sec. 5.1 / Sec. 3: marking of a top fraction of macro elements and 2D red-green
- *     refinement of the macro mesh (kl-refinement, Alg. 2).
+ *     eta_T (Eq. 4.14, Sec. 4.4), in L2 or, per the Remark in Sec. 4, in the energy norm or a
+ *     goal-oriented local seminorm.
+ *   - Sec. 5.1 / Sec. 3 / Alg. 3: marking of a top fraction of macro elements and 2D or 3D
+ *     red-green refinement of the macro mesh (kl-refinement, Alg. 2).
  *
  * Conventions (all entry points):
  *   - Every function returns an hhg_status; on failure hhg_last_error() gives a message
@@ -84,6 +85,7 @@ typedef struct {
   int n_colours;              /* macro-interior colours of the smoother (max over cells)   */
 } hhg_mesh_info;
 
+/* Global estimator values; norms are L2 (hhg_estimate) or the norm chosen in hhg_estimate_norm. */
 typedef struct {
   double eta_j;    /* theta~_l^j ||e~_l||, l = L - j          (Eq. 4.6)  */
   double theta;    /* ||e~_l|| / ||e~_{l-1}||                 (Eq. 4.5b) */
