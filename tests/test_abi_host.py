@@ -32,6 +32,22 @@ def test_library_exports_every_declared_symbol(P):
     assert not missing, missing
 
 
+def test_every_exported_symbol_is_declared(P):
+    """The reverse direction: the library's dynamic symbols named hhg_* are exactly the header's
+    entry points (nothing leaks into the ABI undocumented)."""
+    import shutil
+    import subprocess
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    out = subprocess.run([nm, "-D", "--defined-only", P.hhg.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.split() and line.split()[-1].startswith("hhg_")}
+    header = open(os.path.join(ROOT, "include", "hhg.h")).read()
+    declared = set(re.findall(r"\b(hhg_[a-z0-9_]+)\s*\(", header))
+    assert exported == declared, (sorted(exported - declared), sorted(declared - exported))
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_lattice_index_arithmetic(P, dim):
     for n in (1, 2, 3, 4, 5, 8, 16, 32, 64):
