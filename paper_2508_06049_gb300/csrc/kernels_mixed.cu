@@ -428,6 +428,21 @@ hhg_status mixed_prepare(hhg_mesh_s* m, int storage) {
   }
   size_t esz = storage == 1 ? 2 : 4;
   if (m->mixed_alloc && m->last_storage == storage) return HHG_OK;
+  if (m->mixed_alloc) {
+    // the correction buffers are reallocated below for the new storage type, and the cached
+    // mixed-precision graphs hold their old addresses: let queued work finish, then drop those
+    // graphs (they are captured again on their next use; their launch counts stay valid)
+    cudaError_t e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    for (auto it = m->graphs.begin(); it != m->graphs.end();) {
+      if (it->first.compare(0, 6, "mixed:") == 0) {
+        cudaGraphExecDestroy(it->second);
+        it = m->graphs.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
   for (auto& Lv : m->lv) {
     if (!m->mixed_alloc) {
       cudaError_t e;
