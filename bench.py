@@ -2,9 +2,10 @@
 
 Workload (default): unit cube, 4^3 cubes x 6 Kuhn tets = 384 macro tets, L = 6 structured levels
 (16,581,375 unknowns), f = 3 pi^2 prod sin(pi x_i), g = 0; FMG with nu = 2 V(2,1) cycles per
-level, estimator j = 1, marking of the top 12.5 %.  Precision: binary64 (--precision fp64) or
-binary32 V-cycles with bfloat16 correction storage inside binary64 iterative refinement
-(--precision mixed, the default), at the binary64 discretisation error.
+level, estimator j = 1, marking of the top 12.5 %.  Precision: binary64 (--precision fp64) and
+binary32 V-cycles inside binary64 iterative refinement (--precision mixed; coarse corrections stored
+in binary32 by default, --storage 1 bfloat16, --storage 2 binary16), both at the binary64
+discretisation error; --precision both (the default) runs the two arms.
 
 Metric: unknowns / (time of hhg_fmg_solve + hhg_estimate + hhg_mark) per step, device-timed with
 CUDA events on the library's stream, inputs resident in HBM.  e2e: the same through host buffers
@@ -50,7 +51,7 @@ def parse():
     ap.add_argument("--workload", default=None, help="default cube384_l6 (step) or waves3d_l8 (alg5)")
     ap.add_argument("--level", type=int, default=None, help="--program alg5 / effectivity: override the finest level L")
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
-    ap.add_argument("--storage", type=int, default=None, help="mixed arm: 0 binary32, 1 bfloat16")
+    ap.add_argument("--storage", type=int, default=None, help="mixed arm correction storage: 0 binary32 (default), 1 bfloat16, 2 binary16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel-only", type=int, default=0,

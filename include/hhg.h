@@ -60,9 +60,13 @@ typedef enum {
  * precision = 1 (mixed, no counterpart in the paper): iterative refinement whose residual
  *   r = b - A u and update u += c are binary64 on level L; the correction c solves A c = r with
  *   FMG (first step) or ir_vcycles V-cycles (later steps) computed in binary32, with the level
- *   vectors of the correction stored as `storage` (0 = binary32, 1 = bfloat16; 2 = binary16 is
- *   rejected with HHG_ERR_ARG) and accumulated in binary32.  ir_steps refinement steps follow the
- *   first one.
+ *   vectors of the correction stored as `storage` (0 = binary32, 1 = bfloat16, 2 = binary16) and
+ *   accumulated in binary32.  ir_steps refinement steps follow the first one.
+ *   binary16 (five exponent bits) stores each coarse level's correction times a power of two set
+ *   on the device after the restriction: the largest 2^e with 2^e * B_l * max|r_l| <= 2^10, where
+ *   B_l = 2^(l*dim) * |A_0^{-1}|_inf * (largest interface copy count) bounds |A_l^{-1}|_inf for the
+ *   partial right-hand side r_l; stores beyond +-65504 saturate.  It needs at least one free macro
+ *   vertex (|A_0^{-1}| comes from the direct coarse solve): otherwise HHG_ERR_ARG.
  * One Gauss-Seidel sweep updates, in this order: the macro vertices together with the even
  * edge-local nodes, the odd edge nodes, (3D) the face block - every macro face by Gauss-Seidel
  * over its colours (a + 2b) mod 3 with all nodes outside the face at their values from the start

@@ -26,7 +26,12 @@ template <> struct Conv<float, __nv_bfloat16> {
 };
 template <> struct Conv<float, __half> {
   static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
-  static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+  // saturating store: a magnitude beyond binary16's largest finite value is stored as +-65504 (NaN
+  // stays NaN), so a correction that outgrows its scale is clipped, not turned into an infinity
+  static __device__ __forceinline__ void st(__half* p, float v) {
+    if (fabsf(v) > 65504.0f) v = copysignf(65504.0f, v);
+    *p = __float2half_rn(v);
+  }
 };
 
 template <typename S> struct IsNarrow { static constexpr bool value = false; };

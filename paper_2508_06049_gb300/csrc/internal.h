@@ -121,6 +121,9 @@ struct hhg_mesh_s {
   int n0f = 0;
   std::vector<int> cf_vert;       // compact free-vertex index -> vertex-primitive index
   double* d_Ainv = nullptr;
+  double ainv_inf = 0;            // max row sum of |A_ff^{-1}| (range bound of binary16 corrections)
+  unsigned* d_rmax = nullptr;     // per level: bit pattern of max |r| (binary16 correction storage)
+  double* d_ainv_inf = nullptr;   // device copy of ainv_inf, written on the stream before each binary16 solve
   int* d_cf_vert = nullptr;
   std::vector<hhg::LevelData> lv;
   double* fL = nullptr;

@@ -2,12 +2,17 @@
 //
 // Step 1: FMG (Alg. 4 structure, same stage-ordered smoother) computed in binary32 on the original
 //         problem: the iterate of the current FMG top level is a binary32 vector, the coarse-grid
-//         corrections below it are stored as binary32 or bfloat16 and accumulated in binary32.
-//         The prolongated iterates w_l are written in binary64 for the estimator.
+//         corrections below it are stored as binary32, bfloat16 or binary16 and accumulated in
+//         binary32.  The prolongated iterates w_l are written in binary64 for the estimator.
+//         binary16 has five exponent bits, so each level's correction is stored times a power of two
+//         chosen, after the restriction, from max |r| of its right-hand side and a bound of
+//         |A_l^{-1}|_inf (k_set_scale16).
 // Steps 2..: r = b_L - A_L u_L and u_L += c in binary64 on level L; the correction c solves
 //         A_L c = r with V-cycles computed in binary32 (same storage rule for the coarse levels).
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <cmath>
 #include <type_traits>
 
 #include "internal.h"
@@ -50,6 +55,46 @@ __global__ void k_add_f32(const float* __restrict__ c, double* __restrict__ u, i
   grid_dependency_sync();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) u[i] += (double)c[i];
+}
+
+// ---- binary16 correction storage: per-level power-of-two scale ----
+// The correction c_l of a coarse level solves A_l c_l = r_l, so |c_l|_inf <= |A_l^{-1}|_inf |r_l|_inf.
+// For nested P1 meshes |A_l^{-1}|_inf grows like 2^{l d} |A_0^{-1}|_inf (the discrete Green's function
+// of a level-l lattice), and |A_0^{-1}|_inf is known exactly from the direct coarse solve.  The stored
+// right-hand sides are partial at interface nodes (a node's value is the sum over its copies), so the
+// assembled |r_l|_inf is bounded by the largest copy count times the largest stored |r|.  The scale
+// 2^e puts that bound at or below kScale16Target, far enough under binary16's largest finite value
+// (65504) to absorb an underestimate of |A_l^{-1}|_inf (coefficient jumps make the level-0 estimate
+// low by a small factor) and Gauss-Seidel iterates overshooting the solution.
+constexpr double kScale16Target = 1024.0;
+
+// max |r| over a vector, as the bit pattern of a non-negative binary32 (ordered like unsigned
+// integers; NaN orders above infinity), combined per warp and then by atomicMax into *out
+__global__ void k_absmax_bits(const float* __restrict__ r, int64_t n, unsigned* __restrict__ out) {
+  grid_dependency_sync();
+  unsigned v = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v = max(v, __float_as_uint(fabsf(r[i])));
+  v = __reduce_max_sync(0xffffffffu, v);
+  if ((threadIdx.x & 31) == 0) atomicMax(out, v);
+}
+
+// scale = the largest 2^e (|e| <= 120) with 2^e * bound * max|r| <= kScale16Target, where
+// bound = level_factor * |A_0^{-1}|_inf; 1 when max|r| is zero or not finite (the solve's finite
+// check then reports the divergence)
+__global__ void k_set_scale16(const unsigned* __restrict__ rmax_bits, const double* __restrict__ ainv_inf,
+                              double level_factor, float* __restrict__ scale) {
+  grid_dependency_sync();
+  if (threadIdx.x != 0) return;
+  const float rmax = __uint_as_float(*rmax_bits);
+  const double bound = level_factor * *ainv_inf;
+  float sc = 1.0f;
+  if (rmax > 0.0f && isfinite(rmax) && bound > 0.0) {
+    int e = ilogb(kScale16Target / (bound * (double)rmax));
+    e = max(-120, min(120, e));
+    sc = ldexpf(1.0f, e);
+  }
+  *scale = sc;
 }
 
 // binary32 FMG start: x_0 = g on Dirichlet nodes, 0 elsewhere
@@ -312,6 +357,19 @@ static void coarse32(hhg_mesh_s* m, U* u, const float* rhs, cudaStream_t s) {
                                                vec_of<U>(m, 0, u), m->d_Ainv);
 }
 
+// the scale of level l's binary16 correction from its restricted right-hand side r32 (k_set_scale16)
+template <int DIM>
+static void set_scale16(hhg_mesh_s* m, int l, cudaStream_t s) {
+  const LevelData& C = m->lv[l];
+  cudaMemsetAsync(m->d_rmax + l, 0, sizeof(unsigned), s);
+  unsigned nb = std::min<unsigned>(blocks_for(C.N), (unsigned)(2 * m->sm_count));
+  hhg_launch(k_absmax_bits, nb, kBlock, 0, s, (const float*)C.r32, (int64_t)C.N, m->d_rmax + l);
+  const int copies = std::max({1, m->verts.max_copies, m->edges.max_copies, m->faces.max_copies});
+  const double level_factor = std::ldexp((double)copies, l * DIM);
+  hhg_launch(k_set_scale16, 1, 32, 0, s, (const unsigned*)(m->d_rmax + l), (const double*)m->d_ainv_inf,
+             level_factor, C.cscale);
+}
+
 // V(pre, post)-cycle in binary32 on level l for A x = rhs; x has storage type U (binary32 on the
 // top level), the coarse corrections have storage type S.
 template <int DIM, typename S, typename U>
@@ -330,6 +388,7 @@ static void vcycle32(hhg_mesh_s* m, int l, U* x, const float* rhs, const hhg_sol
                                    false);
   dim3 gr(blocks_for(C.Nt), m->nc);
   hhg_launch(k_restrict<DIM, float, float, float>, gr, kBlock, 0, s, ctx(m, l), ctx(m, l - 1), m->d_dirmask, Lv.t32, C.r32);
+  if constexpr (std::is_same<S, __half>::value) set_scale16<DIM>(m, l - 1, s);
   S* c = (S*)C.c16;
   cudaMemsetAsync(c, 0, sizeof(S) * (size_t)C.N, s);
   vcycle32<DIM, S, S>(m, l - 1, c, C.r32, p, s);
@@ -415,19 +474,30 @@ void mixed_enqueue_solve(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t 
   if (p.storage == 1) {
     if (m->dim == 2) mixed_solve_t<2, __nv_bfloat16>(m, p, s);
     else mixed_solve_t<3, __nv_bfloat16>(m, p, s);
+  } else if (p.storage == 2) {
+    if (m->dim == 2) mixed_solve_t<2, __half>(m, p, s);
+    else mixed_solve_t<3, __half>(m, p, s);
   } else {
     if (m->dim == 2) mixed_solve_t<2, float>(m, p, s);
     else mixed_solve_t<3, float>(m, p, s);
   }
 }
 
+// binary16 storage: the bound |A_0^{-1}|_inf (changed by hhg_set_coefficient) is copied on the mesh
+// stream before every solve, so graphs captured earlier read the current value
+static hhg_status upload_ainv_inf(hhg_mesh_s* m) {
+  cudaError_t e = cudaMemcpyAsync(m->d_ainv_inf, &m->ainv_inf, sizeof(double), cudaMemcpyHostToDevice, m->stream);
+  return e == cudaSuccess ? HHG_OK : cuda_fail(e, "cudaMemcpyAsync");
+}
+
 hhg_status mixed_prepare(hhg_mesh_s* m, int storage) {
-  if (storage == 2) {
-    set_error("binary16 correction storage is not implemented; use storage 0 (binary32) or 1 (bfloat16)");
+  if (storage == 2 && m->n0f == 0) {
+    set_error("binary16 correction storage needs at least one free macro vertex (the range of the corrections "
+              "is bounded through the inverse of the level-0 operator); use storage 0 or 1");
     return HHG_ERR_ARG;
   }
-  size_t esz = storage == 1 ? 2 : 4;
-  if (m->mixed_alloc && m->last_storage == storage) return HHG_OK;
+  size_t esz = storage == 0 ? 4 : 2;
+  if (m->mixed_alloc && m->last_storage == storage) return storage == 2 ? upload_ainv_inf(m) : HHG_OK;
   if (m->mixed_alloc) {
     // the correction buffers are reallocated below for the new storage type, and the cached
     // mixed-precision graphs hold their old addresses: let queued work finish, then drop those
@@ -443,7 +513,20 @@ hhg_status mixed_prepare(hhg_mesh_s* m, int storage) {
       }
     }
   }
+  if (storage == 2 && !m->d_rmax) {
+    cudaError_t e;
+    if ((e = cudaMalloc(&m->d_rmax, sizeof(unsigned) * (m->L + 1))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMemset(m->d_rmax, 0, sizeof(unsigned) * (m->L + 1))) != cudaSuccess) return cuda_fail(e, "cudaMemset");
+    if ((e = cudaMalloc(&m->d_ainv_inf, sizeof(double))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    m->bytes += (long long)(sizeof(unsigned) * (m->L + 1) + sizeof(double));
+  }
   for (auto& Lv : m->lv) {
+    if (m->mixed_alloc && m->last_storage == 2) {
+      // leaving binary16 storage: the other storage types run with scale 1
+      float one = 1.0f;
+      cudaError_t e = cudaMemcpy(Lv.cscale, &one, sizeof(float), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+    }
     if (!m->mixed_alloc) {
       cudaError_t e;
       // kVecPad spare values: the staged interior stage copies 16-byte windows that may end past
@@ -471,7 +554,7 @@ hhg_status mixed_prepare(hhg_mesh_s* m, int storage) {
   }
   m->mixed_alloc = true;
   m->last_storage = storage;
-  return HHG_OK;
+  return storage == 2 ? upload_ainv_inf(m) : HHG_OK;
 }
 
 hhg_status mixed_profile_interior(hhg_mesh_s* m, int reps, cudaStream_t s, long long* units, double* bytes,

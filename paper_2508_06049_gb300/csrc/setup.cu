@@ -432,6 +432,12 @@ hhg_status upload_coefficient(hhg_mesh_s* m) {
       set_error("coarse operator is not positive definite (check Dirichlet flags / mesh)");
       return HHG_ERR_MESH;
     }
+    m->ainv_inf = 0;
+    for (int i = 0; i < n0; ++i) {
+      double rs = 0;
+      for (int j = 0; j < n0; ++j) rs += std::fabs(A[(size_t)i * n0 + j]);
+      m->ainv_inf = std::max(m->ainv_inf, rs);
+    }
     CK(cudaMemcpy(m->d_Ainv, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice));
   }
   return HHG_OK;
@@ -855,7 +861,7 @@ void free_mesh(hhg_mesh_s* m) {
     F(P->d_ptr); F(P->d_cell); F(P->d_loc); F(P->d_dir); F(P->d_pinv); F(P->d_pinvf); F(P->d_fw); F(P->d_fwf);
   }
   for (auto& g : m->groups) F(g.d_cells);
-  F(m->d_Ainv); F(m->d_cf_vert);
+  F(m->d_Ainv); F(m->d_cf_vert); F(m->d_rmax); F(m->d_ainv_inf);
   for (auto& Lv : m->lv) {
     F(Lv.d_ijk); F(Lv.d_icol); F(Lv.d_bnd); F(Lv.d_tiles); F(Lv.d_invl); F(Lv.d_invlf); F(Lv.d_fcol); F(Lv.u); F(Lv.b); F(Lv.rc); F(Lv.w); F(Lv.tmp);
     F(Lv.c16); F(Lv.r32); F(Lv.t32); F(Lv.cscale); F(Lv.x32); F(Lv.b32);

@@ -1,5 +1,5 @@
-"""Mixed precision (binary32 V-cycles, binary32/bfloat16 coarse-correction storage, binary64
-iterative refinement) against the binary64 oracle.
+"""Mixed precision (binary32 V-cycles, binary32/bfloat16/binary16 coarse-correction storage,
+binary64 iterative refinement) against the binary64 oracle.
 
 The binary64 oracle fixes the target: refinement steps must converge to the exact discrete solution,
 the first (binary32 FMG) step must stay within single-precision distance of the binary64 FMG, the
@@ -61,13 +61,17 @@ def test_binary32_fmg_step_and_estimator(P, name, L, storage, eta_tol):
     the iterates (~1e-7 |u|) bounds it to ~1e-3 relative: binary32 storage 5e-3, bfloat16 correction
     storage 2e-2.  Marking equals the binary64
     marking except for cells whose binary64 indicator lies within that error of the threshold."""
+    _fmg_step_and_estimator(P, name, L, storage, eta_tol, 1e-5 if storage == 0 else 1e-3)
+
+
+def _fmg_step_and_estimator(P, name, L, storage, eta_tol, u_tol):
     mesh, h, prob, idx = _setup(P, name, L)
     u32 = mesh.solve(nu=2, pre=2, post=1, precision=1, storage=storage, ir_steps=0)
     e32 = mesh.estimate(1)
     uo, ws, _ = O.fmg(prob, 2, 2, 1)
     eo = O.estimate(h, uo, ws, 1)
     scale = np.abs(uo).max()
-    assert np.abs(u32 - uo[idx]).max() / scale < (1e-5 if storage == 0 else 1e-3)
+    assert np.abs(u32 - uo[idx]).max() / scale < u_tol
     assert abs(e32["eta_j"] - eo["eta_j"]) / eo["eta_j"] < eta_tol
     assert np.abs(e32["eta_T"] - eo["eta_T"]).max() / eo["eta_T"].max() < eta_tol
     for frac in (0.2, 0.125):
@@ -108,4 +112,105 @@ def test_equal_error_on_full_size_cube(P):
         e = _l2_error(mesh, L, x, u, ue)
         assert abs(e - e_conv) <= 0.01 * e_conv, (storage, e, e_conv)
         assert np.array_equal(P.mark(mesh.estimate(1)["eta_T"], 0.125), m64)
+    mesh.close()
+
+
+# ---- binary16 correction storage (storage = 2) ----------------------------------------------
+# binary16 keeps 11 significand bits (bfloat16: 8) but only five exponent bits, so every coarse
+# level's correction is stored times a power of two chosen on the device from the level's
+# restricted residual and a bound of |A_l^{-1}|_inf.  The checks below are those of the other
+# storage types, with bfloat16's tolerances (binary16 rounds at least 8 times finer).
+
+@pytest.mark.parametrize("name,L", [("lshape_l7", 5), ("cube384_l6", 3), ("fichera336_l6", 3)])
+def test_binary16_storage_refinement_converges_to_exact_discrete_solution(P, name, L):
+    mesh, h, prob, idx = _setup(P, name, L)
+    u = mesh.solve(nu=2, pre=2, post=1, precision=1, storage=2, ir_steps=12, ir_vcycles=2)
+    ex = O.exact_solve(prob)
+    err = np.abs(u - ex[idx]).max() / np.abs(ex).max()
+    assert err < 1e-10, err
+    mesh.close()
+
+
+@pytest.mark.parametrize("name,L", [("lshape_l7", 6), ("cube384_l6", 4)])
+def test_binary16_storage_fmg_step_and_estimator(P, name, L):
+    _fmg_step_and_estimator(P, name, L, 2, 2e-2, 1e-3)
+
+
+def test_binary16_storage_on_four_decade_coefficients(P):
+    """3072-tet cube, k_T log-uniform over [1e-2, 1e2], L = 2: the level-0 bound of |A_l^{-1}|
+    underestimates the finer levels most here (coefficient jumps).  After the same number of
+    refinement steps the binary16 solution is as close to the exact discrete solution as the
+    binary32-storage one (the V-cycle, not the storage, limits the contraction on this field)."""
+    mesh, h, prob, idx = _setup(P, "cube3072_l7", 2)
+    ex = O.exact_solve(prob)
+    errs = {}
+    for storage in (0, 2):
+        u = mesh.solve(nu=2, pre=2, post=1, precision=1, storage=storage, ir_steps=12, ir_vcycles=2)
+        errs[storage] = np.abs(u - ex[idx]).max() / np.abs(ex).max()
+    assert np.isfinite(errs[2]) and errs[2] <= 1.5 * errs[0] + 1e-13, errs
+    mesh.close()
+
+
+def test_binary16_storage_leaves_the_other_storage_types_unchanged(P):
+    """A binary16 solve between two bfloat16 solves on one mesh changes nothing in the second (the
+    scales return to 1 when another storage type is selected), bit for bit."""
+    mesh, h, prob, idx = _setup(P, "cube384_l6", 3)
+    u1 = mesh.solve(nu=2, pre=2, post=1, precision=1, storage=1, ir_steps=2, ir_vcycles=2)
+    mesh.solve(nu=2, pre=2, post=1, precision=1, storage=2, ir_steps=2, ir_vcycles=2)
+    u1b = mesh.solve(nu=2, pre=2, post=1, precision=1, storage=1, ir_steps=2, ir_vcycles=2)
+    assert np.array_equal(u1, u1b)
+    mesh.close()
+
+
+def test_binary16_storage_needs_a_free_macro_vertex(P):
+    """Two macro triangles whose four vertices are all on the Dirichlet boundary: no level-0
+    operator, no range bound, so binary16 storage is rejected before anything runs."""
+    co, ce = W.square_mesh(1)
+    mesh = P.Mesh(co, ce, 2)
+    x = mesh.level_coords(2)
+    mesh.set_data(np.ones(len(x)), np.zeros(len(x)))
+    with pytest.raises(P.HHGError) as e:
+        mesh.solve(nu=2, pre=2, post=1, precision=1, storage=2)
+    assert e.value.status == 1  # HHG_ERR_ARG
+    mesh.close()
+
+
+def test_binary16_storage_equal_error_on_full_size_cube3072(P):
+    """3072-tet cube at its full size, L = 7 (1.07e9 unknowns, k_T over four decades): the mixed
+    solve with binary16 correction storage reaches the discretisation error to two digits
+    (algebraic error <= 1 % of eta_1 against a converged binary64 reference), the criterion the
+    bfloat16 arm meets in the full-size tests."""
+    import torch
+    co, ce, L, f, g, k, _ = W.workload("cube3072_l7")
+    mesh = P.Mesh(co, ce, L)
+    mesh.set_coefficient(k)
+    N = mesh.n_nodes(L)
+    dev = torch.device("cuda:0")
+    fd = torch.ones(N, dtype=torch.float64, device=dev)
+    gd = torch.zeros(N, dtype=torch.float64, device=dev)
+    mesh.set_data(fd, gd)
+    del fd, gd
+    cells = torch.empty(len(ce), dtype=torch.float64, device=dev)
+    ref = torch.empty(N, dtype=torch.float64, device=dev)
+    u = torch.empty(N, dtype=torch.float64, device=dev)
+    mesh.solve(P.solve_params(n_extra=100), out=ref)
+    torch.cuda.synchronize()
+    eta = mesh.estimate(1)["eta_j"]
+
+    def err_of(params):
+        mesh.solve(params, out=u)
+        mesh.cell_mass_norms_noalloc(u, ref, cells)
+        torch.cuda.synchronize()
+        return math.sqrt(float(cells.sum().item()))
+
+    ok = None
+    for steps in (16, 24, 32, 48):
+        err = err_of(P.solve_params(precision=1, storage=2, ir_steps=steps, ir_vcycles=2))
+        assert math.isfinite(err)
+        if err <= 0.01 * eta:
+            ok = steps
+            break
+    assert ok is not None, (err, eta)
+    print("cube3072_l7: binary16 storage reaches equal error after %d refinement steps" % ok)
+    del ref, u, cells
     mesh.close()
