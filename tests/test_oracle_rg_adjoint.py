@@ -181,6 +181,46 @@ def test_adjoint_gradients_match_central_differences(name, L):
         assert abs(fd - gf[j]) <= 1e-6 * abs(gf).max(), (j, fd, gf[j])
 
 
+@pytest.mark.parametrize("name,L", [("fichera336_l6", 1), ("square_l4", 3)])
+def test_adjoint_taylor_remainders(name, L):
+    """Taylor test of the adjoint gradients along random directions.  The discrete solution is
+    affine in the nodal source f, so J(f + e d) - J(f) - e <dJ/df, d> equals e^2 J(S d) exactly,
+    where S d solves the problem with source d and zero boundary data (this also covers f at
+    Dirichlet nodes, which reaches free rows through b = M f).  In k the remainder
+    J(k + e dk) - J(k) - e <dJ/dk, dk> is O(e^2): it falls by a factor 4 when e is halved, where a
+    wrong gradient leaves an O(e) remainder that falls by 2."""
+    co, ce, _, f, g, k, _ = W.workload(name, L)
+    if k is None:
+        k = W.coeff_uniform(len(ce), seed=5)
+    in_S = np.all(co[ce].mean(axis=1) > 0.5, axis=1)
+    h = O.Hierarchy(co, ce, L, k=k)
+    x = h.levels[L].x
+    fL = f(x) + 0.1 * np.sin(3 * x.sum(axis=1))
+
+    def J_of(hh, ff, gg):
+        uu = O.exact_solve(O.Problem(hh, ff, gg))
+        return float(O.local_mass_sq(hh.levels[L], uu, len(ce))[in_S].sum())
+
+    def zero(y):
+        return np.zeros(len(y))
+
+    u = O.exact_solve(O.Problem(h, fL, g))
+    J, gf, gk, _ = O.adjoint_gradients(h, u, in_S)
+    rng = np.random.default_rng(7)
+    d = rng.uniform(-1.0, 1.0, len(x))
+    Jd = J_of(h, d, zero)
+    assert Jd > 0
+    for e in (1.0, 0.1):
+        R = J_of(h, fL + e * d, g) - J - e * float(gf @ d)
+        scale = max(J, e * abs(float(gf @ d)), e * e * Jd)
+        assert abs(R - e * e * Jd) <= 1e-10 * scale, (e, R, e * e * Jd)
+    dk = k * rng.uniform(-1.0, 1.0, len(k))
+    slope = float(gk @ dk)
+    R = [J_of(O.Hierarchy(co, ce, L, k=k + e * dk), fL, g) - J - e * slope for e in (1e-2, 5e-3)]
+    assert abs(R[0]) <= 1e-2 * abs(slope), (R, slope)
+    assert 3.6 <= R[0] / R[1] <= 4.4, R
+
+
 # ---------------------------------------------------------------- planted mistakes
 
 def test_planted_mass_mistake_is_caught(monkeypatch):
