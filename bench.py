@@ -316,7 +316,8 @@ def run_arm(args, rank, world, su, precision):
         peak = pk.get("hbm_gbs", 6800.0)
         rf_obj = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                   "traffic": TRAFFIC_BYTES.get((args.workload, precision)), "peak_kind": pk_kind + " (MEASURED_PEAKS.json hbm_gbs)", "tflops": tfl}
-    rf_obj.update({"kernel": "k_smooth_interior (level L, colour 0)", "ms_per_launch": ms_k,
+    kname = "k_smooth_interior" if precision == "fp64" else "k_smooth_interior_multi (binary32, four cells per thread)"
+    rf_obj.update({"kernel": kname + " (level L, first cell group, colour 0)", "ms_per_launch": ms_k,
                    "units_per_launch": units, "algorithmic_bytes_per_launch": kbytes,
                    "algorithmic_flops_per_launch": kflops})
     launches = mesh.launch_count(prm) + 7   # solve graph + estimator kernels (j = 1)
