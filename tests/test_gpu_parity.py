@@ -351,3 +351,47 @@ def test_level_coords_device_path_matches_host_path(P, name):
         dist, _ = cKDTree(h.levels[lev].x).query(xh)
         assert dist.max() < 1e-12
     mesh.close()
+
+
+DEGENERATE = {
+    # two macro triangles of the unit square: all four macro vertices on the Dirichlet boundary
+    "two_triangles": lambda: (*W.square_mesh(1), 5),
+    # one general macro tet: every vertex, edge and face on the Dirichlet boundary
+    "one_tet": lambda: (np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.2, 0.9, 0.0], [0.3, 0.25, 0.8]]),
+                        np.array([[0, 1, 2, 3]]), 4),
+}
+
+
+@pytest.mark.parametrize("name", list(DEGENERATE))
+def test_coarse_grid_without_unknowns(P, name):
+    """Degenerate coarse grid: level 0 has no unknown, so the direct coarse solve is empty and every
+    V-cycle bottoms out on level 1.  FMG u_L, the stored w_l, the estimator for j = 1, 2 and the
+    marking match the oracle, and the mixed-precision refinement (binary32 storage) converges to the
+    exact discrete solution."""
+    co, ce, L = DEGENERATE[name]()
+    h = O.Hierarchy(co, ce, L)
+    assert not h.levels[0].free.any() and h.levels[L].free.any()
+    mesh = P.Mesh(co, ce, L)
+    maps = []
+    for l in range(L + 1):
+        dist, idx = cKDTree(h.levels[l].x).query(mesh.level_coords(l))
+        assert dist.max() < 1e-9
+        maps.append(idx)
+    f, g = fg(h.dim)
+    x = mesh.level_coords(L)
+    mesh.set_data(np.ascontiguousarray(f(x)), np.ascontiguousarray(g(x)))
+    u = mesh.solve(nu=2, pre=2, post=1)
+    prob = O.Problem(h, f, g)
+    uo, ws, _ = O.fmg(prob, 2, 2, 1)
+    close(u, uo[maps[L]])
+    for l in range(L):
+        close(mesh.get_vector(1, l), ws[l][maps[l + 1]])
+    for j in (1, 2):
+        eg = mesh.estimate(j)
+        eo = O.estimate(h, uo, ws, j)
+        close_estimates(eg, eo, h, uo)
+        assert np.array_equal(P.mark(eg["eta_T"], 0.5), O.mark_top_fraction(eo["eta_T"], 0.5))
+    um = mesh.solve(nu=2, pre=2, post=1, precision=1, storage=0, ir_steps=12, ir_vcycles=2)
+    ex = O.exact_solve(prob)
+    assert np.abs(um - ex[maps[L]]).max() <= 1e-10 * np.abs(ex).max()
+    mesh.close()
