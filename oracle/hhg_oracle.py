@@ -1,4 +1,5 @@
-"""Plain CPU FP64 oracle: HHG refinement, P1 assembly, FMG (Alg. 4), estimator, marking, 2D red-green.
+"""Plain CPU FP64 oracle: HHG refinement, P1 assembly, FMG (Alg. 4), estimator, marking, 2D and 3D
+red-green refinement (Alg. 3), adjoint gradients.
 
 TEST INFRASTRUCTURE ONLY -- imported by tests, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py``; never by the product path.
@@ -44,9 +45,17 @@ What each part follows
   ||G(v|_T)||, here G(v|_T) = sqrt(w_T) v|_T with per-macro weights w_T.
 * Theorem 4.1 / Corollaries 4.3-4.4: effectivity constants.
 * Sec. 3 and Sec. 5.1: marking of a top fraction of macro elements; 2D red-green
-  refinement with greens reverted before the next step.
+  refinement with greens reverted before the next step; Alg. 3 (3D red-green: red
+  by Bey's rule, the face and tet closure rules, three green types).
+* No paper counterpart: gradients of J(u) = u^T M_S u with respect to the nodal source
+  and the per-macro coefficients, by an exact adjoint solve (implicit differentiation).
 
 No kernel blocking, fusion or reordering beyond the definitions above.
+
+Pins: every function here is checked against facts that do not come from this file
+(closed forms, invariants, brute force, the paper's printed constants, finite
+differences, planted mistakes) in tests/test_oracle_pins.py, test_oracle_norms.py,
+test_oracle_rg_adjoint.py and test_rg3d.py; none is parity-unpinned.
 """
 
 from __future__ import annotations
