@@ -101,3 +101,37 @@ def test_gpu_entry_points_fail_cleanly_without_gpu(P):
     co, ce = W.square_mesh(2)
     with pytest.raises(P.HHGError):
         P.Mesh(co, ce, 2)
+
+
+def test_binding_argument_kinds_match_header():
+    """Every entry point the Python binding declares has the header's parameter list: the same
+    number of arguments and, position by position, the same kind (pointer or handle, int, double).
+    A mismatch would pass garbage through ctypes, so this is checked without calling anything."""
+    hdr = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "hhg.h")).read(), flags=re.S)
+    decls = {}
+    for m in re.finditer(r"\b(?:hhg_status|int|const char\s*\*|void)\s+(hhg_\w+)\s*\(([^)]*)\)\s*;", hdr):
+        kinds = []
+        for a in m.group(2).split(","):
+            a = a.strip()
+            if not a or a == "void":
+                continue
+            if "*" in a or re.match(r"(const\s+)?hhg_(mesh|rg2d|rg3d)\b", a):
+                kinds.append("ptr")
+            elif re.match(r"(const\s+)?double\b", a):
+                kinds.append("double")
+            elif re.match(r"(const\s+)?(int|long long|unsigned)\b", a):
+                kinds.append("int")
+            else:
+                kinds.append("?" + a)
+        decls[m.group(1)] = kinds
+    src = open(os.path.join(ROOT, "paper_2508_06049_gb300", "hhg.py")).read()
+    start = src.index("sig = {")
+    body = src[start:src.index("}", start)]
+    kind_of = {"vp": "ptr", "u8": "ptr", "i": "int", "d": "double"}
+    bound = dict()
+    for m in re.finditer(r'"(hhg_\w+)":\s*\[([^\]]*)\]', body):
+        toks = [t.strip() for t in m.group(2).split(",") if t.strip()]
+        bound[m.group(1)] = ["ptr" if t.startswith("C.POINTER(") else kind_of.get(t, "?" + t) for t in toks]
+    assert bound and set(bound) == set(decls), sorted(set(bound) ^ set(decls))
+    for name, kinds in bound.items():
+        assert kinds == decls[name], (name, kinds, decls[name])
