@@ -277,6 +277,42 @@ def test_face_block_is_per_face_gauss_seidel_with_frozen_surroundings():
 
 # ---------------------------------------------------------------- discretisation (Sec. 5)
 
+def _inv_inf(lev):
+    A = lev.A.toarray()[np.ix_(lev.free, lev.free)]
+    return float(np.abs(np.linalg.inv(A)).sum(axis=1).max())
+
+
+@pytest.mark.parametrize("mesh,L,lo,hi", [
+    ("square", 3, 1.0, 1.5), ("lshape", 2, 1.0, 1.5), ("cube", 2, 1.0, 1.5),
+    ("cube_k4", 2, 1.0, 16.0),
+])
+def test_inverse_norm_grows_like_the_level_volume(mesh, L, lo, hi):
+    """The range bound of binary16 correction storage: |A_l^{-1}|_inf / (2^{l d} |A_0^{-1}|_inf)
+    stays within [lo, hi] (the discrete Green's function of a nested P1 level grows like 2^{l d}).
+    Dense inverses of the assembled free-node operators on the first levels.  With a constant
+    coefficient the ratio stays near 1 (at most 1.18 / 1.21 / 1.32 on these meshes); with k_T
+    log-uniform over four decades level 0 does not resolve the coefficient jumps and the ratio
+    levels off near 15 on this 384-tet cube (5.3, 13.2, 14.1, 14.5 on levels 1-4)."""
+    if mesh == "square":
+        co, ce = W.square_mesh(2)
+        k = None
+    elif mesh == "lshape":
+        co, ce = W.lshape_mesh()
+        k = None
+    elif mesh == "cube":
+        co, ce = W.cube_mesh(2)
+        k = None
+    else:
+        co, ce = W.cube_mesh(4)
+        k = W.coeff_loguniform(len(ce), seed=0)
+    h = O.Hierarchy(co, ce, L, k=k)
+    d = h.dim
+    a0 = _inv_inf(h.levels[0])
+    for l in range(1, L + 1):
+        r = _inv_inf(h.levels[l]) / (2.0 ** (l * d) * a0)
+        assert lo <= r <= hi, (l, r)
+
+
 def _errors(name, Ls, fn=None):
     out = []
     for L in Ls:
