@@ -334,6 +334,44 @@ def test_full_size_cube384_l6_properties(P):
     assert 3.5 < errs[0] / errs[1] < 4.5, errs
 
 
+def test_full_size_cube384_l6_sampled_estimator_parity(P):
+    """The benchmark workload at its full size (384-tet cube, L = 6, 16.6 M unknowns; binary64 FMG
+    with nu = 2, V(2,1) and 4 extra V-cycles, the solve and estimator graphs bench.py times).
+    eta_T is local: eta_T^2 = (u_L - w_{L-1})^T M_{L,T} (u_L - w_{L-1}) over macro cell T's own
+    closure nodes.  For sampled cells the oracle recomputes it from the library's u_L and w_{L-1} on
+    that cell alone (a one-cell hierarchy, mass matrix assembled element by element); the squared
+    indicators sum to ||e~_{L-1}||^2 and the marking equals the oracle's marking of them."""
+    co, ce, L, f, g, k, _ = W.workload("cube384_l6")
+    _sampled_estimator_parity(P, co, ce, L, f, g)
+
+
+def _sampled_estimator_parity(P, co, ce, L, f, g, n_sample=4):
+    mesh = P.Mesh(co, ce, L)
+    x = mesh.level_coords(L)
+    mesh.set_data(np.ascontiguousarray(f(x)), np.ascontiguousarray(g(x)))
+    u = mesh.solve(nu=2, pre=2, post=1, n_extra=4)
+    w = mesh.get_vector(1, L - 1)
+    est = mesh.estimate(1)
+    nc = len(ce)
+    Nt = len(x) // nc
+    assert Nt * nc == len(x)
+    rng = np.random.default_rng(11)
+    cells = sorted({0, nc - 1} | set(rng.choice(nc, n_sample, replace=False).tolist()))
+    for T in cells:
+        hT = O.Hierarchy(co[ce[T]], np.arange(co.shape[1] + 1)[None, :], L)
+        lev = hT.levels[L]
+        sl = slice(T * Nt, (T + 1) * Nt)
+        dist, idx = cKDTree(x[sl]).query(lev.x)
+        assert dist.max() < 1e-12 and len(np.unique(idx)) == Nt
+        e = (u[sl] - w[sl])[idx]
+        ref = float(e @ (lev.M @ e))
+        assert abs(est["eta_T"][T] ** 2 - ref) <= 1e-11 * ref, (T, est["eta_T"][T] ** 2, ref)
+    sq = est["eta_T"] ** 2
+    assert abs(est["err_Lm1"] ** 2 - sq.sum()) <= 1e-12 * sq.sum()
+    assert np.array_equal(P.mark(est["eta_T"], 0.125), O.mark_top_fraction(est["eta_T"], 0.125))
+    mesh.close()
+
+
 @pytest.mark.parametrize("name", ["lshape", "cube"])
 def test_level_coords_device_path_matches_host_path(P, name):
     """hhg_level_coords into device memory (one kernel) gives the host path's coordinates bit for
