@@ -204,7 +204,11 @@ hhg_status hhg_rg3d_mark_refine(hhg_rg3d rg, const double* eta_T, double fractio
 /* Adjoint of the discrete solve (no counterpart in the paper): for J(u) = u^T M_S u with
  * M_S the mass matrix of the micro elements inside the macro cells flagged in in_S, on the
  * solution of the last hhg_fmg_solve, solve A lambda = 2 M_S u (lambda = 0 on Dirichlet nodes)
- * with FMG + params->n_extra V-cycles and return
+ * and return the results below.  params->precision = 0: FMG + params->n_extra V-cycles in binary64.
+ * precision = 1: binary64 refinement from lambda = 0 whose corrections come from binary32
+ * V-cycles stored as params->storage (as in hhg_fmg_solve): a first step of ir_vcycles V-cycles
+ * (the adjoint right-hand side is given on level L only, so there is no binary32 FMG step), then
+ * ir_steps steps of ir_vcycles V-cycles and n_extra steps of one.  The results are
  *   J (host), grad_f = M_L lambda (dJ/d nodal f_L; host or device, N_L, may be NULL),
  *   grad_k[T] = -lambda^T A_T^(1) u (dJ/dk_T; host, n_cells, may be NULL). */
 hhg_status hhg_adjoint_l2(hhg_mesh mesh, const hhg_solve_params* params, const unsigned char* in_S,

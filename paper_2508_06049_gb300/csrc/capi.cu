@@ -26,6 +26,7 @@ hhg_status mixed_profile_interior(hhg_mesh_s* m, int reps, cudaStream_t s, long 
                                   double* flops, int variant = 0);
 hhg_status mixed_prepare(hhg_mesh_s* m, int storage);
 void mixed_enqueue_solve(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t s);
+void mixed_enqueue_adjoint(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t s);
 }  // namespace hhg
 
 using namespace hhg;
@@ -601,10 +602,13 @@ hhg_status hhg_adjoint_l2(hhg_mesh m, const hhg_solve_params* params, const unsi
   REQUIRE(m && in_S, HHG_ERR_ARG, "NULL argument");
   hhg_status st = check_params(m, params);
   if (st != HHG_OK) return st;
-  REQUIRE(params->precision == 0, HHG_ERR_ARG, "the adjoint solve runs in binary64 (precision = 0)");
   REQUIRE(m->solved, HHG_ERR_STATE, "hhg_adjoint_l2 needs a previous hhg_fmg_solve");
   DeviceGuard g(m->device);
   ENTER(m);
+  if (params->precision == 1) {  // mixed-precision buffers before any work is queued
+    st = mixed_prepare(m, params->storage);
+    if (st != HHG_OK) return st;
+  }
   cudaStream_t s = m->stream;
   const int L = m->L, nc = m->nc;
   LevelData& LL = m->lv[L];
@@ -623,10 +627,15 @@ hhg_status hhg_adjoint_l2(hhg_mesh m, const hhg_solve_params* params, const unsi
   launch_mass_norm_sq(m, usave, nullptr, m->d_red, s);
   std::vector<double> h(nc);
   cudaMemcpyAsync(h.data(), m->d_red, sizeof(double) * nc, cudaMemcpyDeviceToHost, s);
-  // adjoint rhs 2 M_S u on level L, then FMG with zero Dirichlet data
+  // adjoint rhs 2 M_S u on level L, then FMG with zero Dirichlet data (binary64), or binary64
+  // refinement with binary32 V-cycles (mixed)
   launch_adjoint_rhs(m, dS, usave, LL.b, s);
   hhg_solve_params p = *params;
-  st = run_graph(m, graph_key("adjoint", p), [&](cudaStream_t cs) { enqueue_fmg(m, p, true, cs); });
+  if (p.precision == 0) {
+    st = run_graph(m, graph_key("adjoint", p), [&](cudaStream_t cs) { enqueue_fmg(m, p, true, cs); });
+  } else {
+    st = run_graph(m, graph_key("mixed-adjoint", p), [&](cudaStream_t cs) { mixed_enqueue_adjoint(m, p, cs); });
+  }
   if (st == HHG_OK) {
     if (grad_f) {
       launch_apply_op(m, L, 1, LL.u, LL.tmp, s);

@@ -196,6 +196,7 @@ void launch_mixed_update_L(hhg_mesh_s* m, int storage, cudaStream_t s);  // u_L 
 void launch_mixed_vcycle_ops(hhg_mesh_s* m, int storage);        // (declared for completeness)
 void mixed_enqueue_vcycle(hhg_mesh_s* m, int l, int storage, const hhg_solve_params& p, cudaStream_t s);
 void mixed_enqueue_fmg(hhg_mesh_s* m, int storage, const hhg_solve_params& p, cudaStream_t s);
+void mixed_enqueue_adjoint(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t s);
 void mixed_set_scales(hhg_mesh_s* m, int storage, cudaStream_t s);
 
 }  // namespace hhg

@@ -470,6 +470,45 @@ static void mixed_solve_t(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t
   launch_finite_check(m, LL.u, LL.N, s);
 }
 
+// One binary64 refinement step on level L: r = b_L - A_L u_L in binary64 (interface partials
+// collected), the correction from nv binary32 V-cycles (coarse corrections stored as S), u_L += c.
+template <int DIM, typename S>
+static void ir_step(hhg_mesh_s* m, int nv, const hhg_solve_params& p, cudaStream_t s) {
+  LevelData& LL = m->lv[m->L];
+  ir_residual<DIM>(m, s);
+  cudaMemsetAsync(LL.x32, 0, sizeof(float) * (size_t)LL.N, s);
+  for (int q = 0; q < nv; ++q) vcycle32<DIM, S, float>(m, m->L, LL.x32, LL.r32, p, s);
+  hhg_launch(k_add_f32, blocks_for(LL.N), kBlock, 0, s, LL.x32, LL.u, LL.N);
+}
+
+// Mixed-precision adjoint solve A lam = b_L, where b_L holds the adjoint right-hand side and the
+// Dirichlet values are zero: binary64 refinement from lam = 0 with the forward solve's storage rule.
+// The adjoint right-hand side is given on level L only, so the first step takes ir_vcycles binary32
+// V-cycles where the forward solve takes a binary32 FMG; ir_steps steps of ir_vcycles V-cycles and
+// n_extra steps of one V-cycle follow, as in the forward solve.
+template <int DIM, typename S>
+static void mixed_adjoint_t(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t s) {
+  LevelData& LL = m->lv[m->L];
+  cudaMemsetAsync(LL.u, 0, sizeof(double) * (size_t)LL.N, s);
+  for (int it = 0; it <= p.ir_steps; ++it) ir_step<DIM, S>(m, p.ir_vcycles, p, s);
+  for (int q = 0; q < p.n_extra; ++q) ir_step<DIM, S>(m, 1, p, s);
+  cudaMemsetAsync(m->d_flag, 0, sizeof(int), s);
+  launch_finite_check(m, LL.u, LL.N, s);
+}
+
+void mixed_enqueue_adjoint(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t s) {
+  if (p.storage == 1) {
+    if (m->dim == 2) mixed_adjoint_t<2, __nv_bfloat16>(m, p, s);
+    else mixed_adjoint_t<3, __nv_bfloat16>(m, p, s);
+  } else if (p.storage == 2) {
+    if (m->dim == 2) mixed_adjoint_t<2, __half>(m, p, s);
+    else mixed_adjoint_t<3, __half>(m, p, s);
+  } else {
+    if (m->dim == 2) mixed_adjoint_t<2, float>(m, p, s);
+    else mixed_adjoint_t<3, float>(m, p, s);
+  }
+}
+
 void mixed_enqueue_solve(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t s) {
   if (p.storage == 1) {
     if (m->dim == 2) mixed_solve_t<2, __nv_bfloat16>(m, p, s);
@@ -500,12 +539,13 @@ hhg_status mixed_prepare(hhg_mesh_s* m, int storage) {
   if (m->mixed_alloc && m->last_storage == storage) return storage == 2 ? upload_ainv_inf(m) : HHG_OK;
   if (m->mixed_alloc) {
     // the correction buffers are reallocated below for the new storage type, and the cached
-    // mixed-precision graphs hold their old addresses: let queued work finish, then drop those
-    // graphs (they are captured again on their next use; their launch counts stay valid)
+    // mixed-precision graphs (keys "mixed:..." and "mixed-adjoint:...") hold their old addresses:
+    // let queued work finish, then drop those graphs (they are captured again on their next use;
+    // their launch counts stay valid)
     cudaError_t e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     for (auto it = m->graphs.begin(); it != m->graphs.end();) {
-      if (it->first.compare(0, 6, "mixed:") == 0) {
+      if (it->first.compare(0, 5, "mixed") == 0) {
         cudaGraphExecDestroy(it->second);
         it = m->graphs.erase(it);
       } else {

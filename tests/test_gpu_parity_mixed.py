@@ -214,3 +214,55 @@ def test_binary16_storage_equal_error_on_full_size_cube3072(P):
     print("cube3072_l7: binary16 storage reaches equal error after %d refinement steps" % ok)
     del ref, u, cells
     mesh.close()
+
+
+# ---- mixed-precision adjoint ------------------------------------------------------------------
+# hhg_adjoint_l2 with precision = 1: binary64 refinement from lam = 0 with binary32 V-cycles (no
+# binary32 FMG step: the adjoint right-hand side is given on level L only).  Refinement converges to
+# the exact discrete adjoint, so the gradients meet the binary64 adjoint's tolerance against the
+# oracle's exact sparse solves (J, dJ/df, dJ/dk to 1e-9 relative).
+
+@pytest.mark.parametrize("name,L,storage", [("fichera336_l6", 3, 0), ("fichera336_l6", 3, 2),
+                                            ("square_l4", 4, 1)])
+def test_mixed_adjoint_gradients_match_oracle(P, name, L, storage):
+    mesh, h, prob, idx = _setup(P, name, L)
+    co, ce = h.coords, h.cells
+    prm = P.solve_params(nu=2, pre=2, post=1, precision=1, storage=storage, ir_steps=20, ir_vcycles=2)
+    mesh.solve(prm)
+    in_S = np.all(co[ce].mean(axis=1) > 0.5, axis=1)
+    assert in_S.any()
+    J, gf, gk = mesh.adjoint_l2(in_S, params=prm)
+    uo = O.exact_solve(prob)
+    Jo, gfo, gko, _ = O.adjoint_gradients(h, uo, in_S)
+    assert abs(J - Jo) <= 1e-9 * abs(Jo), (J, Jo)
+    assert np.abs(gf - gfo[idx]).max() <= 1e-9 * np.abs(gfo).max()
+    assert np.abs(gk - gko).max() <= 1e-9 * np.abs(gko).max()
+    mesh.close()
+
+
+def test_mixed_adjoint_through_autograd(P):
+    """The autograd wrapper with mixed-precision parameters (forward and adjoint solves by binary64
+    refinement with binary32 V-cycles) gives the binary64 adjoint's gradients."""
+    import torch
+    from paper_2508_06049_gb300.autograd import l2_functional
+    co, ce = W.fichera_mesh()
+    L = 3
+    k0 = W.coeff_uniform(len(ce), seed=1)
+    mesh = P.Mesh(co, ce, L)
+    x = mesh.level_coords(L)
+    dev = torch.device("cuda:0")
+    f = torch.tensor(np.sin(3 * x[:, 0]) + x[:, 2], dtype=torch.float64, device=dev, requires_grad=True)
+    k = torch.tensor(k0, dtype=torch.float64, requires_grad=True)
+    in_S = np.all(co[ce].mean(axis=1) > 0.5, axis=1)
+    prm32 = P.solve_params(nu=2, pre=2, post=1, precision=1, storage=0, ir_steps=20, ir_vcycles=2)
+    J = l2_functional(f, k, mesh, in_S, params=prm32)
+    J.backward()
+    prm64 = P.solve_params(n_extra=40)
+    mesh.set_coefficient(k0)
+    mesh.set_data(f.detach().cpu().numpy(), np.zeros(len(x)))
+    mesh.solve(prm64)
+    Jr, gf, gk = mesh.adjoint_l2(in_S, params=prm64)
+    assert abs(J.item() - Jr) <= 1e-9 * abs(Jr)
+    assert np.abs(f.grad.cpu().numpy() - gf).max() <= 1e-9 * np.abs(gf).max()
+    assert np.abs(k.grad.numpy() - gk).max() <= 1e-9 * np.abs(gk).max()
+    mesh.close()
