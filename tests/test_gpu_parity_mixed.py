@@ -266,3 +266,35 @@ def test_mixed_adjoint_through_autograd(P):
     assert np.abs(f.grad.cpu().numpy() - gf).max() <= 1e-9 * np.abs(gf).max()
     assert np.abs(k.grad.numpy() - gk).max() <= 1e-9 * np.abs(gk).max()
     mesh.close()
+
+
+def test_mixed_adjoint_full_size_fichera336_l6(P):
+    """Fichera corner at its full size (L = 6, k_T uniform in [0.5, 2], J = int over [0.5, 1]^3 of
+    u^2).  The mixed forward and adjoint solves give J and both gradients within 1e-8 relative of
+    the binary64 ones (which the full-size tests check against central differences), and the mixed
+    gradients satisfy the homogeneity identities sum_i f_i dJ/df_i = 2 J and
+    sum_T k_T dJ/dk_T = -2 J (J is quadratic in f and of degree -2 in k)."""
+    co, ce, L, f, g, k, _ = W.workload("fichera336_l6")
+    mesh = P.Mesh(co, ce, L)
+    mesh.set_coefficient(k)
+    x = mesh.level_coords(L)
+    f0 = np.ascontiguousarray(f(x))
+    mesh.set_data(f0, np.zeros(len(x)))
+    in_S = np.all(co[ce].mean(axis=1) > 0.5, axis=1)
+    prm64 = P.solve_params(n_extra=40)
+    mesh.solve(prm64)
+    J64, gf64, gk64 = mesh.adjoint_l2(in_S, params=prm64)
+    prm32 = P.solve_params(nu=2, pre=2, post=1, precision=1, storage=0, ir_steps=20, ir_vcycles=2)
+    mesh.solve(prm32)
+    J32, gf32, gk32 = mesh.adjoint_l2(in_S, params=prm32)
+    assert J64 > 0 and abs(J32 - J64) <= 1e-8 * J64, (J32, J64)
+    assert np.abs(gf32 - gf64).max() <= 1e-8 * np.abs(gf64).max()
+    assert np.abs(gk32 - gk64).max() <= 1e-8 * np.abs(gk64).max()
+    # weight of each interface copy: 1 / (number of copies of its node)
+    key = np.round(x * 2 ** (L + 3)).astype(np.int64) + 4096
+    key = key[:, 0] | (key[:, 1] << 16) | (key[:, 2] << 32)
+    _, inv, cnt = np.unique(key, return_inverse=True, return_counts=True)
+    w = 1.0 / cnt[inv.ravel()]
+    assert abs(np.sum(w * f0 * gf32) - 2 * J32) <= 1e-8 * J32
+    assert abs(np.sum(k * gk32) + 2 * J32) <= 1e-8 * J32
+    mesh.close()
