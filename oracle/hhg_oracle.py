@@ -77,6 +77,8 @@ _PAD = np.int64(1 << 40)
 
 def _red_children_2d():
     # vertices 0,1,2 ; midpoints 3=(0,1) 4=(1,2) 5=(2,0)
+    """Red refinement of a triangle (Sec. 2): its three edges and four children, as indices into
+    [vertices 0..2, edge midpoints 3..5]."""
     edges = [(0, 1), (1, 2), (2, 0)]
     children = [(0, 3, 5), (3, 1, 4), (5, 4, 2), (4, 5, 3)]
     return edges, children
@@ -85,6 +87,8 @@ def _red_children_2d():
 def _bey_children_3d():
     # vertices 0..3 ; midpoints 4=(0,1) 5=(0,2) 6=(0,3) 7=(1,2) 8=(1,3) 9=(2,3)
     # Bey's rule: four corner tets and the interior octahedron cut along x02-x13.
+    """Bey's rule for a tetrahedron (Sec. 2): its six edges and eight children (four corner tets and
+    the inner octahedron cut along the x02-x13 diagonal), as indices into [vertices, midpoints]."""
     edges = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
     children = [
         (0, 4, 5, 6), (4, 1, 7, 8), (5, 7, 2, 9), (6, 8, 9, 3),
@@ -94,7 +98,7 @@ def _bey_children_3d():
 
 
 def _refine_weights(W, dim):
-    """One uniform refinement of micro elements given by integer weight vectors.
+    """One uniform refinement of micro elements given by integer weight vectors (Sec. 2).
 
     W has shape (nE, d+1, d+1): W[e, a] is the weight vector of vertex a of element e
     over the d+1 vertices of its macro element (weights sum to 2^l).  Returns the
@@ -116,7 +120,8 @@ def _refine_weights(W, dim):
 # --------------------------------------------------------------------------------------
 
 def _canonical_keys(wts, macro, cells):
-    """Canonical key rows for points with integer weights `wts` (N, d+1) over macro `macro`.
+    """Canonical key rows for points with integer weights `wts` (N, d+1) over macro `macro`, so that
+    nodes on shared macro primitives coincide (Sec. 2).
 
     Key = (global vertex id, weight) pairs with nonzero weight, sorted by global id,
     padded with (_PAD, 0).  Shape (N, 2(d+1)) int64.
@@ -138,7 +143,7 @@ def _canonical_keys(wts, macro, cells):
 # --------------------------------------------------------------------------------------
 
 def _element_matrices(X):
-    """P1 stiffness (unit coefficient) and mass matrices for simplices X (nE, d+1, d).
+    """P1 stiffness (unit coefficient) and mass matrices of Eq. 5.1 for simplices X (nE, d+1, d).
 
     Stiffness K_ab = |E| grad(phi_a) . grad(phi_b); mass M_ab = |E| (1 + delta_ab) / ((d+1)(d+2)).
     """
@@ -157,6 +162,8 @@ def _element_matrices(X):
 
 
 def _assemble(elems, Ke, n):
+    """Sparse global matrix summed element by element from element matrices (the assembly of the
+    P1 system A_l u_l = b_l, Eq. 4.15)."""
     dp1 = elems.shape[1]
     rows = np.repeat(elems, dp1, axis=1).ravel()
     cols = np.tile(elems, (1, dp1)).ravel()
@@ -168,7 +175,8 @@ def _assemble(elems, Ke, n):
 # --------------------------------------------------------------------------------------
 
 def _faces_of(cells, dim):
-    """Facets (sorted vertex tuples) of each cell: edges in 2D, triangles in 3D."""
+    """Facets (sorted vertex tuples) of each cell, the macro primitives of Sec. 2: edges in 2D,
+    triangles in 3D."""
     from itertools import combinations
     out = []
     for c in cells:
@@ -178,6 +186,8 @@ def _faces_of(cells, dim):
 
 @dataclass
 class Level:
+    """One level T_l of the HHG (Sec. 2): nodes, micro elements, the assembled A_l and M_l (Eq. 4.15),
+    Dirichlet flags, the smoother's stages (Alg. 4) and the interpolation P from level l-1 (Sec. 4.4)."""
     l: int
     keys: np.ndarray          # (N, 2(d+1)) canonical node keys
     x: np.ndarray             # (N, d) coordinates
@@ -239,6 +249,8 @@ class Hierarchy:
 
     # ---- topology and boundary (Sec. 2: macro primitives) ----
     def _topology(self, dirichlet):
+        """Boundary macro primitives of T_0 (Sec. 2: vertices, edges, faces) and the Dirichlet flag of
+        each macro vertex (every boundary vertex unless flags are given)."""
         d = self.dim
         facets = _faces_of(self.cells, d)
         count = {}
@@ -264,6 +276,8 @@ class Hierarchy:
         self.cell_of_vertex_set = {tuple(sorted(int(v) for v in c)): t for t, c in enumerate(self.cells)}
 
     def _node_dirichlet(self, keys):
+        """A node is a Dirichlet node when it lies on a boundary macro primitive whose vertices are all
+        Dirichlet (the boundary of the HHG primitives, Sec. 2)."""
         d = self.dim
         g = keys[:, 0::2]
         s = (g != _PAD).sum(axis=1)
@@ -279,6 +293,8 @@ class Hierarchy:
         return out
 
     def _build_level(self, l, W, macro):
+        """Level l (Sec. 2): nodes de-duplicated through their canonical keys, coordinates, element
+        matrices with k_T (Eq. 5.1) and the assembled A_l, M_l of Eq. 4.15."""
         d = self.dim
         nE = W.shape[0]
         flat_w = W.reshape(nE * (d + 1), d + 1)
@@ -333,7 +349,7 @@ class Hierarchy:
 
     # ---- smoother stage ordering (reading of "Gauss-Seidel", Sec. 5) ----
     def _colouring(self):
-        """Per macro (alpha_T, m_T) for the macro-cell interior colours.
+        """Per macro (alpha_T, m_T) for the macro-cell interior colours (smoother reading of Alg. 4).
 
         Decided from the interior couplings of macro T on level 2 (the interior stencil is
         the same on every level): m=2 with the first alpha in a fixed candidate list for
@@ -376,7 +392,8 @@ class Hierarchy:
             self.alpha[t], self.mcol[t] = chosen
 
     def _local_p(self, key, t):
-        """Lattice coordinates of a node (given by key) in macro t: weights on cells[t][1..d]."""
+        """Lattice coordinates (Sec. 2) of a node, given by key, in macro t: its weights on
+        cells[t][1..d]."""
         g = key[0::2]
         w = key[1::2]
         p = np.zeros(self.dim, dtype=np.int64)
@@ -386,7 +403,7 @@ class Hierarchy:
         return p
 
     def _local_coords(self, keys):
-        """For macro-cell interior nodes: (macro id, lattice coords); -1 elsewhere."""
+        """For macro-cell interior nodes: (macro id, lattice coordinates of Sec. 2); -1 elsewhere."""
         d = self.dim
         g = keys[:, 0::2]
         w = keys[:, 1::2]
@@ -406,6 +423,8 @@ class Hierarchy:
         return macro, p
 
     def _stages(self, lev):
+        """The ordered stage list of one Gauss-Seidel sweep on this level (the smoother of Alg. 4, in the
+        reading stated in the module docstring), with each stage's rows and diagonal."""
         d = self.dim
         keys = lev.keys
         g = keys[:, 0::2]
@@ -454,7 +473,8 @@ class Hierarchy:
 
 
 def _row_hash(keys):
-    """64-bit hash of each key row (collisions are checked by the callers)."""
+    """64-bit hash of each key row for the node de-duplication of Sec. 2 (collisions are checked by
+    the callers)."""
     h = np.full(len(keys), np.uint64(1469598103934665603))
     with np.errstate(over="ignore"):
         for c in range(keys.shape[1]):
@@ -464,7 +484,8 @@ def _row_hash(keys):
 
 
 def _unique_rows(keys):
-    """Unique key rows (ordered by hash) and the inverse map; exact (hash collisions rejected)."""
+    """Unique key rows (ordered by hash) and the inverse map, for the node de-duplication of Sec. 2;
+    exact (hash collisions rejected)."""
     h = _row_hash(keys)
     uh, first, inv = np.unique(h, return_index=True, return_inverse=True)
     uniq = keys[first]
@@ -474,7 +495,8 @@ def _unique_rows(keys):
 
 
 def _lookup(keys_unique, q):
-    """Row indices of the rows of q inside `keys_unique` (as produced by _unique_rows)."""
+    """Row indices of the rows of q inside `keys_unique` (as produced by _unique_rows; node
+    de-duplication, Sec. 2)."""
     hk = _row_hash(keys_unique)
     order = np.argsort(hk)
     pos = np.searchsorted(hk[order], _row_hash(q))
@@ -490,7 +512,8 @@ def _lookup(keys_unique, q):
 # --------------------------------------------------------------------------------------
 
 def inject_from_finest(h: Hierarchy, vL: np.ndarray, l: int) -> np.ndarray:
-    """Values at level-l nodes taken from a level-L nodal vector (nested nodes: key * 2^(L-l))."""
+    """Values at level-l nodes taken from a level-L nodal vector (the nodes are nested, Sec. 2:
+    key * 2^(L-l))."""
     if l == h.L:
         return np.asarray(vL, dtype=np.float64).copy()
     keys = h.levels[l].keys.copy()
@@ -499,14 +522,16 @@ def inject_from_finest(h: Hierarchy, vL: np.ndarray, l: int) -> np.ndarray:
 
 
 def nodal(h: Hierarchy, fn, l: int) -> np.ndarray:
-    """A nodal vector on level l from a callable of x (N, d) or a level-L nodal array."""
+    """A nodal vector on level l (f_l or g_l of Sec. 4.4) from a callable of x (N, d) or a level-L
+    nodal array."""
     if callable(fn):
         return np.asarray(fn(h.levels[l].x), dtype=np.float64)
     return inject_from_finest(h, fn, l)
 
 
 class Problem:
-    """b_l = M_l f_l and Dirichlet values g_l for every level of a hierarchy."""
+    """b_l = M_l f_l (the right-hand side of Eq. 4.15, Sec. 4.4) and Dirichlet values g_l for every
+    level of a hierarchy."""
 
     def __init__(self, h: Hierarchy, f, g):
         self.h = h
@@ -524,7 +549,7 @@ class Problem:
 # --------------------------------------------------------------------------------------
 
 def smooth(lev: Level, u: np.ndarray, rhs: np.ndarray) -> None:
-    """One Gauss-Seidel sweep as the ordered stage list; Jacobi inside a stage (in place).
+    """One Gauss-Seidel sweep of Alg. 4 as the ordered stage list; Jacobi inside a stage (in place).
 
     3D face block: the three face colours update each macro face's nodes by Gauss-Seidel over the
     face (its own nodes at their current values), with every node outside the face taken at its
@@ -545,14 +570,15 @@ def smooth(lev: Level, u: np.ndarray, rhs: np.ndarray) -> None:
 
 
 def residual(lev: Level, u: np.ndarray, rhs: np.ndarray) -> np.ndarray:
-    """r = rhs - A u on free nodes, zero on Dirichlet nodes."""
+    """r = rhs - A u on free nodes, zero on Dirichlet nodes (V-cycle of Alg. 4)."""
     r = rhs - lev.A @ u
     r[lev.dirichlet] = 0.0
     return r
 
 
 def coarse_solve(prob: Problem, u: np.ndarray, rhs: np.ndarray) -> None:
-    """u <- u + A_ff^{-1} (rhs - A u)_f on level 0 (exact; the converged limit of CG)."""
+    """u <- u + A_ff^{-1} (rhs - A u)_f on level 0 (Alg. 4): exact, the converged limit of the CG that
+    Sec. 5.4 runs."""
     lev0 = prob.h.levels[0]
     F = prob.coarse_free
     if len(F) == 0:
@@ -562,7 +588,7 @@ def coarse_solve(prob: Problem, u: np.ndarray, rhs: np.ndarray) -> None:
 
 
 def vcycle(prob: Problem, l: int, u: np.ndarray, rhs: np.ndarray, pre: int = 2, post: int = 1) -> None:
-    """One V(pre, post)-cycle on level l for A_l u = rhs (in place)."""
+    """One V(pre, post)-cycle on level l for A_l u = rhs (in place) (Alg. 4)."""
     h = prob.h
     if l == 0:
         coarse_solve(prob, u, rhs)
@@ -609,7 +635,8 @@ def fmg(prob: Problem, nu: int = 2, pre: int = 2, post: int = 1, n_extra: int = 
 # --------------------------------------------------------------------------------------
 
 def local_mass_sq(lev: Level, e: np.ndarray, n_cells: int) -> np.ndarray:
-    """Per macro T: e^T M_{l,T} e, summing the element mass forms of micro elements inside T."""
+    """Per macro T: e^T M_{l,T} e, summing the element mass forms of the micro elements inside T (the
+    local indicator of Eq. 4.14)."""
     ee = e[lev.elems]
     per_elem = np.einsum("ea,eab,eb->e", ee, lev.Me, ee)
     return np.bincount(lev.emacro, weights=per_elem, minlength=n_cells)
@@ -625,7 +652,7 @@ def local_energy_sq(lev: Level, e: np.ndarray, n_cells: int) -> np.ndarray:
 
 
 def prolong_to_finest(h: Hierarchy, v: np.ndarray, l: int) -> np.ndarray:
-    """I_l^L v for a level-l nodal vector."""
+    """I_l^L v for a level-l nodal vector (interpolation, Sec. 4.4)."""
     for m in range(l + 1, h.L + 1):
         v = h.levels[m].P @ v
     return v
@@ -675,7 +702,8 @@ def estimate(h: Hierarchy, u_L: np.ndarray, ws, j: int = 1, norm: str = "l2", we
 
 
 def l2_error_sq(h: Hierarchy, u_L: np.ndarray, u_exact) -> float:
-    """||I u - u_L||_M^2 on level L (nodal interpolant of the exact solution)."""
+    """||I u - u_L||_M^2 on level L with the nodal interpolant of the exact solution (the error
+    measure of Sec. 5)."""
     lev = h.levels[h.L]
     e = u_exact(lev.x) - u_L
     return float(e @ (lev.M @ e))
@@ -710,8 +738,8 @@ def corollary_dgamma_bounds(theta_min: float, theta_max: float, j: int, eps: flo
 # --------------------------------------------------------------------------------------
 
 def mark_top_fraction(eta: np.ndarray, fraction: float) -> np.ndarray:
-    """Boolean mask: n = max(1, ceil(fraction * N - 1e-9)); eta* = n-th largest value
-    (ties ordered by index); mark every T with eta_T >= (1 - 1e-8) eta*."""
+    """Marking of Sec. 5.1 as a boolean mask: n = max(1, ceil(fraction * N - 1e-9)); eta* = n-th
+    largest value (ties ordered by index); mark every T with eta_T >= (1 - 1e-8) eta*."""
     eta = np.asarray(eta, dtype=np.float64)
     N = len(eta)
     if N == 0:
@@ -751,10 +779,12 @@ class RG2D:
         self.mid = {}
 
     def mesh(self):
+        """The current conforming mesh (coords, cells) of the red-green refinement (Sec. 3)."""
         return (np.array(self.coords, dtype=np.float64),
                 np.array([t[:3] for t in self.tris], dtype=np.int32).reshape(-1, 3))
 
     def _midpoint(self, a, b, create):
+        """Midpoint vertex of edge (a, b), created on request in creation order (Sec. 3)."""
         key = (min(a, b), max(a, b))
         m = self.mid.get(key)
         if m is None and create:
@@ -765,6 +795,7 @@ class RG2D:
         return m
 
     def _red(self, t):
+        """Red refinement of one triangle into four through its edge midpoints (Sec. 3)."""
         v0, v1, v2 = t
         m01 = self._midpoint(v0, v1, True)
         m12 = self._midpoint(v1, v2, True)
@@ -772,6 +803,8 @@ class RG2D:
         return [(v0, m01, m20), (m01, v1, m12), (m20, m12, v2), (m12, m20, m01)]
 
     def _split_info(self, t):
+        """Split edges of a triangle and whether a split edge's half is split again (the closure
+        condition of step 2, Sec. 3)."""
         v = t
         split = []
         over = False
@@ -785,6 +818,7 @@ class RG2D:
         return split, over
 
     def refine(self, marked):
+        """One red-green step on the current mesh (Sec. 3): steps 1-3 of the class docstring."""
         marked = np.asarray(marked).astype(bool)
         if len(marked) != len(self.tris):
             raise ValueError("one flag per current cell")
@@ -867,10 +901,12 @@ class RG3D:
         self.mid = {}
 
     def mesh(self):
+        """The current conforming mesh (coords, cells) of the 3D red-green refinement (Alg. 3)."""
         return (np.array(self.coords, dtype=np.float64),
                 np.array([t[0] for t in self.tets], dtype=np.int32).reshape(-1, 4))
 
     def _midpoint(self, a, b, create):
+        """Midpoint vertex of edge (a, b), created on request in creation order (Alg. 3)."""
         key = (min(a, b), max(a, b))
         m = self.mid.get(key)
         if m is None and create:
@@ -881,6 +917,7 @@ class RG3D:
         return m
 
     def _red(self, t):
+        """Red refinement of one tet by Bey's rule with orientation-keeping children (Alg. 3, Sec. 2)."""
         x = {}
         for a, b in _TET_EDGES:
             x[(a, b)] = self._midpoint(t[a], t[b], True)
@@ -890,9 +927,12 @@ class RG3D:
                 (x01, x02, x03, x13), (x02, x01, x12, x13), (x02, x03, x13, x23), (x12, x02, x13, x23)]
 
     def _split_edges(self, t):
+        """Indices (edge order 01, 02, 03, 12, 13, 23) of a tet's split edges (Alg. 3)."""
         return [e for e, (a, b) in enumerate(_TET_EDGES) if self._midpoint(t[a], t[b], False) is not None]
 
     def _over(self, t):
+        """True when a split edge's half is split again, or a fully split face has a split midline
+        (the red conditions of Alg. 3 beyond the count of split edges)."""
         for a, b in _TET_EDGES:
             m = self._midpoint(t[a], t[b], False)
             if m is not None and (self._midpoint(t[a], m, False) is not None or
@@ -908,6 +948,8 @@ class RG3D:
         return False
 
     def _close_faces(self, tets):
+        """Split the third edge of every face with exactly two split edges until none is left (the face
+        rule of Alg. 3)."""
         changed = True
         while changed:
             changed = False
@@ -921,6 +963,8 @@ class RG3D:
                         changed = True
 
     def _green(self, t, split):
+        """Children of a tet with one split edge, two opposite split edges, or the three split edges of
+        one face (the three green types of Alg. 3), by slot substitution."""
         def sub(tt, slot, v):
             tt = list(tt)
             tt[slot] = v
@@ -950,6 +994,7 @@ class RG3D:
         raise AssertionError("split pattern is not a green type")
 
     def refine(self, marked):
+        """One red-green step on the current mesh (Alg. 3): steps 1-3 of the class docstring."""
         marked = np.asarray(marked).astype(bool)
         if len(marked) != len(self.tets):
             raise ValueError("one flag per current cell")
@@ -996,7 +1041,8 @@ class RG3D:
 # --------------------------------------------------------------------------------------
 
 def exact_solve(prob: Problem) -> np.ndarray:
-    """Exact discrete solution u_L of A_L u = b_L with Dirichlet values g_L (sparse LU)."""
+    """Exact discrete solution u_L of A_L u = b_L (Eq. 4.15) with Dirichlet values g_L, by sparse LU
+    (the pins' reference)."""
     import scipy.sparse.linalg as spla
     h = prob.h
     lev = h.levels[h.L]
@@ -1010,7 +1056,8 @@ def exact_solve(prob: Problem) -> np.ndarray:
 
 
 def adjoint_gradients(h: Hierarchy, u_L: np.ndarray, in_S: np.ndarray):
-    """J = sum_{T in S} u^T M_{L,T} u and its gradients w.r.t. nodal f and per-macro k_T.
+    """J = sum_{T in S} u^T M_{L,T} u and its gradients w.r.t. nodal f and per-macro k_T (no
+    counterpart in the paper).
 
     Solves A_ff lam_f = 2 (M_S u)_f (lam = 0 on Dirichlet nodes) exactly, then
       dJ/df = M_L lam          (b_L = M_L f_L),
