@@ -108,10 +108,15 @@ typedef struct {
 hhg_status hhg_mesh_create(int dim, int n_verts, const double* coords, int n_cells, const int* cells,
                            const unsigned char* vert_is_dirichlet, int L, void* cuda_stream,
                            hhg_mesh* out);
+/* Release the hierarchy and every device buffer it owns (no counterpart in the paper: object
+ * lifetime).  NULL is accepted. */
 hhg_status hhg_mesh_destroy(hhg_mesh mesh);
+/* Sizes of the hierarchy (Sec. 2): dimension, L, macro cells and vertices, nodes per level in the
+ * layout above, free distinct level-L nodes (the DoF count), device bytes, interior colours. */
 hhg_status hhg_mesh_get_info(hhg_mesh mesh, hhg_mesh_info* info);
 
-/* Coordinates of the level-l nodes in the layout above (x = x_0 + J p / 2^l per cell).
+/* Coordinates of the level-l nodes of the uniformly refined macro cells (Sec. 2) in the layout
+ * above (x = x_0 + J p / 2^l per cell).
  * xyz: host or device, N_l*dim doubles, node-major.  Device memory of the mesh's device is written
  * by one kernel on the mesh's stream (the call returns after it completes); any other pointer is
  * filled from host threads in batches of cells.  Both paths round every product and sum
@@ -122,7 +127,8 @@ hhg_status hhg_level_coords(hhg_mesh mesh, int level, double* xyz);
 /* Piecewise-constant coefficient k_T > 0 per macro cell (Eq. 5.1 with k); NULL = 1. */
 hhg_status hhg_set_coefficient(hhg_mesh mesh, const double* k_per_cell);
 
-/* Source f and Dirichlet data g at the level-L nodes (host or device, N_L each).  Copied. */
+/* Source f and Dirichlet data g of Eq. 5.1 at the level-L nodes (host or device, N_L each, one
+ * value per interface copy, equal copies).  Copied on the mesh's stream. */
 hhg_status hhg_set_data(hhg_mesh mesh, const double* f_L, const double* g_L);
 
 /* FMG solve (Alg. 4): b_l = M_l f_l on every level, FMG with the given parameters, w_l kept
@@ -148,13 +154,14 @@ hhg_status hhg_estimate(hhg_mesh mesh, int j, double* eta_T, double* eta_jT, hhg
 hhg_status hhg_estimate_norm(hhg_mesh mesh, int j, int norm, const double* cell_weights, double* eta_T,
                              double* eta_jT, hhg_estimate_out* out);
 
-/* Read an internal level vector of the last solve into `out` (host or device, N_l doubles):
+/* Read an internal level vector of the last solve (Alg. 4) into `out` (host or device, N_l doubles):
  * which = 0: u_l after its FMG V-cycles (l = L: the solution, l < L: overwritten by later
  * corrections, so only l = L is meaningful after the solve), 1: w_l (l = 0..L-1, stored on
  * level l+1, N_{l+1} doubles), 2: b_l summed over interface copies (N_l). */
 hhg_status hhg_get_vector(hhg_mesh mesh, int which, int level, double* out);
 
-/* Operator application for testing: out = Op_l in on level l with in/out of N_l doubles
+/* Operator application for testing (the operators of Eq. 4.15 and Sec. 4.4, and the smoother of
+ * Alg. 4): out = Op_l in on level l with in/out of N_l doubles
  * (host or device), interface rows summed over adjacent cells.
  * op = 0: stiffness A_l (all rows, Dirichlet rows included as plain P1 rows),
  * op = 1: mass M_l, op = 2: interpolation from level l-1 (in has N_{l-1} entries),
@@ -174,11 +181,13 @@ hhg_status hhg_mark(int n, const double* eta, double fraction, unsigned char* ma
  * cells: host, n_cells*3, 0-based.  Errors: HHG_ERR_ARG (sizes, vertex ids), HHG_ERR_MESH (a cell
  * with a repeated vertex or zero area), HHG_ERR_OOM. */
 hhg_status hhg_rg2d_create(int n_verts, const double* coords, int n_cells, const int* cells, hhg_rg2d* out);
+/* One red-green step (Sec. 3) on the current mesh with the given marks. */
 hhg_status hhg_rg2d_refine(hhg_rg2d rg, const unsigned char* marked /* host, one flag per current cell */);
-/* Current conforming mesh; pass NULL arrays to query the sizes first. */
+/* Current conforming mesh (Sec. 3); pass NULL arrays to query the sizes first. */
 hhg_status hhg_rg2d_mesh(hhg_rg2d rg, int* n_verts, double* coords, int* n_cells, int* cells);
 hhg_status hhg_rg2d_destroy(hhg_rg2d rg);
-/* Marking + one red-green step: marked (host, n_cells of the current mesh, may be NULL). */
+/* Marking (Sec. 5.1, as hhg_mark) + one red-green step (Sec. 3): marked (host, n_cells of the
+ * current mesh, may be NULL). */
 hhg_status hhg_mark_refine(hhg_rg2d rg, const double* eta_T, double fraction, unsigned char* marked);
 
 /* 3D red-green refinement of a tetrahedral macro mesh (Alg. 3, Sec. 3), the k-step of the 3D
@@ -194,8 +203,9 @@ hhg_status hhg_mark_refine(hhg_rg2d rg, const double* eta_T, double fraction, un
  * HHG_ERR_MESH (a cell with a repeated vertex or zero volume), HHG_ERR_STATE (corrupt state),
  * HHG_ERR_OOM. */
 hhg_status hhg_rg3d_create(int n_verts, const double* coords, int n_cells, const int* cells, hhg_rg3d* out);
+/* One 3D red-green step (Alg. 3) on the current mesh with the given marks. */
 hhg_status hhg_rg3d_refine(hhg_rg3d rg, const unsigned char* marked /* host, one flag per current cell */);
-/* Current conforming mesh; pass NULL arrays to query the sizes first. */
+/* Current conforming mesh (Alg. 3); pass NULL arrays to query the sizes first. */
 hhg_status hhg_rg3d_mesh(hhg_rg3d rg, int* n_verts, double* coords, int* n_cells, int* cells);
 hhg_status hhg_rg3d_destroy(hhg_rg3d rg);
 /* Marking (hhg_mark) + one 3D red-green step: marked (host, n_cells of the current mesh, may be NULL). */
@@ -214,11 +224,12 @@ hhg_status hhg_rg3d_mark_refine(hhg_rg3d rg, const double* eta_T, double fractio
 hhg_status hhg_adjoint_l2(hhg_mesh mesh, const hhg_solve_params* params, const unsigned char* in_S,
                           double* J, double* grad_f, double* grad_k);
 
-/* Host self-check of the lattice index arithmetic against brute force (no GPU needed).
+/* Host self-check of the lattice index arithmetic (the structured level-l lattice of a macro cell,
+ * Sec. 2) against brute force (no GPU needed).
  * Returns 0 if consistent, otherwise the number of mismatches. */
 int hhg_lattice_selfcheck(int dim, int n);
 
-/* Profiling support.  Enqueue `reps` launches of one kernel of the solve on the mesh's stream,
+/* Profiling support (no counterpart in the paper).  Enqueue `reps` launches of one kernel of the solve on the mesh's stream,
  * exactly as the solve launches it, without synchronising (bracket it with events on that stream).
  * kernel 0: macro-interior smoothing stage of colour 0 on level L for the first cell group;
  * kernel 1 (3D, binary64): the level-L macro-face stage of colour 0 (units only; bytes = flops = 0);
@@ -233,7 +244,8 @@ int hhg_lattice_selfcheck(int dim, int n);
 hhg_status hhg_profile_kernel(hhg_mesh mesh, int kernel, int precision, int reps, long long* units,
                               double* bytes, double* flops);
 
-/* Number of kernel nodes in the captured graph of a solve with these parameters (after a first
+/* Measurement support (no counterpart in the paper).  Number of kernel nodes in the captured graph
+ * of a solve (Alg. 4) with these parameters (after a first
  * hhg_fmg_solve with the same parameters), i.e. kernel launches per solve. */
 hhg_status hhg_solve_launch_count(hhg_mesh mesh, const hhg_solve_params* params, long long* n_kernels);
 
@@ -254,10 +266,12 @@ hhg_status hhg_solve_launch_count(hhg_mesh mesh, const hhg_solve_params* params,
  * current. */
 hhg_status hhg_cell_mass_norms_noalloc(hhg_mesh mesh, const double* a, const double* b, double* out);
 
-/* Debug builds (compiled with HHG_CHECK): first recorded out-of-range index of a kernel
+/* Debug builds (compiled with HHG_CHECK; no counterpart in the paper): first recorded out-of-range
+ * index of a kernel
  * (code, block x, block y, thread, index, bound, 0, 1), then cleared; all zeros otherwise. */
 hhg_status hhg_debug_check(long long* out8);
 
+/* Message of the last failing call on this thread (no counterpart in the paper). */
 const char* hhg_last_error(void);
 
 #ifdef __cplusplus
