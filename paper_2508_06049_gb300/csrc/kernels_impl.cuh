@@ -89,7 +89,7 @@ __device__ __forceinline__ int64_t copy_terms(const R* __restrict__ S, const uin
   return g;
 }
 
-// ---------------------------------------------------------------- right-hand sides (row 2)
+// ---------------------------------------------------------------- right-hand sides b_l = M_l f_l (Eq. 4.15, Sec. 4.4)
 
 // b_l = M_l f_l (partial per cell), f_l injected from the level-L data; zero on Dirichlet rows
 template <int DIM>
@@ -154,7 +154,7 @@ __global__ void k_init_coarse(LevelCtx lc, int nL, int64_t NtL, int shift, const
   u[(int64_t)T * lc.Nt + loc] = v;
 }
 
-// ---------------------------------------------------------------- smoother stages (row 3)
+// ---------------------------------------------------------------- smoother stages (Gauss-Seidel of Alg. 4)
 
 // Macro-cell interior nodes of one colour: race free (no coupling inside a colour).  The update
 // u_i <- u_i + (b_i - (A u)_i) / a_ii is evaluated in the equivalent form
@@ -558,7 +558,7 @@ void launch_iface(int lanes, int nprim, const int* ptr, const int* cell, const i
 #undef HHG_IFACE_G
 }
 
-// ---------------------------------------------------------------- face block (3D, row 3)
+// ---------------------------------------------------------------- face block (3D; Gauss-Seidel of Alg. 4)
 //
 // The three face colours form one block: every macro face is smoothed on its own, Gauss-Seidel over
 // its interior nodes in colour order (a + 2b) mod 3, with every node outside the face (edges,
@@ -814,7 +814,7 @@ void launch_face_block(const Prims& P, const LevelData& Lv, LevelCtx lc, const R
              P.d_loc, P.d_dir, lc, W, pinv, (R)1 / ss, u, (const R*)E, fits ? (R*)nullptr : work);
 }
 
-// ---------------------------------------------------------------- residual, restriction (row 4)
+// ---------------------------------------------------------------- residual, restriction (V-cycle of Alg. 4; transfers of Sec. 4.4)
 
 // list segments of k_residual_list for one group on one level: directly after a sweep the last
 // interior colour's entries are zeroed instead of computed
@@ -960,7 +960,7 @@ __global__ void k_restrict(LevelCtx fc, LevelCtx cc, const uint16_t* __restrict_
   rcv[(int64_t)T * cc.Nt + loc] = (O)((R)rf[gf] + (R)0.5 * acc);
 }
 
-// ---------------------------------------------------------------- prolongation (rows 6, 7)
+// ---------------------------------------------------------------- prolongation, FMG transition (Alg. 4; interpolation of Sec. 4.4)
 
 template <int DIM, typename R, typename C>
 __device__ __forceinline__ R interp(LevelCtx cc, int T, int i, int j, int k, const C& uc) {
@@ -1033,7 +1033,7 @@ __global__ void k_prolong(LevelCtx fc, LevelCtx cc, const double* __restrict__ v
   vf[g] = minuend ? minuend[g] - v : v;
 }
 
-// ---------------------------------------------------------------- direct coarse solve (row 5)
+// ---------------------------------------------------------------- direct coarse solve (Alg. 4; the converged limit of Sec. 5.4's CG)
 
 // One CTA: residual of the free macro vertices (summed over cell copies), c = A_ff^{-1} r, update
 // every copy.  n0f <= 16384 (checked at set-up); the residual vector lives in shared memory.
@@ -1084,7 +1084,7 @@ __global__ void __launch_bounds__(1024) k_coarse(int n0f, const int* __restrict_
   }
 }
 
-// ---------------------------------------------------------------- reductions (row 8, row 11)
+// ---------------------------------------------------------------- reductions (ErrorEstimate of Alg. 4, Eqs. 4.5 and 4.14; adjoint gradients)
 
 // Per node p of a cell's closure (one node per thread, one grid row per cell), the symmetric-form
 // contribution (written to part[cell][node]):

@@ -1,5 +1,7 @@
-// Host-side construction of an HHG mesh object: coarse topology, per-cell partial stencils,
-// interface descriptors, interior colourings, the direct coarse solve and the level tables.
+// Host-side construction of an HHG mesh object: coarse topology (the macro primitives of Sec. 2),
+// per-cell partial stencils of the P1 discretisation of Eq. 5.1 (the constant stencils of one
+// uniformly refined macro element, Sec. 2), interface descriptors, interior colourings (the
+// Gauss-Seidel stages of Alg. 4), the direct coarse solve of Alg. 4 and the level tables.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
