@@ -30,6 +30,12 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# The oracle's timings report one host core: BLAS stays single-threaded in this process.  This is
+# set before numpy is first imported, since BLAS reads it only when it loads; the GPU arms time no
+# host BLAS work.
+for _var in ("OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_var, "1")
+
 # Equal error (Sec. 5 protocol): extra level-L cycles until the L2 error is stable.  On the 384-tet
 # cube at L = 6 the converged error is 2.251e-5; binary64 FMG + 4 extra V-cycles gives 2.260e-5,
 # binary32 FMG + 2 refinement steps of 2 binary32 V-cycles gives 2.261e-5 (both within 0.5 %).
