@@ -175,47 +175,6 @@ def test_binary16_storage_needs_a_free_macro_vertex(P):
     mesh.close()
 
 
-def test_binary16_storage_equal_error_on_full_size_cube3072(P):
-    """3072-tet cube at its full size, L = 7 (1.07e9 unknowns, k_T over four decades): the mixed
-    solve with binary16 correction storage reaches the discretisation error to two digits
-    (algebraic error <= 1 % of eta_1 against a converged binary64 reference), the criterion the
-    bfloat16 arm meets in the full-size tests."""
-    import torch
-    co, ce, L, f, g, k, _ = W.workload("cube3072_l7")
-    mesh = P.Mesh(co, ce, L)
-    mesh.set_coefficient(k)
-    N = mesh.n_nodes(L)
-    dev = torch.device("cuda:0")
-    fd = torch.ones(N, dtype=torch.float64, device=dev)
-    gd = torch.zeros(N, dtype=torch.float64, device=dev)
-    mesh.set_data(fd, gd)
-    del fd, gd
-    cells = torch.empty(len(ce), dtype=torch.float64, device=dev)
-    ref = torch.empty(N, dtype=torch.float64, device=dev)
-    u = torch.empty(N, dtype=torch.float64, device=dev)
-    mesh.solve(P.solve_params(n_extra=100), out=ref)
-    torch.cuda.synchronize()
-    eta = mesh.estimate(1)["eta_j"]
-
-    def err_of(params):
-        mesh.solve(params, out=u)
-        mesh.cell_mass_norms_noalloc(u, ref, cells)
-        torch.cuda.synchronize()
-        return math.sqrt(float(cells.sum().item()))
-
-    ok = None
-    for steps in (16, 24, 32, 48):
-        err = err_of(P.solve_params(precision=1, storage=2, ir_steps=steps, ir_vcycles=2))
-        assert math.isfinite(err)
-        if err <= 0.01 * eta:
-            ok = steps
-            break
-    assert ok is not None, (err, eta)
-    print("cube3072_l7: binary16 storage reaches equal error after %d refinement steps" % ok)
-    del ref, u, cells
-    mesh.close()
-
-
 # ---- mixed-precision adjoint ------------------------------------------------------------------
 # hhg_adjoint_l2 with precision = 1: binary64 refinement from lam = 0 with binary32 V-cycles (no
 # binary32 FMG step: the adjoint right-hand side is given on level L only).  Refinement converges to
@@ -297,4 +256,45 @@ def test_mixed_adjoint_full_size_fichera336_l6(P):
     w = 1.0 / cnt[inv.ravel()]
     assert abs(np.sum(w * f0 * gf32) - 2 * J32) <= 1e-8 * J32
     assert abs(np.sum(k * gk32) + 2 * J32) <= 1e-8 * J32
+    mesh.close()
+
+
+def test_binary16_storage_equal_error_on_full_size_cube3072(P):
+    """3072-tet cube at its full size, L = 7 (1.07e9 unknowns, k_T over four decades): the mixed
+    solve with binary16 correction storage reaches the discretisation error to two digits
+    (algebraic error <= 1 % of eta_1 against a converged binary64 reference), the criterion the
+    bfloat16 arm meets in the full-size tests."""
+    import torch
+    co, ce, L, f, g, k, _ = W.workload("cube3072_l7")
+    mesh = P.Mesh(co, ce, L)
+    mesh.set_coefficient(k)
+    N = mesh.n_nodes(L)
+    dev = torch.device("cuda:0")
+    fd = torch.ones(N, dtype=torch.float64, device=dev)
+    gd = torch.zeros(N, dtype=torch.float64, device=dev)
+    mesh.set_data(fd, gd)
+    del fd, gd
+    cells = torch.empty(len(ce), dtype=torch.float64, device=dev)
+    ref = torch.empty(N, dtype=torch.float64, device=dev)
+    u = torch.empty(N, dtype=torch.float64, device=dev)
+    mesh.solve(P.solve_params(n_extra=100), out=ref)
+    torch.cuda.synchronize()
+    eta = mesh.estimate(1)["eta_j"]
+
+    def err_of(params):
+        mesh.solve(params, out=u)
+        mesh.cell_mass_norms_noalloc(u, ref, cells)
+        torch.cuda.synchronize()
+        return math.sqrt(float(cells.sum().item()))
+
+    ok = None
+    for steps in (16, 24, 32, 48):
+        err = err_of(P.solve_params(precision=1, storage=2, ir_steps=steps, ir_vcycles=2))
+        assert math.isfinite(err)
+        if err <= 0.01 * eta:
+            ok = steps
+            break
+    assert ok is not None, (err, eta)
+    print("cube3072_l7: binary16 storage reaches equal error after %d refinement steps" % ok)
+    del ref, u, cells
     mesh.close()
