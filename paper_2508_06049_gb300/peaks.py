@@ -7,16 +7,17 @@ import os
 import subprocess
 import sys
 
-from .build import ARCH, _nvcc
+from .build import ARCH, PEAK_PROBE, _nvcc
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 def main():
-    exe = os.path.join(HERE, "_build", "peak_probe")
-    os.makedirs(os.path.dirname(exe), exist_ok=True)
-    subprocess.run([_nvcc()] + ARCH + ["-O3", "-o", exe, os.path.join(HERE, "peak_probe.cu")], check=True,
-                   capture_output=True)
+    exe = PEAK_PROBE
+    if not os.path.exists(exe):  # build() compiles it; compile here when it has not run
+        os.makedirs(os.path.dirname(exe), exist_ok=True)
+        subprocess.run([_nvcc()] + ARCH + ["-O3", "-lineinfo", "-o", exe, os.path.join(HERE, "peak_probe.cu")],
+                       check=True, capture_output=True)
     r = subprocess.run([exe], capture_output=True, text=True)
     sys.stdout.write(r.stdout)
     return r.returncode
