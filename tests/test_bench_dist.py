@@ -1,10 +1,14 @@
 """The N > 1 launch of bench.py (replicas, one process per GPU) on CPU: two gloo ranks rendezvous at
 127.0.0.1, pass the barrier, and agree on the maximum of their step times (the max over ranks that
-the bench's whole-job value divides by)."""
+the bench's whole-job value divides by); the reference arm under two ranks prints one line from
+rank 0 and lets rank 1 exit without work."""
 
+import json
 import multiprocessing as mp
 import os
 import socket
+import subprocess
+import sys
 
 
 def _free_port():
@@ -36,3 +40,24 @@ def test_gloo_two_ranks_barrier_and_max_over_ranks():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert out == [(0, 2, 2.5), (1, 2, 2.5)]
+
+
+
+def test_reference_arm_on_two_ranks_prints_once_from_rank_0():
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    port = _free_port()
+    procs = []
+    for r in range(2):
+        env = dict(os.environ, RANK=str(r), LOCAL_RANK=str(r), WORLD_SIZE="2", MASTER_ADDR="127.0.0.1",
+                   MASTER_PORT=str(port), HHG_BENCH_GLOO="1")
+        procs.append(subprocess.Popen([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                                       "--gpus", "2", "--steps", "1", "--warmup", "0"],
+                                      cwd=root, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+    outs = [p.communicate(timeout=300) for p in procs]
+    assert [p.returncode for p in procs] == [0, 0], [o[1][-2000:] for o in outs]
+    lines0 = [ln for ln in outs[0][0].splitlines() if ln.startswith("{")]
+    assert len(lines0) == 1 and not [ln for ln in outs[1][0].splitlines() if ln.startswith("{")]
+    line = json.loads(lines0[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
