@@ -5,6 +5,7 @@ The binary64 oracle fixes the target: refinement steps must converge to the exac
 the first (binary32 FMG) step must stay within single-precision distance of the binary64 FMG, the
 estimator computed from the binary32 FMG iterates must mark the same elements, and on the full-size
 cube the mixed solve must reach the binary64 discretisation error (equal error, first two digits).
+The mixed-precision adjoint must give the gradients of the exact discrete adjoint.
 """
 
 import math
