@@ -27,18 +27,8 @@ def P():
     return pkg
 
 
-def perturbed(name, seed=4, amp=0.12):
-    """Interior macro vertices moved randomly: general triangles / tets (full stencils)."""
-    co, ce = W.lshape_mesh() if name == "lshape" else W.cube_mesh(2)
-    co = co.copy()
-    rng = np.random.default_rng(seed)
-    h = 0.5
-    inner = np.all(np.abs(co) < 1 - 1e-9, axis=1) if name == "lshape" else \
-        np.all((co > 1e-9) & (co < 1 - 1e-9), axis=1)
-    if name == "lshape":
-        inner &= ~((np.abs(co[:, 0]) < 1e-9) | (np.abs(co[:, 1]) < 1e-9))
-    co[inner] += amp * h * rng.uniform(-1, 1, size=(inner.sum(), co.shape[1]))
-    return co, ce
+def perturbed(name, seed=4, amp=0.12, m=2):
+    return W.perturbed_mesh(name, seed=seed, amp=amp, m=m)
 
 
 CASES = {
@@ -47,7 +37,12 @@ CASES = {
     "lshape_pert": lambda: (*perturbed("lshape"), 4, None),
     "cube384": lambda: (*W.cube_mesh(4), 3, None),
     "cube_pert_k": lambda: (*perturbed("cube"), 3, W.coeff_uniform(48, seed=3)),
-    "cube3072_k": lambda: (*W.cube_mesh(8), 2, W.coeff_loguniform(3072, seed=0)),
+    # L = 3 is the first level of the 3072-tet cube whose face block takes the binary64 sparse
+    # slot loop (macro faces x face-interior nodes >= 1e5: 6528 x 21), the path the full-size
+    # binary64 solves take on their finest levels
+    "cube3072_k": lambda: (*W.cube_mesh(8), 3, W.coeff_loguniform(3072, seed=0)),
+    # general tets (15-point stencils, 4 interior colours) on the same sparse face path
+    "cube3072_pert_k": lambda: (*perturbed("cube", seed=6, m=8), 3, W.coeff_loguniform(3072, seed=0)),
     "fichera_k": lambda: (*W.fichera_mesh(), 3, W.coeff_uniform(336, seed=1)),
 }
 
@@ -99,6 +94,18 @@ def close_estimates(eg, eo, h, uo):
     # theta and eta_j are ratios / products of those norms: first-order error propagation
     rel = TOL * u_glob * (1 / eo["err_l"] + 1 / eo["err_lm1"])
     assert abs(eg["theta"] - eo["theta"]) <= rel * eo["theta"]
+
+
+def test_cases_reach_the_sparse_face_path():
+    """The binary64 face block switches to its sparse slot loop when macro faces x face-interior
+    nodes reach 1e5; the two 3072-tet cases are above that on their finest level (and below it on
+    the level under it), so the parity tests below cover both loops."""
+    for name in ("cube3072_k", "cube3072_pert_k"):
+        co, ce, L, _ = CASES[name]()
+        tri = np.sort(ce[:, [[0, 1, 2], [0, 1, 3], [0, 2, 3], [1, 2, 3]]].reshape(-1, 3), axis=1)
+        n_faces = len(np.unique(tri, axis=0))
+        nf = lambda l: (2 ** l - 1) * (2 ** l - 2) // 2
+        assert n_faces * nf(L) >= 100000 > n_faces * nf(L - 1), (name, n_faces)
 
 
 @pytest.mark.parametrize("name", list(CASES))

@@ -30,8 +30,31 @@ def P():
     return pkg
 
 
+def _f3(x):
+    return np.sin(3 * x[:, 0]) * np.cos(2 * x[:, 1]) + x[:, 2]
+
+
+def _g3(x):
+    return 0.1 * x[:, 0] - x[:, 2] * x[:, 1]
+
+
+# Meshes beyond the Kuhn-lattice workloads, for the binary32 kernels' other code paths:
+# general triangles / tets (7- and 15-point interior stencils, three / four interior colours), and
+# a single interior-stencil group of 162 cells (not a multiple of four: the binary32 interior stage
+# takes four cells per thread and the residual two, and a short last group repeats its last cell).
+GENERAL = {
+    "lshape_pert": lambda: (*W.perturbed_mesh("lshape"), lambda x: np.sin(3 * x[:, 0]) * np.cos(2 * x[:, 1]) + 1.0,
+                            lambda x: 0.25 + x[:, 0] * x[:, 1], None),
+    "cube_pert_k": lambda: (*W.perturbed_mesh("cube"), _f3, _g3, W.coeff_uniform(48, seed=3)),
+    "cube162": lambda: (*W.cube_mesh(3), _f3, _g3, None),
+}
+
+
 def _setup(P, name, L):
-    co, ce, _, f, g, k, ue = W.workload(name, L)
+    if name in GENERAL:
+        co, ce, f, g, k = GENERAL[name]()
+    else:
+        co, ce, _, f, g, k, ue = W.workload(name, L)
     mesh = P.Mesh(co, ce, L)
     if k is not None:
         mesh.set_coefficient(k)
@@ -42,7 +65,8 @@ def _setup(P, name, L):
     return mesh, h, O.Problem(h, f, g), idx
 
 
-@pytest.mark.parametrize("name,L", [("lshape_l7", 5), ("cube384_l6", 3), ("fichera336_l6", 3)])
+@pytest.mark.parametrize("name,L", [("lshape_l7", 5), ("cube384_l6", 3), ("fichera336_l6", 3), ("lshape_pert", 4),
+                                    ("cube_pert_k", 3), ("cube162", 3)])
 @pytest.mark.parametrize("storage", [0, 1])
 def test_refinement_converges_to_exact_discrete_solution(P, name, L, storage):
     mesh, h, prob, idx = _setup(P, name, L)
@@ -53,7 +77,8 @@ def test_refinement_converges_to_exact_discrete_solution(P, name, L, storage):
     mesh.close()
 
 
-@pytest.mark.parametrize("name,L", [("lshape_l7", 6), ("cube384_l6", 4)])
+@pytest.mark.parametrize("name,L", [("lshape_l7", 6), ("cube384_l6", 4), ("lshape_pert", 5), ("cube_pert_k", 4),
+                                    ("cube162", 4)])
 @pytest.mark.parametrize("storage,eta_tol", [(0, 5e-3), (1, 2e-2)])
 def test_binary32_fmg_step_and_estimator(P, name, L, storage, eta_tol):
     """The binary32 FMG step alone (no refinement): its solution is within single-precision distance
@@ -122,7 +147,8 @@ def test_equal_error_on_full_size_cube(P):
 # restricted residual and a bound of |A_l^{-1}|_inf.  The checks below are those of the other
 # storage types, with bfloat16's tolerances (binary16 rounds at least 8 times finer).
 
-@pytest.mark.parametrize("name,L", [("lshape_l7", 5), ("cube384_l6", 3), ("fichera336_l6", 3)])
+@pytest.mark.parametrize("name,L", [("lshape_l7", 5), ("cube384_l6", 3), ("fichera336_l6", 3), ("cube_pert_k", 3),
+                                    ("cube162", 3)])
 def test_binary16_storage_refinement_converges_to_exact_discrete_solution(P, name, L):
     mesh, h, prob, idx = _setup(P, name, L)
     u = mesh.solve(nu=2, pre=2, post=1, precision=1, storage=2, ir_steps=12, ir_vcycles=2)

@@ -145,6 +145,23 @@ def fichera_mesh():
     return co / 4.0, ce
 
 
+def perturbed_mesh(name: str, seed: int = 4, amp: float = 0.12, m: int = 2):
+    """General (non-lattice) macro meshes: the L-shape ("lshape") or the m^3 Kuhn cube ("cube") with
+    every vertex off the boundary (and, for the L-shape, off the axes through the re-entrant corner)
+    moved by amp * h * U(-1, 1) per coordinate (numpy default_rng(seed)), h = 1/2 for the L-shape and
+    1/m for the cube.  Triangles / tets then have full 7- / 15-point stencils."""
+    co, ce = lshape_mesh() if name == "lshape" else cube_mesh(m)
+    co = co.copy()
+    rng = np.random.default_rng(seed)
+    h = 0.5 if name == "lshape" else 1.0 / m
+    inner = np.all(np.abs(co) < 1 - 1e-9, axis=1) if name == "lshape" else \
+        np.all((co > 1e-9) & (co < 1 - 1e-9), axis=1)
+    if name == "lshape":
+        inner &= ~((np.abs(co[:, 0]) < 1e-9) | (np.abs(co[:, 1]) < 1e-9))
+    co[inner] += amp * h * rng.uniform(-1, 1, size=(inner.sum(), co.shape[1]))
+    return co, ce
+
+
 # ---- manufactured functions (evaluated at points x of shape (N, d)) ----
 
 def sin_product_u(x: np.ndarray) -> np.ndarray:
