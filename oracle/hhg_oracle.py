@@ -530,12 +530,26 @@ def nodal(h: Hierarchy, fn, l: int) -> np.ndarray:
 
 
 class Problem:
-    """b_l = M_l f_l (the right-hand side of Eq. 4.15, Sec. 4.4) and Dirichlet values g_l for every
-    level of a hierarchy."""
+    """The right-hand sides b_l of Eq. 4.15 (Sec. 4.4) and Dirichlet values g_l for every level of a
+    hierarchy.  The paper does not say how the coarse levels' right-hand sides are formed; two
+    readings are offered:
+      rhs="injected" (default): b_l = M_l f_l with f_l the values of f at the level-l nodes;
+      rhs="restricted": b_L = M_L f_L and b_l = I_l^T b_{l+1} for l < L (I = the interpolation of
+        Sec. 4.4), i.e. the load vector of the level-L interpolant of f tested with the level-l hat
+        functions (each of which is a combination of level-L hat functions)."""
 
-    def __init__(self, h: Hierarchy, f, g):
+    def __init__(self, h: Hierarchy, f, g, rhs: str = "injected"):
         self.h = h
-        self.b = [lev.M @ nodal(h, f, lev.l) for lev in h.levels]
+        if rhs == "injected":
+            self.b = [lev.M @ nodal(h, f, lev.l) for lev in h.levels]
+        elif rhs == "restricted":
+            b = [None] * (h.L + 1)
+            b[h.L] = h.levels[h.L].M @ nodal(h, f, h.L)
+            for l in range(h.L, 0, -1):
+                b[l - 1] = h.levels[l].P.T @ b[l]
+            self.b = b
+        else:
+            raise ValueError("rhs must be 'injected' or 'restricted'")
         self.g = [nodal(h, g, lev.l) for lev in h.levels]
         lev0 = h.levels[0]
         F = np.nonzero(lev0.free)[0]

@@ -136,6 +136,46 @@ def test_galerkin_identity(name, L):
             assert diff <= 1e-13 * abs(coarse).max(), (op, l, diff)
 
 
+@pytest.mark.parametrize("name,L", [("square_l4", 3), ("cube384_l6", 2)])
+def test_restricted_rhs_is_the_load_vector_of_the_fine_interpolant(name, L):
+    """The restricted right-hand sides b_l = I^T b_{l+1}, b_L = M_L f_L: (i) for f the interpolant of
+    a level-m function (f_L = I ... I f_m) they equal the injected b_l = M_l f_l on every level l >= m
+    (Galerkin identity I^T M_{l+1} I = M_l; there f_l is the interpolant too), and a generic f makes
+    them differ below level L; (ii) on every level,
+    b_l^T v_l = b_L^T (I ... I v_l) for any level-l vector v_l (b_l tests the level-L load vector with
+    the level-l hat functions written in the level-L basis)."""
+    h, *_ = _hier(name, L)
+    rng = np.random.default_rng(4)
+    m = 1
+    fm = rng.standard_normal(len(h.levels[m].keys))
+    fL = fm
+    for l in range(m + 1, L + 1):
+        fL = h.levels[l].P @ fL
+    zero = lambda x: np.zeros(len(x))
+    pr = O.Problem(h, fL, zero, rhs="restricted")
+    pi = O.Problem(h, fL, zero, rhs="injected")
+    for l in range(L + 1):
+        scale = np.abs(pi.b[l]).max()
+        diff = np.abs(pr.b[l] - pi.b[l]).max()
+        if l >= m:
+            assert diff <= 1e-13 * scale, (l, diff)
+    # a generic f: the restricted and injected coarse right-hand sides differ below level L
+    x = h.levels[L].x
+    pr2 = O.Problem(h, lambda y: np.exp(3 * y[:, 0]) * np.cos(5 * y[:, 1]), zero, rhs="restricted")
+    pi2 = O.Problem(h, lambda y: np.exp(3 * y[:, 0]) * np.cos(5 * y[:, 1]), zero, rhs="injected")
+    assert np.array_equal(pr2.b[L], pi2.b[L])
+    assert np.abs(pr2.b[L - 1] - pi2.b[L - 1]).max() > 1e-6 * np.abs(pi2.b[L - 1]).max()
+    for l in range(L + 1):
+        v = rng.standard_normal(len(h.levels[l].keys))
+        vL = v
+        for q in range(l + 1, L + 1):
+            vL = h.levels[q].P @ vL
+        lhs, rhs = float(pr2.b[l] @ v), float(pr2.b[L] @ vL)
+        assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(rhs)), (l, lhs, rhs)
+    with pytest.raises(ValueError):
+        O.Problem(h, zero, zero, rhs="other")
+
+
 def test_interpolation_reproduces_linear_functions():
     h, *_ = _hier("cube3072_l7", 2)
     rng = np.random.default_rng(3)
