@@ -36,11 +36,15 @@ sys.path.insert(0, ROOT)
 for _var in ("OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_var, "1")
 
-# Equal error (Sec. 5 protocol): extra level-L cycles until the L2 error is stable.  On the 384-tet
-# cube at L = 6 the converged error is 2.251e-5; binary64 FMG + 4 extra V-cycles gives 2.260e-5,
-# binary32 FMG + 2 refinement steps of 2 binary32 V-cycles gives 2.261e-5 (both within 0.5 %).
-FP64_EXTRA = 4
-MIXED_DEFAULT = dict(storage=0, ir_steps=2, ir_vcycles=2)
+# Equal error (Sec. 5: extra level-L cycles until the L2 error is stable to two digits).  Each arm's
+# parameters are searched on the device before it is timed (equal_error_search): the least work whose
+# error is within 1 % of the converged binary64 error (workloads with an exact solution), or whose
+# algebraic error is within 1 % of the estimated discretisation error eta_1 (the others).
+REF_EXTRA = 24          # extra binary64 V-cycles of the converged reference solve (exact solution known)
+REF_EXTRA_ALG = 160     # the same where the reference itself is the target (V-cycles contracting ~0.9)
+BIG_NODES = 2e8         # level-L layouts above this many nodes get coordinates and data on the device
+FP64_EXTRA = 4          # binary64 extra V-cycles of the CPU oracle's timed step (cpu_baseline, reference arm)
+MIXED_STORAGE = 0       # default correction storage of the mixed arm (binary32)
 
 
 def parse():
@@ -56,8 +60,14 @@ def parse():
                          "kl_compare: uniform vs Alg. 1 vs Alg. 2 refinement (Sec. 5.1-5.2, final error and rho)")
     ap.add_argument("--workload", default=None, help="default cube384_l6 (step) or waves3d_l8 (alg5)")
     ap.add_argument("--level", type=int, default=None, help="--program alg5 / effectivity: override the finest level L")
+    ap.add_argument("--rhs", type=int, default=0, choices=[0, 1],
+                    help="coarse right-hand sides: 0 = M_l f_l with f at the level-l nodes, 1 = restricted from "
+                         "b_L (--program effectivity / kl_compare)")
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
     ap.add_argument("--storage", type=int, default=None, help="mixed arm correction storage: 0 binary32 (default), 1 bfloat16, 2 binary16")
+    ap.add_argument("--fixed", default=None,
+                    help="fixed arm parameters instead of the equal-error search, 'N,S,V': binary64 FMG + N extra "
+                         "V-cycles, mixed S refinement steps of V V-cycles (for profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel-only", type=int, default=0,
@@ -156,13 +166,96 @@ def make_problem(name, L=None):
     return co, ce, LL, f, g, k, ue
 
 
-def params_for(precision, P, storage=None):
-    if precision == "fp64":
-        return P.solve_params(nu=2, pre=2, post=1, n_extra=FP64_EXTRA, precision=0)
-    kw = dict(MIXED_DEFAULT)
-    if storage is not None:
-        kw["storage"] = storage
-    return P.solve_params(nu=2, pre=2, post=1, n_extra=0, precision=1, **kw)
+def fp64_params(P, n_extra):
+    return P.solve_params(nu=2, pre=2, post=1, n_extra=n_extra, precision=0)
+
+
+def mixed_params(P, storage, ir_steps, ir_vcycles):
+    return P.solve_params(nu=2, pre=2, post=1, n_extra=0, precision=1, storage=storage, ir_steps=ir_steps,
+                          ir_vcycles=ir_vcycles)
+
+
+def least_passing(ok, hi):
+    """Smallest n in [0, hi] with ok(n) true, for ok monotone in n (doubling, then bisection); None if
+    ok(hi) is false."""
+    if ok(0):
+        return 0
+    lo, n = 0, 1
+    while n < hi and not ok(n):
+        lo, n = n, 2 * n
+    n = min(n, hi)
+    if n == hi and not ok(hi):
+        return None
+    while n - lo > 1:
+        mid = (lo + n) // 2
+        if ok(mid):
+            n = mid
+        else:
+            lo = mid
+    return n
+
+
+def equal_error_search(su, P, storage):
+    """Each arm's least work at the binary64 discretisation error (Sec. 5's two-digit rule), measured on
+    the device: the squared M-norm of a difference is the sum of the per-cell mass forms.  With an
+    exact solution u: error = ||I u - u_L||_M, criterion |error - error_ref| <= 1 % error_ref, the
+    reference being binary64 FMG + REF_EXTRA extra V-cycles.  Without one: error = ||u_L - u_ref||_M
+    (algebraic), criterion <= 1 % of eta_1 of the reference.  binary64 arm: least n_extra; mixed arm:
+    least refinement V-cycles (ir_steps x ir_vcycles, ir_vcycles in {1, 2})."""
+    import torch
+    mesh, s = su.mesh, su.s
+    ud = torch.empty_like(su.fd)
+    cells = torch.empty(mesh.n_cells, dtype=torch.float64, device=su.fd.device)
+
+    def m_dist(a, b):
+        mesh.cell_mass_norms_noalloc(a, b, cells)
+        mesh.synchronize()
+        return math.sqrt(max(0.0, float(cells.sum().item())))
+
+    ref_extra = REF_EXTRA if su.ued is not None else REF_EXTRA_ALG
+    mesh.solve(fp64_params(P, ref_extra), out=ud)
+    ref = ud.clone()
+    eta_ref = mesh.estimate(1, want_local=False)["eta_j"]
+    if su.ued is not None:
+        e_ref = m_dist(su.ued, ref)
+        err = lambda u: m_dist(su.ued, u)
+        ok_err = lambda e: abs(e - e_ref) <= 0.01 * e_ref
+        crit = "|e - e_ref| <= 1 %% of e_ref, e = ||I u - u_L||_M, e_ref = %.6e (binary64 FMG + %d extra V-cycles)" % (
+            e_ref, ref_extra)
+    else:
+        e_ref = None
+        err = lambda u: m_dist(ref, u)
+        ok_err = lambda e: e <= 0.01 * eta_ref
+        crit = ("||u_L - u_ref||_M <= 1 %% of eta_1(u_ref) = %.6e, u_ref = binary64 FMG + %d extra V-cycles"
+                % (eta_ref, ref_extra))
+    tried64, tried32 = {}, {}
+
+    def ok64(n):
+        if n not in tried64:
+            mesh.solve(fp64_params(P, n), out=ud)
+            tried64[n] = err(ud)
+        return ok_err(tried64[n])
+
+    def ok32(steps, nv):
+        key = "%dx%d" % (steps, nv)
+        if key not in tried32:
+            mesh.solve(mixed_params(P, storage, steps, nv), out=ud)
+            tried32[key] = err(ud)
+        return ok_err(tried32[key])
+
+    n64 = least_passing(ok64, ref_extra)
+    best = None
+    for nv in (1, 2):
+        st = least_passing(lambda k: ok32(k, nv), 64)
+        # least V-cycles; on a tie fewer refinement steps (each adds a binary64 residual and update)
+        if st is not None and (best is None or (st * nv, st) < (best[0] * best[1], best[0])):
+            best = (st, nv)
+    if n64 is None or best is None:
+        raise RuntimeError("equal-error search found no passing configuration: %s %s" % (tried64, tried32))
+    return {"criterion": crit, "reference_error": e_ref, "reference_eta_1": eta_ref,
+            "fp64": {"n_extra": n64, "error": tried64[n64], "tried_n_extra": tried64},
+            "mixed": {"storage": storage, "ir_steps": best[0], "ir_vcycles": best[1],
+                      "error": tried32["%dx%d" % best], "tried_steps_x_vcycles": tried32}}
 
 
 def peaks():
@@ -173,8 +266,10 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# measured binary64 FMA throughput of the GB300 (paper_2508_06049_gb300/peak_probe.cu, summarised under profiles/)
-FP64_PEAK_TFLOPS = 1.205
+# binary64 FMA peak of the GB300 from its unit counts and clock: 152 SMs x 2 binary64 FMA per SM and
+# clock x 2 flops x 2.070 GHz = 1.259 TFLOP/s (the nominal 1.25 TFLOP/s of the part at its maximum
+# SM clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) of one launch of the roofline kernel on the 384-tet cube at L = 6, from
 # one ncu capture of that kernel (summarised under profiles/); None for other workloads
 TRAFFIC_BYTES = {("cube384_l6", "fp64"): 369.5e6, ("cube384_l6", "mixed"): 165.6e6}
@@ -197,27 +292,51 @@ class Setup:
         self.mesh = P.Mesh(co, ce, L, stream=self.s)
         if k is not None:
             self.mesh.set_coefficient(k)
-        self.x = self.mesh.level_coords(L)
-        self.fh = torch.from_numpy(np.ascontiguousarray(f(self.x))).pin_memory()
-        self.gh = torch.from_numpy(np.ascontiguousarray(g(self.x))).pin_memory()
+        N = self.mesh.n_nodes(L)
+        self.N = N
+        self.ued = None  # the exact solution at the level-L nodes (device), for the equal-error search
+        if N <= BIG_NODES:
+            x = self.mesh.level_coords(L)
+            self.fh = torch.from_numpy(np.ascontiguousarray(f(x))).pin_memory()
+            self.gh = torch.from_numpy(np.ascontiguousarray(g(x))).pin_memory()
+            with torch.cuda.stream(self.s):
+                self.fd = self.fh.to("cuda", non_blocking=True)
+                self.gd = self.gh.to("cuda", non_blocking=True)
+                if ue is not None:
+                    self.ued = torch.from_numpy(np.ascontiguousarray(ue(x))).to("cuda", non_blocking=True)
+        else:
+            # coordinates and data evaluated on the device (no host copy of the level-L vectors, so no
+            # e2e leg)
+            self.fh = self.gh = None
+            with torch.cuda.stream(self.s):
+                xd = torch.empty((N, co.shape[1]), dtype=torch.float64, device="cuda")
+            self.mesh.level_coords(L, out=xd)
+            with torch.cuda.stream(self.s):
+                self.fd = f(xd).contiguous()
+                self.gd = g(xd).contiguous()
+                if ue is not None:
+                    self.ued = ue(xd).contiguous()
+                del xd
         with torch.cuda.stream(self.s):
-            self.fd = self.fh.to("cuda", non_blocking=True)
-            self.gd = self.gh.to("cuda", non_blocking=True)
             self.ud = torch.empty_like(self.fd)
         self.s.synchronize()
         self.mesh.set_data(self.fd, self.gd)
         self.L, self.ce, self.ue = L, ce, ue
 
 
-def run_arm(args, rank, world, su, precision):
+def run_arm(args, rank, world, su, precision, search):
     import numpy as np
     import torch
 
     import paper_2508_06049_gb300 as P
-    mesh, s, x, L, ce, ue = su.mesh, su.s, su.x, su.L, su.ce, su.ue
+    mesh, s, N, L, ce, ue = su.mesh, su.s, su.N, su.L, su.ce, su.ue
     fh, gh, fd, gd, ud, dev = su.fh, su.gh, su.fd, su.gd, su.ud, su.dev
     mesh.set_data(fd, gd)
-    prm = params_for(precision, P, args.storage)
+    if precision == "fp64":
+        prm = fp64_params(P, search["fp64"]["n_extra"])
+    else:
+        sm = search["mixed"]
+        prm = mixed_params(P, sm["storage"], sm["ir_steps"], sm["ir_vcycles"])
     unknowns = mesh.info.n_unknowns
     frac = 0.125
 
@@ -229,15 +348,8 @@ def run_arm(args, rank, world, su, precision):
 
     for _ in range(args.warmup):
         est = step()
-    # accuracy of this configuration against the exact solution (workloads with a known u)
-    err = None
-    if ue is not None:
-        uu = ud.cpu().numpy()
-        e = np.ascontiguousarray(ue(x) - uu)
-        Me = mesh.apply(L, 1, e)
-        _, inv, cnt = np.unique(np.round(x * 2 ** (L + 3)).astype(np.int64), axis=0, return_inverse=True,
-                                return_counts=True)
-        err = math.sqrt(float(np.sum(e * Me / cnt[inv.ravel()])))
+    # accuracy of this configuration (from the equal-error search)
+    err = search[precision]["error"]
     barrier(world)
     torch.cuda.synchronize()
     clk = ClockSampler(dev)
@@ -259,8 +371,8 @@ def run_arm(args, rank, world, su, precision):
 
     # e2e through host buffers
     e2e = None
-    if not args.no_e2e:
-        uh = torch.empty(len(x), dtype=torch.float64).pin_memory()
+    if not args.no_e2e and fh is not None:
+        uh = torch.empty(N, dtype=torch.float64).pin_memory()
         def step_e2e():
             mesh.set_data(fh, gh)
             mesh.solve(prm, out=uh)
@@ -280,7 +392,7 @@ def run_arm(args, rank, world, su, precision):
         torch.cuda.synchronize()
         ms_e2e = allmax(a0.elapsed_time(a1) / ne, world)
         e2e = {"value": world * unknowns / (ms_e2e * 1e-3), "unit": "DoF/s", "ms_per_step": ms_e2e,
-               "h2d_bytes_per_step": 2 * 8 * len(x), "d2h_bytes_per_step": 8 * len(x) + 8 * len(ce)}
+               "h2d_bytes_per_step": 2 * 8 * N, "d2h_bytes_per_step": 8 * N + 8 * len(ce)}
 
     # device time of each phase of the step, called alone (the estimate includes its D2H of eta_T)
     phases = {}
@@ -316,7 +428,7 @@ def run_arm(args, rank, world, su, precision):
     if precision == "fp64":
         rf_obj = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                   "frac": tfl / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES.get((args.workload, precision)),
-                  "peak_kind": "measured binary64 FMA throughput (paper_2508_06049_gb300/peak_probe.cu)",
+                  "peak_kind": "binary64 FMA peak from unit counts and the maximum SM clock (152 SMs x 2 FMA/clock x 2 flops x 2.07 GHz)",
                   "hbm_gbs": gbs, "hbm_frac": gbs / pk.get("hbm_gbs", 6800.0)}
     else:
         peak = pk.get("hbm_gbs", 6800.0)
@@ -336,11 +448,13 @@ def run_arm(args, rank, world, su, precision):
 
 
 def cpu_baseline(workload, budget_s=20.0):
-    """The oracle as it stands on a bounded sample: the same workload at a lower level."""
+    """The oracle as it stands on a bounded sample: the same workload one level below the timed one
+    in 3D (the 384-tet cube at L = 5: 2.0e6 unknowns, about 10 s per step on one core; building its
+    hierarchy takes about two minutes more), at most L = 6 in 2D."""
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     from oracle import hhg_oracle as O
     co, ce, L, f, g, k, ue = make_problem(workload)
-    Ls = min(L, 4 if co.shape[1] == 3 else 6)
+    Ls = min(L, 5 if co.shape[1] == 3 else 6)
     co, ce, Ls, f, g, k, ue = make_problem(workload, Ls)
     h = O.Hierarchy(co, ce, Ls, k=k)
     prob = O.Problem(h, f, g)
@@ -586,7 +700,7 @@ def study_problems():
 
 
 def effectivity_study(P, device, L=8, K=10, nus=(6, 2), fraction=0.10, names=("waves2d", "lshape"), log=None,
-                      n_extra=STUDY_EXTRA_CYCLES):
+                      n_extra=STUDY_EXTRA_CYCLES, rhs=0):
     """Sec. 5.3: kl-refinement (Alg. 2) with K steps, each marking the given fraction of macro
     triangles with the largest actual local L2 errors for red refinement (Sec. 5 drives refinement
     by the true errors), and at every grid T^k_L the global estimates eta_j, j = 1..4, of the FMG
@@ -602,7 +716,7 @@ def effectivity_study(P, device, L=8, K=10, nus=(6, 2), fraction=0.10, names=("w
     for name in names:
         mk, f, uex, q = problems[name]
         for nu in nus:
-            prm = P.solve_params(nu=nu, pre=2, post=2, n_extra=n_extra, precision=0)
+            prm = P.solve_params(nu=nu, pre=2, post=2, n_extra=n_extra, precision=0, rhs=rhs)
             co, ce = mk()
             rg = P.RG2D(co, ce)
             rows = []
@@ -645,22 +759,24 @@ def effectivity_study(P, device, L=8, K=10, nus=(6, 2), fraction=0.10, names=("w
     return out
 
 
-def coarse_errors_sq(P, device, c, e, f, uex, prm, n=256):
+def coarse_errors_sq(P, device, c, e, f, uex, prm, n=256, Lc=1):
     """Alg. 1's coarse step: the P1 solution u_0 on the macro mesh itself (the exact coarse-grid
-    solve inside the FMG of a one-level hierarchy, read back from w_0 at the macro vertices) and,
-    per macro triangle, the squared L2 norm of u - u_0 (u_0 interpolated linearly onto a side-n
-    lattice, Radon's rule on its micro triangles)."""
+    solve inside the FMG of a hierarchy of Lc levels, read back from w_0 at the macro vertices; the
+    level-0 right-hand side comes from f at the level-Lc nodes as prm.rhs selects) and, per macro
+    triangle, the squared L2 norm of u - u_0 (u_0 interpolated linearly onto a side-n lattice, Radon's
+    rule on its micro triangles)."""
     import torch
-    mesh = P.Mesh(c, e, 1)
-    N1 = mesh.n_nodes(1)
-    x1 = torch.empty((N1, 2), dtype=torch.float64, device=device)
-    mesh.level_coords(1, out=x1)
-    fd, gd = f(x1).contiguous(), uex(x1).contiguous()
+    mesh = P.Mesh(c, e, Lc)
+    NL = mesh.n_nodes(Lc)
+    xL = torch.empty((NL, 2), dtype=torch.float64, device=device)
+    mesh.level_coords(Lc, out=xL)
+    fd, gd = f(xL).contiguous(), uex(xL).contiguous()
     if device != "cpu":
         torch.cuda.synchronize()
     mesh.set_data(fd, gd)
-    u1 = torch.empty(N1, dtype=torch.float64, device=device)
-    mesh.solve(prm, out=u1)
+    uL = torch.empty(NL, dtype=torch.float64, device=device)
+    mesh.solve(prm, out=uL)
+    N1 = mesh.n_nodes(1)
     w0 = torch.empty(N1, dtype=torch.float64, device=device)
     mesh.get_vector(1, 0, out=w0)
     if device != "cpu":
@@ -683,7 +799,7 @@ def coarse_errors_sq(P, device, c, e, f, uex, prm, n=256):
 
 
 def kl_compare_study(P, device, L=8, K=10, fraction=0.10, names=("waves2d", "lshape"), log=None,
-                     n_extra=STUDY_EXTRA_CYCLES):
+                     n_extra=STUDY_EXTRA_CYCLES, rhs=0):
     """Sec. 5.1-5.2: uniform refinement, k+l-refinement (Alg. 1: K steps of solving on the coarse
     grid and marking by its local errors, then L uniform levels) and kl-refinement (Alg. 2: marking
     by the local errors of the level-L solution), each ending with a level-L solve on its final
@@ -693,7 +809,7 @@ def kl_compare_study(P, device, L=8, K=10, fraction=0.10, names=("waves2d", "lsh
     import numpy as np
     import torch
     problems = study_problems()
-    prm = P.solve_params(nu=2, pre=2, post=2, n_extra=n_extra, precision=0)
+    prm = P.solve_params(nu=2, pre=2, post=2, n_extra=n_extra, precision=0, rhs=rhs)
     tri = micro_triangles(1 << L)
 
     def fine_error(c, e):
@@ -719,7 +835,8 @@ def kl_compare_study(P, device, L=8, K=10, fraction=0.10, names=("waves2d", "lsh
     for name in names:
         mk, f, uex, q = problems[name]
         co, ce = mk()
-        e2H = coarse_errors_sq(P, device, co, ce, f, uex, prm)
+        Lc = 1 if rhs == 0 else L   # restricted: the coarse load vector from f at the level-L nodes
+        e2H = coarse_errors_sq(P, device, co, ce, f, uex, prm, Lc=Lc)
         eH = math.sqrt(float(e2H.sum()))
         res = {"coarse_cells": int(len(ce)), "coarse_error": eH}
         # uniform
@@ -729,7 +846,7 @@ def kl_compare_study(P, device, L=8, K=10, fraction=0.10, names=("waves2d", "lsh
         rg = P.RG2D(co, ce)
         for k in range(K):
             c, e = rg.mesh()
-            e2c = e2H if k == 0 else coarse_errors_sq(P, device, c, e, f, uex, prm)
+            e2c = e2H if k == 0 else coarse_errors_sq(P, device, c, e, f, uex, prm, Lc=Lc)
             rg.refine(P.mark(np.sqrt(e2c.cpu().numpy()), fraction))
         c, e = rg.mesh()
         e2, unk = fine_error(c, e)
@@ -763,10 +880,12 @@ def kl_compare(args):
     import paper_2508_06049_gb300 as P
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     t0 = time.perf_counter()
-    res = kl_compare_study(P, "cuda", L=args.level or 8, K=10, log=lambda m: print(m, file=sys.stderr, flush=True))
+    res = kl_compare_study(P, "cuda", L=args.level or 8, K=10, log=lambda m: print(m, file=sys.stderr, flush=True),
+                           rhs=args.rhs)
     line = {"program": "kl_compare", "metric": "final L2 error and rho of uniform, Alg. 1 and Alg. 2 refinement",
             "unit": "1", "L": args.level or 8, "K": 10, "marking": "top 10 % of actual local L2 errors",
             "fmg": "nu=2 V(2,2) + %d level-L cycles, binary64" % STUDY_EXTRA_CYCLES,
+            "coarse_rhs": ["M_l f_l, f at the level-l nodes", "restricted from b_L"][args.rhs],
             "paper_rho_waves2d": {"uniform": 9.8, "alg1": 1.5, "alg2": 0.9},
             "wall_s": time.perf_counter() - t0, "results": res}
     print(json.dumps(line), flush=True)
@@ -779,10 +898,12 @@ def effectivity(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     t0 = time.perf_counter()
     res = effectivity_study(P, "cuda", L=args.level or 8, K=10,
-                            log=lambda m: print(m, file=sys.stderr, flush=True))
+                            log=lambda m: print(m, file=sys.stderr, flush=True), rhs=args.rhs)
     line = {"program": "effectivity", "metric": "worst-case effectivity eta_j / ||u - u_L|| over the kl steps",
             "unit": "ratio", "L": args.level or 8, "K": 10, "marking": "top 10 % of actual local L2 errors",
-            "fmg": "nu V(2,2) + %d level-L cycles, binary64" % STUDY_EXTRA_CYCLES, "wall_s": time.perf_counter() - t0, "results": res}
+            "fmg": "nu V(2,2) + %d level-L cycles, binary64" % STUDY_EXTRA_CYCLES,
+            "coarse_rhs": ["M_l f_l, f at the level-l nodes", "restricted from b_L"][args.rhs],
+            "wall_s": time.perf_counter() - t0, "results": res}
     print(json.dumps(line), flush=True)
 
 
@@ -802,9 +923,6 @@ def main():
         return
     rank, world = dist_init(args.gpus)
     config = {"workload": args.workload, "macro_cells": None, "L": None, "precision": args.precision,
-              "equal_error": "fp64: FMG + %d extra V-cycles; mixed: binary32 FMG + %d x %d binary32 V-cycles "
-                             "in binary64 refinement (both within 0.5 %% of the converged L2 error)"
-                             % (FP64_EXTRA, MIXED_DEFAULT["ir_steps"], MIXED_DEFAULT["ir_vcycles"]),
               "cycle": "FMG nu=2 V(2,1), estimator j=1, marking 12.5%",
               "l2": "level-L vectors exceed the 129 MB L2 (no flush needed)"}
     co, ce, L, *_ = make_problem(args.workload)
@@ -824,22 +942,31 @@ def main():
             print(json.dumps(line), flush=True)
         return
     su = Setup(args)
+    import paper_2508_06049_gb300 as P
+    storage = MIXED_STORAGE if args.storage is None else args.storage
+    if args.fixed:
+        n64, st, nv = (int(v) for v in args.fixed.split(","))
+        search = {"criterion": "fixed parameters (--fixed), not searched", "fp64": {"n_extra": n64, "error": None},
+                  "mixed": {"storage": storage, "ir_steps": st, "ir_vcycles": nv, "error": None}}
+    else:
+        search = equal_error_search(su, P, storage)
+    config["equal_error"] = search
     arms = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
-    res = {a: run_arm(args, rank, world, su, a) for a in arms}
+    res = {a: run_arm(args, rank, world, su, a, search) for a in arms}
     head = res[arms[-1]]
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload)
     if rank == 0:
         def arm_summary(r):
-            return {"value": r["value"], "ms_per_step": r["ms"], "l2_error_vs_exact": r["err"], "eta_1": r["eta"],
+            return {"value": r["value"], "ms_per_step": r["ms"], "error": r["err"], "eta_1": r["eta"],
                     "params": r["params"], "roofline": r["roofline"], "gpu_launches_per_step": r["launches"],
                     "clocks": r["clocks"], "phases_ms": r["phases"]}
         line = {"metric": "FMG DoF/s (FMG + estimator + marking per step, equal error)", "value": head["value"],
                 "unit": "DoF/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if arms[-1] == "fp64" else "f32+f64-refinement", "data": "synthetic",
-                "config": config, "unknowns": head["unknowns"], "l2_error_vs_exact": head["err"],
+                "config": config, "unknowns": head["unknowns"], "error": head["err"],
                 "clocks": head["clocks"], "e2e": head["e2e"], "roofline": head["roofline"], "cpu_baseline": cpu,
                 "gpu_launches": head["launches"] * args.steps, "arms": {a: arm_summary(res[a]) for a in arms}}
         if len(arms) == 2:

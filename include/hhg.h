@@ -71,13 +71,17 @@ typedef enum {
  * edge-local nodes, the odd edge nodes, (3D) the face block - every macro face by Gauss-Seidel
  * over its colours (a + 2b) mod 3 with all nodes outside the face at their values from the start
  * of the block - and the macro-cell interiors by colours (alpha . p) mod m.  Nodes of one stage
- * are updated from the values at the start of the stage. */
+ * are updated from the values at the start of the stage.
+ * rhs: the coarse levels' right-hand sides (the paper does not fix them): 0 = b_l = M_l f_l with f
+ * taken at the level-l nodes; 1 = b_L = M_L f_L and b_l = I^T b_{l+1} (I the interpolation), the
+ * load vector of the level-L interpolant of f tested with the level-l hat functions. */
 typedef struct {
   int nu, pre, post, n_extra;
   int precision;
   int storage;
   int ir_steps;
   int ir_vcycles;
+  int rhs;
 } hhg_solve_params;
 
 typedef struct {
@@ -111,6 +115,9 @@ hhg_status hhg_mesh_create(int dim, int n_verts, const double* coords, int n_cel
 /* Release the hierarchy and every device buffer it owns (no counterpart in the paper: object
  * lifetime).  NULL is accepted. */
 hhg_status hhg_mesh_destroy(hhg_mesh mesh);
+/* Wait until all work queued on the mesh's stream has completed (no counterpart in the paper:
+ * stream ordering).  Errors: HHG_ERR_ARG (NULL), HHG_ERR_CUDA (a failure reported by the stream). */
+hhg_status hhg_mesh_synchronize(hhg_mesh mesh);
 /* Sizes of the hierarchy (Sec. 2): dimension, L, macro cells and vertices, nodes per level in the
  * layout above, free distinct level-L nodes (the DoF count), device bytes, interior colours. */
 hhg_status hhg_mesh_get_info(hhg_mesh mesh, hhg_mesh_info* info);
@@ -165,7 +172,10 @@ hhg_status hhg_get_vector(hhg_mesh mesh, int which, int level, double* out);
  * (host or device), interface rows summed over adjacent cells.
  * op = 0: stiffness A_l (all rows, Dirichlet rows included as plain P1 rows),
  * op = 1: mass M_l, op = 2: interpolation from level l-1 (in has N_{l-1} entries),
- * op = 3: nsweeps Gauss-Seidel sweeps in place on out (the initial guess) with rhs M_l in. */
+ * op = 3: nsweeps Gauss-Seidel sweeps in place on out (the initial guess) with rhs M_l in;
+ * op = 4: the same with the mixed mode's binary32 smoother (rhs and initial guess rounded to
+ * binary32, the result widened to binary64).  Ops 3 and 4 overwrite the level's solve data: run
+ * a solve again before hhg_estimate. */
 hhg_status hhg_apply(hhg_mesh mesh, int level, int op, const double* in, double* out, int nsweeps);
 
 /* Top-fraction marking (Sec. 5.1), host only: n = max(1, ceil(fraction*n - 1e-9)) elements
@@ -219,7 +229,11 @@ hhg_status hhg_rg3d_mark_refine(hhg_rg3d rg, const double* eta_T, double fractio
  * V-cycles stored as params->storage (as in hhg_fmg_solve): a first step of ir_vcycles V-cycles
  * (the adjoint right-hand side is given on level L only, so there is no binary32 FMG step), then
  * ir_steps steps of ir_vcycles V-cycles and n_extra steps of one.  The results are
- *   J (host), grad_f = M_L lambda (dJ/d nodal f_L; host or device, N_L, may be NULL),
+ *   J (host);
+ *   grad_f (host or device, N_L, may be NULL): dJ/df_L for every entry of the level-L layout.  The
+ *   right-hand side b_L = sum_T M_T f_T takes each cell's own copy of an interface node, so the
+ *   entry of copy p in cell T is (M_T lambda)_p; summed over a node's copies it is (M_L lambda)_p,
+ *   the derivative with respect to the node's value;
  *   grad_k[T] = -lambda^T A_T^(1) u (dJ/dk_T; host, n_cells, may be NULL). */
 hhg_status hhg_adjoint_l2(hhg_mesh mesh, const hhg_solve_params* params, const unsigned char* in_S,
                           double* J, double* grad_f, double* grad_k);
@@ -231,16 +245,16 @@ int hhg_lattice_selfcheck(int dim, int n);
 
 /* Profiling support (no counterpart in the paper).  Enqueue `reps` launches of one kernel of the solve on the mesh's stream,
  * exactly as the solve launches it, without synchronising (bracket it with events on that stream).
- * kernel 0: macro-interior smoothing stage of colour 0 on level L for the first cell group;
- * kernel 1 (3D, binary64): the level-L macro-face stage of colour 0 (units only; bytes = flops = 0);
+ * kernel 0: the macro-interior smoothing of level L for the first cell group: precision 0, the
+ * binary64 colour-0 stage; precision 1, the binary32 interior sweep as the mixed solve runs it (in 3D
+ * one launch for all colours where it fits in shared memory, else the colour-0 stage);
+ * kernel 1 (3D, binary64): the level-L macro-face stage (units only; bytes = flops = 0);
  * kernels 2, 3, 4 (binary64): the level-L prolongation-add, residual (every node computed) and
- * estimator mass form of one vector (units = level-L nodes); kernel 5 (binary32, 3D): the interior
- * stage of kernel 0 staged through shared memory by bulk copies; kernel 6 (binary32, 3D): the same
- * stage with two cells per thread (both for comparison with the four-cells-per-thread kernel).
- * precision 0: the binary64 kernel; 1: the binary32 kernel of the mixed path (its buffers are
- * allocated on first use).  units: nodes updated per launch; bytes / flops: algorithmic bytes and floating-point
- * operations of one launch (the model is stated in the library's design notes).  The launches
- * modify the level-L iterate: run a solve again before hhg_estimate. */
+ * estimator mass form of one vector (units = level-L nodes).
+ * precision 1 allocates the mixed path's buffers on first use.  units: nodes updated per launch;
+ * bytes / flops: algorithmic bytes and floating-point operations of one launch (the model is stated
+ * in the library's design notes).  The launches modify the level-L iterate: run a solve again before
+ * hhg_estimate. */
 hhg_status hhg_profile_kernel(hhg_mesh mesh, int kernel, int precision, int reps, long long* units,
                               double* bytes, double* flops);
 

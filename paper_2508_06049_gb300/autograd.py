@@ -1,14 +1,17 @@
 """torch.autograd wrapper of the adjoint FMG solve (no counterpart in the paper).
 
-`L2Functional.apply(f_L, k, mesh, in_S, params)` returns J(u) = u^T M_S u, the squared L2 norm of the
-level-L solution u over the macro cells flagged in `in_S`, where u solves the HHG system with nodal
-source f_L (level-L layout, one value per interface copy, equal copies) and per-cell coefficients k.
-Backward returns dJ/df_L and dJ/dk from one adjoint solve in the library (hhg_adjoint_l2): the
-forward solution is kept by the mesh, not stored by autograd, and recomputed only when the inputs
-change.
+`L2Functional.apply(f_L, k, mesh, in_S, params, g_L)` returns J(u) = u^T M_S u, the squared L2 norm of
+the level-L solution u over the macro cells flagged in `in_S`, where u solves the HHG system with
+source f_L (level-L layout, one value per interface copy) and per-cell coefficients k.
 
-The gradient with respect to f_L is the derivative with respect to the distinct nodal value, written
-to every interface copy of that node; summing over copies would double count.
+Gradients come from one adjoint solve in the library (hhg_adjoint_l2), run in forward only when
+f_L or k requires a gradient; otherwise forward evaluates J from the solution alone.  The forward
+solution is kept by the mesh, not stored by autograd.
+
+dJ/df_L is the derivative with respect to every entry of f_L: the library builds b_L = sum_T M_T f_T
+from each cell's own copy of an interface node, so copy p of cell T gets (M_T lambda)_p.  An
+upstream op that spreads nodal values to the copies (f_L = f_nodes[idx]) therefore sums the copies'
+shares into the nodal derivative (M_L lambda)_p.
 """
 
 from __future__ import annotations
@@ -32,11 +35,18 @@ class L2Functional(torch.autograd.Function):
         u = torch.empty_like(f)
         mesh.solve(params, out=u)
         mask = np.asarray(in_S, dtype=np.uint8)
-        grad_f = torch.empty_like(f)
-        J, _, grad_k = mesh.adjoint_l2(mask, params=params, grad_f=grad_f)
-        ctx.save_for_backward(grad_f, torch.from_numpy(grad_k))
         ctx.k_device = k.device
         ctx.k_dtype = k.dtype
+        if ctx.needs_input_grad[0] or ctx.needs_input_grad[1]:
+            grad_f = torch.empty_like(f)
+            J, _, grad_k = mesh.adjoint_l2(mask, params=params, grad_f=grad_f)
+            ctx.save_for_backward(grad_f, torch.from_numpy(grad_k))
+        else:
+            # no gradient wanted: J = sum over the flagged cells of u^T M_T u, from the solution alone
+            sq = torch.empty(mesh.n_cells, dtype=torch.float64, device=f.device)
+            mesh.cell_mass_norms_noalloc(u, None, sq)
+            mesh.synchronize()
+            J = float(sq.cpu().numpy()[mask.astype(bool)].sum())
         return torch.tensor(J, dtype=torch.float64, device=f.device)
 
     @staticmethod

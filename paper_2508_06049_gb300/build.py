@@ -20,7 +20,6 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 BUILD = os.path.join(HERE, "_build")
 LIBNAME = "libhhg.so"
-PEAK_PROBE = os.path.join(BUILD, "peak_probe")  # executable of peak_probe.cu (run by peaks.py)
 
 CUDA_SOURCES = ["setup.cu", "kernels.cu", "kernels_mixed.cu", "kernels_noalloc.cu", "capi.cu"]
 CXX_SOURCES = ["rg2d.cpp", "rg3d.cpp"]
@@ -53,8 +52,6 @@ def build(debug: bool = False, verbose: bool = False, check: bool = False) -> st
     for src in CUDA_SOURCES:
         obj = os.path.join(BUILD, src + ".o")
         jobs.append([nvcc] + ARCH + common + ["-c", os.path.join(CSRC, src), "-o", obj])
-    # the peak probe (a standalone program, not part of the library) is compiled alongside
-    jobs.append([nvcc] + ARCH + ["-O3", "-lineinfo", "-o", PEAK_PROBE, os.path.join(HERE, "peak_probe.cu")])
     cxx = shutil.which("g++") or "g++"
     for src in CXX_SOURCES:
         obj = os.path.join(BUILD, src + ".o")

@@ -32,6 +32,12 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
+// bulk prefetch of a global range into L2 (no completion to wait for); address 16-byte aligned,
+// size a multiple of 16
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // wait for completion of the barrier phase with the given parity; false after max_tries polls
 // (each poll may suspend the thread for a hardware-defined time)
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int max_tries) {

@@ -23,10 +23,13 @@ void launch_profile_face(hhg_mesh_s* m, int reps, cudaStream_t s, long long* uni
 void launch_profile_level(hhg_mesh_s* m, int kernel, int reps, cudaStream_t s, long long* units, double* bytes,
                           double* flops);
 hhg_status mixed_profile_interior(hhg_mesh_s* m, int reps, cudaStream_t s, long long* units, double* bytes,
-                                  double* flops, int variant = 0);
+                                  double* flops);
 hhg_status mixed_prepare(hhg_mesh_s* m, int storage);
 void mixed_enqueue_solve(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t s);
 void mixed_enqueue_adjoint(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t s);
+void mixed_sweeps(hhg_mesh_s* m, int l, int nsweeps, cudaStream_t s);
+void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+void launch_to_f64(const float* a, double* b, int64_t n, cudaStream_t s);
 }  // namespace hhg
 
 using namespace hhg;
@@ -96,6 +99,7 @@ hhg_status check_params(const hhg_mesh_s* m, const hhg_solve_params* p) {
   REQUIRE(p->pre >= 0 && p->pre <= 64 && p->post >= 0 && p->post <= 64, HHG_ERR_ARG, "pre/post in [0,64]");
   REQUIRE(p->n_extra >= 0 && p->n_extra <= 10000, HHG_ERR_ARG, "n_extra in [0,10000]");
   REQUIRE(p->precision == 0 || p->precision == 1, HHG_ERR_ARG, "precision must be 0 or 1");
+  REQUIRE(p->rhs == 0 || p->rhs == 1, HHG_ERR_ARG, "rhs must be 0 (injected f) or 1 (restricted from level L)");
   if (p->precision == 1) {
     REQUIRE(p->storage >= 0 && p->storage <= 2, HHG_ERR_ARG, "storage must be 0, 1 or 2");
     REQUIRE(p->ir_steps >= 0 && p->ir_steps <= 1000, HHG_ERR_ARG, "ir_steps in [0,1000]");
@@ -124,9 +128,11 @@ void enqueue_vcycle(hhg_mesh_s* m, int l, const double* rhs, const hhg_solve_par
 // coarser levels), zero Dirichlet data, w_l not stored.
 void enqueue_fmg(hhg_mesh_s* m, const hhg_solve_params& p, bool adjoint, cudaStream_t s) {
   const int L = m->L;
-  if (!adjoint) {
+  if (!adjoint && p.rhs == 0) {
     for (int l = 0; l <= L; ++l) launch_build_rhs(m, l, s);
   } else {
+    // b_L = M_L f_L (the adjoint's right-hand side is already in b_L), b_{l-1} = I^T b_l
+    if (!adjoint) launch_build_rhs(m, L, s);
     launch_restrict_rhs_chain(m, s);
   }
   const double* g = adjoint ? nullptr : m->gL;
@@ -142,8 +148,8 @@ void enqueue_fmg(hhg_mesh_s* m, const hhg_solve_params& p, bool adjoint, cudaStr
 
 std::string graph_key(const char* what, const hhg_solve_params& p) {
   char buf[160];
-  snprintf(buf, sizeof(buf), "%s:%d:%d:%d:%d:%d:%d:%d:%d", what, p.nu, p.pre, p.post, p.n_extra, p.precision,
-           p.storage, p.ir_steps, p.ir_vcycles);
+  snprintf(buf, sizeof(buf), "%s:%d:%d:%d:%d:%d:%d:%d:%d:%d", what, p.nu, p.pre, p.post, p.n_extra, p.precision,
+           p.storage, p.ir_steps, p.ir_vcycles, p.rhs);
   return buf;
 }
 
@@ -259,6 +265,13 @@ hhg_status hhg_mesh_destroy(hhg_mesh m) {
   cudaStreamSynchronize(m->stream);
   free_mesh(m);
   delete m;
+  return HHG_OK;
+}
+
+hhg_status hhg_mesh_synchronize(hhg_mesh m) {
+  REQUIRE(m, HHG_ERR_ARG, "mesh is NULL");
+  DeviceGuard g(m->device);
+  CK(cudaStreamSynchronize(m->stream));
   return HHG_OK;
 }
 
@@ -559,11 +572,15 @@ hhg_status hhg_get_vector(hhg_mesh m, int which, int level, double* out) {
 hhg_status hhg_apply(hhg_mesh m, int level, int op, const double* in, double* out, int nsweeps) {
   REQUIRE(m && in && out, HHG_ERR_ARG, "NULL argument");
   REQUIRE(level >= 0 && level <= m->L, HHG_ERR_ARG, "level out of range");
-  REQUIRE(op >= 0 && op <= 3, HHG_ERR_ARG, "op must be 0..3");
+  REQUIRE(op >= 0 && op <= 4, HHG_ERR_ARG, "op must be 0..4");
   REQUIRE(op != 2 || level >= 1, HHG_ERR_ARG, "interpolation needs level >= 1");
-  REQUIRE(op != 3 || (level >= 1 && nsweeps >= 0), HHG_ERR_ARG, "sweeps need level >= 1");
+  REQUIRE(op < 3 || (level >= 1 && nsweeps >= 0), HHG_ERR_ARG, "sweeps need level >= 1");
   DeviceGuard g(m->device);
   ENTER(m);
+  if (op == 4) {  // binary32 buffers of the mixed path before any work is queued
+    hhg_status st = mixed_prepare(m, m->mixed_alloc ? m->last_storage : 0);
+    if (st != HHG_OK) return st;
+  }
   cudaStream_t s = m->stream;
   LevelData& Lv = m->lv[level];
   size_t nin = (size_t)(op == 2 ? m->lv[level - 1].N : Lv.N);
@@ -580,12 +597,21 @@ hhg_status hhg_apply(hhg_mesh m, int level, int op, const double* in, double* ou
     launch_sum_interfaces(m, level, dout, s);
   } else if (op == 2) {
     launch_prolong(m, level, din, dout, s);
-  } else {
+  } else if (op == 3) {
     // rhs = M in (partial), initial guess from out, sweeps in place on the level's u
     launch_apply_op(m, level, 1, din, Lv.b, s);
     cudaMemcpyAsync(Lv.u, out, sizeof(double) * Lv.N, cudaMemcpyDefault, s);
     for (int q = 0; q < nsweeps; ++q) launch_sweep(m, level, Lv.b, s);
     cudaMemcpyAsync(dout, Lv.u, sizeof(double) * Lv.N, cudaMemcpyDeviceToDevice, s);
+    m->solved = false;
+  } else {
+    // the same in binary32 with the mixed path's smoother: rhs and initial guess rounded to binary32
+    launch_apply_op(m, level, 1, din, Lv.b, s);
+    launch_to_f32(Lv.b, Lv.b32, Lv.N, s);
+    cudaMemcpyAsync(dout, out, sizeof(double) * Lv.N, cudaMemcpyDefault, s);
+    launch_to_f32(dout, Lv.x32, Lv.N, s);
+    mixed_sweeps(m, level, nsweeps, s);
+    launch_to_f64(Lv.x32, dout, Lv.N, s);
     m->solved = false;
   }
   cudaMemcpyAsync(out, dout, sizeof(double) * Lv.N, cudaMemcpyDefault, s);
@@ -638,8 +664,9 @@ hhg_status hhg_adjoint_l2(hhg_mesh m, const hhg_solve_params* params, const unsi
   }
   if (st == HHG_OK) {
     if (grad_f) {
+      // dJ/df_L per entry of the level-L layout: b_L = sum_T M_T f_T reads each cell's own copy, so
+      // the derivative by copy p of cell T is (M_T lambda)_p, the partial (unsummed) mass product
       launch_apply_op(m, L, 1, LL.u, LL.tmp, s);
-      launch_sum_interfaces(m, L, LL.tmp, s);
       cudaMemcpyAsync(grad_f, LL.tmp, bytes, cudaMemcpyDefault, s);
     }
     std::vector<double> hk(nc);
@@ -676,18 +703,12 @@ hhg_status hhg_adjoint_l2(hhg_mesh m, const hhg_solve_params* params, const unsi
 hhg_status hhg_profile_kernel(hhg_mesh m, int kernel, int precision, int reps, long long* units, double* bytes,
                               double* flops) {
   REQUIRE(m && units && bytes && flops, HHG_ERR_ARG, "NULL argument");
-  REQUIRE(kernel >= 0 && kernel <= 6, HHG_ERR_ARG, "kernel must be 0 .. 6");
+  REQUIRE(kernel >= 0 && kernel <= 4, HHG_ERR_ARG, "kernel must be 0 .. 4");
   REQUIRE(precision == 0 || precision == 1, HHG_ERR_ARG, "precision must be 0 or 1");
   REQUIRE(reps >= 0 && reps <= 100000, HHG_ERR_ARG, "reps in [0, 100000]");
   DeviceGuard g(m->device);
   ENTER(m);
-  if (kernel == 5 || kernel == 6) {
-    REQUIRE(precision == 1, HHG_ERR_ARG, "probes 5 and 6 are binary32 interior-stage variants");
-    hhg_status st = mixed_prepare(m, m->mixed_alloc ? m->last_storage : 1);
-    if (st != HHG_OK) return st;
-    st = mixed_profile_interior(m, reps, m->stream, units, bytes, flops, kernel - 4);
-    if (st != HHG_OK) return st;
-  } else if (kernel >= 2) {
+  if (kernel >= 2) {
     REQUIRE(precision == 0, HHG_ERR_ARG, "the level probes 2 .. 4 are binary64");
     REQUIRE(m->L >= 1, HHG_ERR_ARG, "the level probes need L >= 1");
     launch_profile_level(m, kernel, reps, m->stream, units, bytes, flops);

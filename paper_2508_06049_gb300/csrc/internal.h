@@ -42,12 +42,13 @@ struct Prims {
   float* d_fwf = nullptr;
 };
 
-// nodes of the u window (planes k0-1 .. k1+1) of one staged interior tile, at most (a single plane
-// range may exceed it)
-constexpr int64_t kTileNodes = 8192;
-// dynamic shared memory a staged CTA may use (tiles beyond it fall back to the list kernel)
+// threads per block of the node-parallel kernels (and of the per-cell reductions' block sums)
+constexpr int kBlock = 256;
+// dynamic shared memory a CTA of the face block or the fused interior sweep may use (larger levels
+// take the global-memory or list variants)
 constexpr size_t kMaxTileSmem = 200 * 1024;
-// spare values past the last node of every vector the staged kernel reads
+// spare values past the last node of every binary32 / 16-bit vector (the fused sweep's bulk copies
+// read 16-byte windows that may end past a cell's last node)
 constexpr int64_t kVecPad = 16;
 
 struct LevelData {
@@ -58,13 +59,10 @@ struct LevelData {
   // (packed local index, j | k << 16)
   std::vector<std::vector<int64_t>> icol_off;
   int2* d_icol = nullptr;
-  // staged interior stage (3D): plane-range tiles {k0, k1, lo, hi} of group g, colour c at
-  // d_tiles[tile_off[g][c] .. + nranges); tile_smem4: largest shared memory (u and list windows) of
-  // one tile with 4-byte values
-  std::vector<std::vector<int64_t>> tile_off;
-  int nranges = 0;
-  int4* d_tiles = nullptr;
-  size_t tile_smem4 = 0;
+  // 3D: per group g, table [colour][plane k = 0 .. n+1] of the first colour-list entry (relative to
+  // the group's first entry) in planes >= k, at d_pcol + pcol_off[g] (the fused interior sweep)
+  std::vector<int64_t> pcol_off;
+  int* d_pcol = nullptr;
   // boundary-type closure nodes (type != 0), sorted by type: (packed local index, i | j << 10 | k << 20)
   int2* d_bnd = nullptr;
   int64_t nbnd = 0;

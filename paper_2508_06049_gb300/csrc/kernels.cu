@@ -8,22 +8,18 @@
 
 namespace hhg {
 
-// One block per cell: deterministic shared-memory tree sum of the cell's np node contributions.
-__global__ void __launch_bounds__(256) k_cell_sum(int64_t np, double scale, const double* __restrict__ part,
-                                                  double* __restrict__ out) {
+// One block per cell: the cell's np block sums (from k_node_form) added in a fixed order (strided
+// per-thread sums, then block_sum_fixed).
+__global__ void __launch_bounds__(kBlock) k_cell_sum(int64_t np, double scale, const double* __restrict__ part,
+                                                     double* __restrict__ out) {
   grid_dependency_sync();
-  __shared__ double sh[256];
+  __shared__ double wsum[kBlock / 32];
   int T = blockIdx.x;
   const double* c = part + (int64_t)T * np;
   double acc = 0;
-  for (int64_t q = threadIdx.x; q < np; q += 256) acc += c[q];
-  sh[threadIdx.x] = acc;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[T] = scale * sh[0];
+  for (int64_t q = threadIdx.x; q < np; q += kBlock) acc += c[q];
+  const double tot = block_sum_fixed(acc, wsum);
+  if (threadIdx.x == 0) out[T] = scale * tot;
 }
 
 // x = a - b elementwise
@@ -79,8 +75,26 @@ void launch_build_rhs(hhg_mesh_s* m, int l, cudaStream_t s) {
   dim3 grid(blocks_for(Lv.Nt), m->nc);
   double ms = mass_scale(m->dim, Lv.n);
   const LevelData& LL = m->lv[m->L];
-  DISPATCH_DIM(m, k_build_rhs, grid, kBlock, 0, s, ctx(m, l), LL.n, LL.Nt, m->L - l, m->fL, m->dM, ms,
-                                                       m->d_dirmask, Lv.b);
+  if (m->dim == 2)
+    hhg_launch(k_build_rhs<2, double, double>, grid, kBlock, 0, s, ctx(m, l), LL.n, LL.Nt, m->L - l, m->fL,
+               (const double*)m->dM, ms, (const uint16_t*)m->d_dirmask, Lv.b);
+  else
+    hhg_launch(k_build_rhs<3, double, double>, grid, kBlock, 0, s, ctx(m, l), LL.n, LL.Nt, m->L - l, m->fL,
+               (const double*)m->dM, ms, (const uint16_t*)m->d_dirmask, Lv.b);
+}
+
+// the same in binary32 (binary32 mass stencils and arithmetic) into the level's binary32 rhs b32
+void launch_build_rhs32(hhg_mesh_s* m, int l, cudaStream_t s) {
+  const LevelData& Lv = m->lv[l];
+  dim3 grid(blocks_for(Lv.Nt), m->nc);
+  float ms = (float)mass_scale(m->dim, Lv.n);
+  const LevelData& LL = m->lv[m->L];
+  if (m->dim == 2)
+    hhg_launch(k_build_rhs<2, float, float>, grid, kBlock, 0, s, ctx(m, l), LL.n, LL.Nt, m->L - l, m->fL,
+               (const float*)m->dM32, ms, (const uint16_t*)m->d_dirmask, Lv.b32);
+  else
+    hhg_launch(k_build_rhs<3, float, float>, grid, kBlock, 0, s, ctx(m, l), LL.n, LL.Nt, m->L - l, m->fL,
+               (const float*)m->dM32, ms, (const uint16_t*)m->d_dirmask, Lv.b32);
 }
 
 void launch_build_rhs_restricted(hhg_mesh_s* m, cudaStream_t s);
@@ -282,7 +296,7 @@ void launch_finite_check(hhg_mesh_s* m, const double* v, int64_t n, cudaStream_t
 static void cell_form(hhg_mesh_s* m, bool diff, const double* tab, double scale, const double* a, const double* b,
                       double* out, cudaStream_t s) {
   const LevelData& Lv = m->lv[m->L];
-  double* contrib = m->d_part;  // N_L doubles of scratch
+  double* contrib = m->d_part;  // one block sum per cell and block of k_node_form
   dim3 grid(blocks_for(Lv.Nt), m->nc);
   if (diff) {
     if (m->dim == 2) hhg_launch(k_node_form<2, true>, grid, kBlock, 0, s, ctx(m, m->L), tab, a, b, contrib);
@@ -291,7 +305,7 @@ static void cell_form(hhg_mesh_s* m, bool diff, const double* tab, double scale,
     if (m->dim == 2) hhg_launch(k_node_form<2, false>, grid, kBlock, 0, s, ctx(m, m->L), tab, a, b, contrib);
     else hhg_launch(k_node_form<3, false>, grid, kBlock, 0, s, ctx(m, m->L), tab, a, b, contrib);
   }
-  hhg_launch(k_cell_sum, m->nc, 256, 0, s, Lv.Nt, scale, contrib, out);
+  hhg_launch(k_cell_sum, m->nc, kBlock, 0, s, (int64_t)grid.x, scale, contrib, out);
 }
 
 void launch_mass_norm_sq(hhg_mesh_s* m, const double* a, const double* b, double* out, cudaStream_t s) {
@@ -412,7 +426,7 @@ void launch_profile_interior(hhg_mesh_s* m, int precision, int reps, cudaStream_
 hhg_status preload_kernels() {
   cudaFuncAttributes fa;
   const void* fns[] = {
-      (const void*)k_build_rhs<2>, (const void*)k_build_rhs<3>, (const void*)k_init_coarse<2>,
+      (const void*)k_build_rhs<2, double, double>, (const void*)k_build_rhs<3, double, double>, (const void*)k_init_coarse<2>,
       (const void*)k_init_coarse<3>, (const void*)k_fmg_prolong<2>, (const void*)k_fmg_prolong<3>,
       (const void*)k_prolong<2>, (const void*)k_prolong<3>, (const void*)k_coarse<2>, (const void*)k_coarse<3>,
       (const void*)k_node_form<2, true>, (const void*)k_node_form<3, true>, (const void*)k_node_form<2, false>,

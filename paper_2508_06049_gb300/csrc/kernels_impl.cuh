@@ -13,7 +13,6 @@
 namespace hhg {
 
 
-constexpr int kBlock = 256;
 
 inline double stiff_scale(int d, int n) { return d == 2 ? 1.0 : 1.0 / (double)n; }
 inline double mass_scale(int d, int n) {
@@ -91,11 +90,13 @@ __device__ __forceinline__ int64_t copy_terms(const R* __restrict__ S, const uin
 
 // ---------------------------------------------------------------- right-hand sides b_l = M_l f_l (Eq. 4.15, Sec. 4.4)
 
-// b_l = M_l f_l (partial per cell), f_l injected from the level-L data; zero on Dirichlet rows
-template <int DIM>
+// b_l = M_l f_l (partial per cell), f_l injected from the level-L data; zero on Dirichlet rows.
+// R: the arithmetic and mass-stencil type (binary64, or binary32 for the coarse right-hand sides of
+// the mixed path's binary32 FMG), O: the stored type.
+template <int DIM, typename R, typename O>
 __global__ void k_build_rhs(LevelCtx lc, int nL, int64_t NtL, int shift, const double* __restrict__ fL,
-                            const double* __restrict__ Mst, double mscale, const uint16_t* __restrict__ dirmask,
-                            double* __restrict__ b) {
+                            const R* __restrict__ Mst, R mscale, const uint16_t* __restrict__ dirmask,
+                            O* __restrict__ b) {
   grid_dependency_sync();
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (loc >= lc.Nt) return;
@@ -105,20 +106,20 @@ __global__ void k_build_rhs(LevelCtx lc, int nL, int64_t NtL, int shift, const d
   int t = boundary_type(DIM, lc.n, i, j, k);
   int64_t g = (int64_t)T * lc.Nt + loc;
   if (dirmask[T] >> t & 1) {
-    b[g] = 0.0;
+    b[g] = (O)0;
     return;
   }
   uint32_t vm = valid_dirs_tab(DIM, t);
-  const double* s = Mst + (size_t)T * kStencilStride + t * kMaxDirs;
+  const R* s = Mst + (size_t)T * kStencilStride + t * kMaxDirs;
   const double* f = fL + (int64_t)T * NtL;
-  double acc = 0;
+  R acc = 0;
   if (shift == 0) {  // level L itself: the level's own neighbour offsets
     int64_t off[15];
     neighbour_offsets(DIM, lc.n, j, k, off);
     mask_offsets(DIM, vm, off);
 #pragma unroll
     for (int d = 0; d < ndirs<DIM>(); ++d)
-      if ((vm >> d & 1) && !HHG_OOB(loc + off[d], NtL, 71)) acc += s[d] * f[loc + off[d]];
+      if ((vm >> d & 1) && !HHG_OOB(loc + off[d], NtL, 71)) acc += s[d] * (R)f[loc + off[d]];
   } else {
 #pragma unroll
     for (int d = 0; d < ndirs<DIM>(); ++d) {
@@ -128,10 +129,10 @@ __global__ void k_build_rhs(LevelCtx lc, int nL, int64_t NtL, int shift, const d
       int64_t q = packed_index(DIM, nL, (int64_t)(i + di) << shift, (int64_t)(j + dj) << shift,
                                (int64_t)(k + dk) << shift);
       if (HHG_OOB(q, NtL, 71)) continue;
-      acc += s[d] * f[q];
+      acc += s[d] * (R)f[q];
     }
   }
-  b[g] = mscale * acc;
+  b[g] = (O)(mscale * acc);
 }
 
 // u_0 = g on Dirichlet nodes, 0 elsewhere
@@ -238,85 +239,8 @@ __global__ void __launch_bounds__(kBlock) k_smooth_interior_multi(const int* __r
     if (c0 + c < ncells) u.set(g[c], acc[c]);
 }
 
-// The same interior colour stage (3D) with the cell's u values staged in shared memory.  One CTA
-// takes one plane range [k0, k1] of one cell (tile = {k0, k1, lo, hi}): the u planes k0-1 .. k1+1
-// are contiguous in the packed layout and the colour's list entries of those planes are the
-// contiguous list range [lo, hi); two bulk asynchronous copies (16-byte aligned windows around
-// them) bring both in, completing on one mbarrier, and the update reads its neighbours from shared
-// memory (b at the updated node from global memory).  Neighbouring CTAs copy each other's
-// boundary planes while those CTAs write their own colour's nodes there; a proper colouring means
-// such values are never used.  The vectors read here carry 16 bytes of padding past their last
-// node.  A copy that does not complete within the bounded wait sets *err and the CTA returns
-// without updating.
+// bounded waits of the bulk-copy pipelines: polls of mbarrier.try_wait before giving up
 constexpr int kBulkWaitTries = 1 << 20;
-
-template <int PM, typename R>
-__global__ void __launch_bounds__(kBlock) k_smooth_interior_tiled(const int* __restrict__ gcells, LevelCtx lc,
-                                                                  const int4* __restrict__ tiles,
-                                                                  const int2* __restrict__ list,
-                                                                  const R* __restrict__ tnorm,
-                                                                  const R* __restrict__ invl, R* u,
-                                                                  const R* __restrict__ b, int* err) {
-  grid_dependency_sync();
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int4 tl = tiles[blockIdx.x];
-  if (tl.w <= tl.z) return;  // no node of this colour in the range (uniform across the CTA)
-  const int T = gcells[blockIdx.y];
-  const int n = lc.n;
-  const int64_t cell0 = (int64_t)T * lc.Nt;
-  const int64_t tn = tet_size(n);
-  const int64_t ua = tn - tet_size(n - tl.x + 1), ue = tn - tet_size(n - tl.y - 2);
-  const uintptr_t gu0 = (uintptr_t)(u + cell0 + ua), gl0 = (uintptr_t)(list + tl.z);
-  const uintptr_t au = gu0 & ~(uintptr_t)15, al = gl0 & ~(uintptr_t)15;
-  const uint32_t nu = (uint32_t)((((uintptr_t)(u + cell0 + ue) - au) + 15) & ~(uintptr_t)15);
-  const uint32_t nl = (uint32_t)((((uintptr_t)(list + tl.w) - al) + 15) & ~(uintptr_t)15);
-  R* su = (R*)(smem + 16);
-  int2* sl = (int2*)(smem + 16 + nu);
-  const uint32_t bar = smem_addr(smem);
-  if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    mbar_arrive_expect_tx(bar, nu + nl);
-    bulk_g2s(smem_addr(su), (const void*)au, nu, bar);
-    bulk_g2s(smem_addr(sl), (const void*)al, nl, bar);
-  }
-  __syncthreads();
-  // the outcome of the bounded wait is made uniform across the CTA before anyone acts on it
-  const int ok = __syncthreads_and(mbar_wait_bounded(bar, 0, kBulkWaitTries));
-  if (!ok) {
-    if (threadIdx.x == 0) atomicOr(err, 1);
-    mbar_wait_bounded(bar, 0, kBulkWaitTries);  // let copies in flight land before the CTA exits
-    return;
-  }
-  const int upad = (int)((gu0 - au) / sizeof(R));
-  const int lpad = (int)((gl0 - al) / sizeof(int2));
-  const R* t = tnorm + (size_t)T * 16;
-  R tv[15];
-#pragma unroll
-  for (int d = 1; d < 15; ++d) tv[d] = ((PM >> ((d - 1) >> 1)) & 1) ? t[d] : (R)0;
-  const R il = invl[T];
-  for (int e = threadIdx.x; e < tl.w - tl.z; e += blockDim.x) {
-    int2 en = sl[lpad + e];
-    int q = en.x, j = en.y & 0xffff, k = en.y >> 16;
-    int64_t off[15];
-    neighbour_offsets(3, n, j, k, off);
-    int c = upad + (int)(q - ua);
-#ifdef HHG_CHECK
-    bool bad = HHG_OOB(c, (int64_t)(nu / sizeof(R)), 43);
-    for (int d = 1; d < 15; ++d)
-      if ((PM >> ((d - 1) >> 1)) & 1) bad |= HHG_OOB(c + off[d], (int64_t)(nu / sizeof(R)), 44);
-    if (bad) continue;
-#endif
-    R acc = b[cell0 + q] * il;
-#pragma unroll
-    for (int qq = 0; qq < 7; ++qq) {
-      if (PM >> qq & 1) {
-        acc -= tv[2 * qq + 1] * su[c + off[2 * qq + 1]];
-        acc -= tv[2 * qq + 2] * su[c + off[2 * qq + 2]];
-      }
-    }
-    u[cell0 + q] = acc;
-  }
-}
 
 // macro vertices: never coupled to each other on levels >= 1, so one pass.  One warp per vertex,
 // lanes over the vertex's cell copies (scattered loads in parallel), fixed-order shuffle sums.
@@ -1086,19 +1010,38 @@ __global__ void __launch_bounds__(1024) k_coarse(int n0f, const int* __restrict_
 
 // ---------------------------------------------------------------- reductions (ErrorEstimate of Alg. 4, Eqs. 4.5 and 4.14; adjoint gradients)
 
+// Fixed-order sum of one value per thread over a block of kBlock threads: xor butterflies inside each
+// warp, then the warp sums combined by the first warp with butterflies over kBlock / 32 lanes.  Every
+// thread of the block must call it (no thread may have returned); thread 0 gets the sum.  The order
+// of the additions depends on the thread index only, so the result is the same on every run.
+__device__ __forceinline__ double block_sum_fixed(double v, double* wsum) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < kBlock / 32 ? wsum[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = kBlock / 64; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;
+}
+
 // Per node p of a cell's closure (one node per thread, one grid row per cell), the symmetric-form
-// contribution (written to part[cell][node]):
+// contribution
 //   c_p = S[t][0] x_p y_p + sum_{d positive, valid} S[t][d] (x_p y_{p+d} + x_{p+d} y_p),
 // with x = y = a - b (b may be null) for the mass form, or x = a, y = b for a bilinear form.  Summed
 // over the closure this is x^T S_T y, because the partial stencil of a cell is symmetric (the entry
 // p->p+d seen from p equals the entry p+d->p seen from p+d: both sum the cell's elements on that
-// edge), so each lattice edge is visited once.  k_cell_sum adds each cell's contributions in a fixed
-// order.
+// edge), so each lattice edge is visited once.  Each block sums its nodes' contributions in a fixed
+// order (block_sum_fixed) into part[cell][block]; k_cell_sum adds a cell's block sums.
 template <int DIM, bool DIFF>
 __global__ void __launch_bounds__(kBlock) k_node_form(LevelCtx lc, const double* __restrict__ tab,
                                                       const double* __restrict__ a, const double* __restrict__ b,
                                                       double* __restrict__ part) {
   grid_dependency_sync();
+  __shared__ double wsum[kBlock / 32];
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int T = blockIdx.y;
   double sum = 0;
@@ -1139,8 +1082,9 @@ __global__ void __launch_bounds__(kBlock) k_node_form(LevelCtx lc, const double*
       }
     }
     sum = DIFF ? xp * (s[0] * xp + 2.0 * ay) : xp * (s[0] * yp + ay) + yp * ax;
-    part[(int64_t)T * lc.Nt + loc] = sum;
   }
+  const double tot = block_sum_fixed(sum, wsum);
+  if (threadIdx.x == 0) part[(int64_t)T * gridDim.x + blockIdx.x] = tot;
 }
 
 // ---------------------------------------------------------------- operators for testing / adjoint

@@ -94,6 +94,24 @@ extern "C" hhg_status hhg_cell_mass_norms_noalloc(hhg_mesh m, const double* a, c
     set_error("hhg_cell_mass_norms_noalloc: device index %d beyond %d", dev, kMaxDevices);
     return HHG_ERR_ARG;
   }
+#ifdef HHG_CHECK
+  // checked build: every pointer must be device memory of the mesh's device (allocates nothing)
+  {
+    const void* ptrs[3] = {a, b, out};
+    const char* names[3] = {"a", "b", "out"};
+    for (int q = 0; q < 3; ++q) {
+      if (!ptrs[q]) continue;
+      cudaPointerAttributes pa;
+      cudaError_t pe = cudaPointerGetAttributes(&pa, ptrs[q]);
+      if (pe != cudaSuccess || pa.type != cudaMemoryTypeDevice || pa.device != m->device) {
+        cudaGetLastError();
+        set_error("hhg_cell_mass_norms_noalloc: %s = %p is not device memory of device %d", names[q], ptrs[q],
+                  m->device);
+        return HHG_ERR_STATE;
+      }
+    }
+  }
+#endif
   const LevelData& Lv = m->lv[m->L];
   // chunks of items * 256 nodes per cell such that all partials fit the static scratch
   int64_t per_cell_max = kNoAllocScratch / m->nc;

@@ -743,41 +743,30 @@ hhg_status build_mesh(hhg_mesh_s* m, const double* coords, const int* cells, con
         Lv.icol_off[g].push_back((int64_t)icol.size());
       }
     }
-    // plane-range tiles of the staged interior stage (3D): consecutive interior planes
-    // k = 1 .. n-3, as many per tile as keep its u window (planes k0-1 .. k1+1) within kTileNodes
-    Lv.tile_off.assign(m->groups.size(), {});
-    std::vector<int4> tiles;
-    if (d == 3 && Lv.n >= 4) {
-      const int n = Lv.n;
-      auto P = [&](int k) { return tet_size(n) - tet_size(n - k); };
-      std::vector<std::pair<int, int>> ranges;
-      for (int k0 = 1; k0 <= n - 3;) {
-        int k1 = k0;
-        while (k1 + 1 <= n - 3 && P(k1 + 3) - P(k0 - 1) <= kTileNodes) ++k1;
-        ranges.push_back({k0, k1});
-        k0 = k1 + 1;
-      }
-      Lv.nranges = (int)ranges.size();
-      auto r16 = [](int64_t bytes) { return (size_t)((bytes + 32 + 15) & ~(int64_t)15); };
-      for (size_t g = 0; g < m->groups.size(); ++g)
-        for (int c = 0; c < m->groups[g].m; ++c) {
-          Lv.tile_off[g].push_back((int64_t)tiles.size());
-          auto b0 = icol.begin() + Lv.icol_off[g][c], b1 = icol.begin() + Lv.icol_off[g][c + 1];
-          auto by_q = [](const int2& e, int64_t q) { return (int64_t)e.x < q; };
-          for (auto& r : ranges) {
-            int64_t lo = std::lower_bound(b0, b1, P(r.first), by_q) - icol.begin();
-            int64_t hi = std::lower_bound(b0, b1, P(r.second + 1), by_q) - icol.begin();
-            tiles.push_back(make_int4(r.first, r.second, (int)lo, (int)hi));
-            size_t sm = r16(4 * (P(r.second + 2) - P(r.first - 1))) + r16(8 * (hi - lo));
-            Lv.tile_smem4 = std::max(Lv.tile_smem4, sm);
+    if ((st = upload(m, &Lv.d_icol, icol)) != HHG_OK) return st;
+    // plane ranges of the colour lists (3D, fused interior sweep): for group g, colour c and plane k
+    // = 0 .. n+1, the first entry of the colour-c list whose node lies in plane >= k, relative to the
+    // group's first entry; table [c][k] at d_pcol + pcol_off[g]
+    {
+      std::vector<int> pcol;
+      Lv.pcol_off.assign(m->groups.size(), 0);
+      if (d == 3) {
+        const int n = Lv.n;
+        for (size_t g = 0; g < m->groups.size(); ++g) {
+          Lv.pcol_off[g] = (int64_t)pcol.size();
+          for (int c = 0; c < m->groups[g].m; ++c) {
+            auto b0 = icol.begin() + Lv.icol_off[g][c], b1 = icol.begin() + Lv.icol_off[g][c + 1];
+            for (int k = 0; k <= n + 1; ++k) {
+              const int64_t P = k <= n ? tet_size(n) - tet_size(n - k) : tet_size(n);
+              auto it = std::lower_bound(b0, b1, P, [](const int2& e, int64_t q) { return (int64_t)e.x < q; });
+              pcol.push_back((int)(it - icol.begin() - Lv.icol_off[g][0]));
+            }
           }
         }
+      }
+      if (pcol.empty()) pcol.push_back(0);
+      if ((st = upload(m, &Lv.d_pcol, pcol)) != HHG_OK) return st;
     }
-    if ((st = upload(m, &Lv.d_tiles, tiles)) != HHG_OK) return st;
-    // two spare entries: the staged stage copies 16-byte windows that may end past the last entry
-    icol.push_back(make_int2(0, 0));
-    icol.push_back(make_int2(0, 0));
-    if ((st = upload(m, &Lv.d_icol, icol)) != HHG_OK) return st;
     // boundary-type nodes, sorted by type (stable: packed order inside a type)
     std::vector<std::pair<int, int64_t>> bt;
     for (int64_t q = 0; q < Lv.Nt; ++q) {
@@ -815,8 +804,8 @@ hhg_status build_mesh(hhg_mesh_s* m, const double* coords, const int* cells, con
     if ((st = dalloc(m, &m->lv[l].w, m->lv[l + 1].N)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->fL, m->lv[L].N)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->gL, m->lv[L].N)) != HHG_OK) return st;
-  // reduction scratch: one value per level-L node
-  m->part_len = m->lv[L].N;
+  // reduction scratch: one block sum per cell and block of the level-L per-cell forms
+  m->part_len = (int64_t)nc * ((m->lv[L].Nt + kBlock - 1) / kBlock);
   if ((st = dalloc(m, &m->d_part, (size_t)m->part_len)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->d_red, (size_t)nc * 4)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->d_flag, 4)) != HHG_OK) return st;
@@ -865,7 +854,7 @@ void free_mesh(hhg_mesh_s* m) {
   for (auto& g : m->groups) F(g.d_cells);
   F(m->d_Ainv); F(m->d_cf_vert); F(m->d_rmax); F(m->d_ainv_inf);
   for (auto& Lv : m->lv) {
-    F(Lv.d_ijk); F(Lv.d_icol); F(Lv.d_bnd); F(Lv.d_tiles); F(Lv.d_invl); F(Lv.d_invlf); F(Lv.d_fcol); F(Lv.u); F(Lv.b); F(Lv.rc); F(Lv.w); F(Lv.tmp);
+    F(Lv.d_ijk); F(Lv.d_icol); F(Lv.d_pcol); F(Lv.d_bnd); F(Lv.d_invl); F(Lv.d_invlf); F(Lv.d_fcol); F(Lv.u); F(Lv.b); F(Lv.rc); F(Lv.w); F(Lv.tmp);
     F(Lv.c16); F(Lv.r32); F(Lv.t32); F(Lv.cscale); F(Lv.x32); F(Lv.b32);
   }
   F(m->fL); F(m->gL); F(m->d_part); F(m->d_red); F(m->d_flag); F(m->d_err); F(m->d_face_work); F(m->d_scal32);

@@ -29,7 +29,7 @@ class HHGError(RuntimeError):
 class SolveParams(C.Structure):
     _fields_ = [("nu", C.c_int), ("pre", C.c_int), ("post", C.c_int), ("n_extra", C.c_int),
                 ("precision", C.c_int), ("storage", C.c_int), ("ir_steps", C.c_int),
-                ("ir_vcycles", C.c_int)]
+                ("ir_vcycles", C.c_int), ("rhs", C.c_int)]
 
 
 class MeshInfo(C.Structure):
@@ -59,6 +59,7 @@ def lib():
         "hhg_mesh_create": [i, i, vp, i, vp, vp, i, vp, C.POINTER(vp)],
         "hhg_mesh_destroy": [vp],
         "hhg_mesh_get_info": [vp, C.POINTER(MeshInfo)],
+        "hhg_mesh_synchronize": [vp],
         "hhg_level_coords": [vp, i, vp],
         "hhg_set_coefficient": [vp, vp],
         "hhg_set_data": [vp, vp, vp],
@@ -116,8 +117,8 @@ def _f64(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
 
 
-def solve_params(nu=2, pre=2, post=1, n_extra=0, precision=0, storage=1, ir_steps=0, ir_vcycles=2):
-    return SolveParams(nu, pre, post, n_extra, precision, storage, ir_steps, ir_vcycles)
+def solve_params(nu=2, pre=2, post=1, n_extra=0, precision=0, storage=1, ir_steps=0, ir_vcycles=2, rhs=0):
+    return SolveParams(nu, pre, post, n_extra, precision, storage, ir_steps, ir_vcycles, rhs)
 
 
 class Mesh:
@@ -146,6 +147,10 @@ class Mesh:
             self.close()
         except Exception:
             pass
+
+    def synchronize(self):
+        """Wait for the work queued on the mesh's stream (hhg_mesh_synchronize)."""
+        _check(lib().hhg_mesh_synchronize(self._h))
 
     def get_info(self):
         info = MeshInfo()
@@ -214,7 +219,21 @@ class Mesh:
 
     def cell_mass_norms_noalloc(self, a, b, out):
         """(a-b)^T M_T (a-b) per cell into the device tensor `out` without allocating (queued on the
-        mesh stream, not synchronised); a, b, out are CUDA tensors."""
+        mesh stream, not synchronised).  a, b (b may be None): CUDA float64 contiguous tensors of N_L
+        entries; out: CUDA float64 contiguous, one entry per macro cell; all on the mesh's device."""
+        n = self.n_nodes(self.L)
+        dev = None
+        for name, t, size in (("a", a, n), ("b", b, n), ("out", out, self.n_cells)):
+            if t is None and name == "b":
+                continue
+            if isinstance(t, np.ndarray) or not getattr(t, "is_cuda", False):
+                raise ValueError("%s must be a CUDA tensor" % name)
+            if str(t.dtype) != "torch.float64" or not t.is_contiguous() or t.numel() != size:
+                raise ValueError("%s must be a contiguous float64 tensor of %d entries" % (name, size))
+            if dev is None:
+                dev = t.device
+            elif t.device != dev:
+                raise ValueError("a, b and out must be on the same device")
         _check(lib().hhg_cell_mass_norms_noalloc(self._h, _ptr(a), _ptr(b), _ptr(out)))
         return out
 

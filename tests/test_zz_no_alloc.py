@@ -40,8 +40,13 @@ def test_noalloc_mass_norms_match_estimator(name, L):
     eta = mesh.estimate(1)["eta_T"]
     ref = eta ** 2
     for call in range(2):
+        allocated = torch.cuda.memory_allocated()
+        free_before = torch.cuda.mem_get_info()[0]
         mesh.cell_mass_norms_noalloc(u, w, out)
         s.synchronize()
+        if call == 1:  # after the first call (kernel loading, symbol look-up) nothing is allocated
+            assert torch.cuda.mem_get_info()[0] == free_before
+        assert torch.cuda.memory_allocated() == allocated
         got = out.cpu().numpy()
         assert np.all(np.isfinite(got))
         assert np.abs(got - ref).max() <= TOL * ref.max(), call
@@ -53,4 +58,12 @@ def test_noalloc_mass_norms_match_estimator(name, L):
     mesh.cell_mass_norms_noalloc(u, zero, out)
     s.synchronize()
     assert np.abs(a_only - out.cpu().numpy()).max() <= TOL * a_only.max()
+    # the binding rejects arguments the kernel would read out of bounds
+    with torch.cuda.stream(s):
+        bad = [u.float(), u[:-1], out[:-1].contiguous()]
+    for a_, o_ in ((bad[0], out), (bad[1], out), (u, bad[2])):
+        with pytest.raises(ValueError):
+            mesh.cell_mass_norms_noalloc(a_, None, o_)
+    with pytest.raises(ValueError):
+        mesh.cell_mass_norms_noalloc(u.cpu(), None, out)
     mesh.close()

@@ -241,7 +241,9 @@ def _zero(x):
 
 
 def _one(x):
-    return np.ones(x.shape[0])
+    if isinstance(x, np.ndarray):
+        return np.ones(x.shape[0])
+    return x.new_ones(x.shape[0])
 
 
 # name -> (mesh builder, finest level L, f, g, coefficient builder or None, exact u or None)
