@@ -59,7 +59,7 @@ def parse():
                          "effectivity: the estimator study of Sec. 5.3 (kl loops with K = 10, j = 1..4, nu = 6 and 2); "
                          "kl_compare: uniform vs Alg. 1 vs Alg. 2 refinement (Sec. 5.1-5.2, final error and rho)")
     ap.add_argument("--workload", default=None, help="default cube384_l6 (step) or waves3d_l8 (alg5)")
-    ap.add_argument("--level", type=int, default=None, help="--program alg5 / effectivity: override the finest level L")
+    ap.add_argument("--level", type=int, default=None, help="override the workload's finest level L")
     ap.add_argument("--rhs", type=int, default=0, choices=[0, 1],
                     help="coarse right-hand sides: 0 = M_l f_l with f at the level-l nodes, 1 = restricted from "
                          "b_L (--program effectivity / kl_compare)")
@@ -288,7 +288,7 @@ class Setup:
         self.dev = int(os.environ.get("LOCAL_RANK", "0"))
         torch.cuda.set_device(self.dev)
         self.s = torch.cuda.Stream()
-        co, ce, L, f, g, k, ue = make_problem(args.workload)
+        co, ce, L, f, g, k, ue = make_problem(args.workload, args.level)
         self.mesh = P.Mesh(co, ce, L, stream=self.s)
         if k is not None:
             self.mesh.set_coefficient(k)
@@ -422,6 +422,7 @@ def run_arm(args, rank, world, su, precision, search):
     units, kbytes, kflops = mesh.profile_kernel(0, prec_id, reps)
     k1.record(s)
     torch.cuda.synchronize()
+    mesh.synchronize()  # raises if a bounded wait ran out in the profiled launches
     ms_k = k0.elapsed_time(k1) / reps
     gbs = kbytes / (ms_k * 1e-3) / 1e9
     tfl = kflops / (ms_k * 1e-3) / 1e12
@@ -925,7 +926,7 @@ def main():
     config = {"workload": args.workload, "macro_cells": None, "L": None, "precision": args.precision,
               "cycle": "FMG nu=2 V(2,1), estimator j=1, marking 12.5%",
               "l2": "level-L vectors exceed the 129 MB L2 (no flush needed)"}
-    co, ce, L, *_ = make_problem(args.workload)
+    co, ce, L, *_ = make_problem(args.workload, args.level)
     config["macro_cells"] = int(len(ce))
     config["L"] = int(L)
     if args.impl == "reference":

@@ -50,7 +50,7 @@ typedef enum {
   HHG_ERR_NOT_CONVERGED = 5,  /* an iteration did not reach its target                      */
   HHG_ERR_DIVERGED = 6,       /* NaN/Inf or growth detected in the solution                 */
   HHG_ERR_STATE = 7,          /* call order violated (e.g. estimate before a solve)         */
-  HHG_ERR_TIMEOUT = 8         /* a bounded device-side wait ran out (results invalid)       */
+  HHG_ERR_TIMEOUT = 8         /* reserved: no kernel of this version waits on other blocks  */
 } hhg_status;
 
 /* Solve parameters (Alg. 4).  nu: V-cycles per FMG level; pre/post: Gauss-Seidel sweeps
@@ -138,10 +138,9 @@ hhg_status hhg_set_coefficient(hhg_mesh mesh, const double* k_per_cell);
  * value per interface copy, equal copies).  Copied on the mesh's stream. */
 hhg_status hhg_set_data(hhg_mesh mesh, const double* f_L, const double* g_L);
 
-/* FMG solve (Alg. 4): b_l = M_l f_l on every level, FMG with the given parameters, w_l kept
- * for hhg_estimate.  u_L: host or device, N_L doubles (output).  Returns HHG_ERR_DIVERGED
- * if the result holds NaN/Inf, HHG_ERR_TIMEOUT if a kernel's bounded wait for its asynchronous
- * shared-memory copies ran out (the flag is cleared; the mesh stays usable). */
+/* FMG solve (Alg. 4): the right-hand sides of every level (params->rhs), FMG with the given
+ * parameters, w_l kept for hhg_estimate.  u_L: host or device, N_L doubles (output).  Returns
+ * HHG_ERR_DIVERGED if the result holds NaN/Inf. */
 hhg_status hhg_fmg_solve(hhg_mesh mesh, const hhg_solve_params* params, double* u_L);
 
 /* ErrorEstimate of Alg. 4 with offset j (1 <= j <= L-1) on the last solve.

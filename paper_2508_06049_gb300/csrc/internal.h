@@ -44,12 +44,8 @@ struct Prims {
 
 // threads per block of the node-parallel kernels (and of the per-cell reductions' block sums)
 constexpr int kBlock = 256;
-// dynamic shared memory a CTA of the face block or the fused interior sweep may use (larger levels
-// take the global-memory or list variants)
+// dynamic shared memory a CTA of the face block may use (larger faces sweep in global scratch)
 constexpr size_t kMaxTileSmem = 200 * 1024;
-// spare values past the last node of every binary32 / 16-bit vector (the fused sweep's bulk copies
-// read 16-byte windows that may end past a cell's last node)
-constexpr int64_t kVecPad = 16;
 
 struct LevelData {
   int l = 0, n = 1;
@@ -59,10 +55,6 @@ struct LevelData {
   // (packed local index, j | k << 16)
   std::vector<std::vector<int64_t>> icol_off;
   int2* d_icol = nullptr;
-  // 3D: per group g, table [colour][plane k = 0 .. n+1] of the first colour-list entry (relative to
-  // the group's first entry) in planes >= k, at d_pcol + pcol_off[g] (the fused interior sweep)
-  std::vector<int64_t> pcol_off;
-  int* d_pcol = nullptr;
   // boundary-type closure nodes (type != 0), sorted by type: (packed local index, i | j << 10 | k << 20)
   int2* d_bnd = nullptr;
   int64_t nbnd = 0;
@@ -130,7 +122,6 @@ struct hhg_mesh_s {
   int64_t part_len = 0;
   double* d_red = nullptr;        // per-cell reduction results (3 x n_cells)
   int* d_flag = nullptr;
-  int* d_err = nullptr;  // sticky: set by a device-side bounded wait that ran out
   void* d_face_work = nullptr;  // face-block scratch for levels whose faces exceed shared memory
   float* d_scal32 = nullptr;      // scratch scalars for the mixed path
   std::map<std::string, cudaGraphExec_t> graphs;

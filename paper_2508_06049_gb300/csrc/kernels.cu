@@ -297,7 +297,7 @@ static void cell_form(hhg_mesh_s* m, bool diff, const double* tab, double scale,
                       double* out, cudaStream_t s) {
   const LevelData& Lv = m->lv[m->L];
   double* contrib = m->d_part;  // one block sum per cell and block of k_node_form
-  dim3 grid(blocks_for(Lv.Nt), m->nc);
+  dim3 grid(blocks_for(Lv.Nt, kBlock * kFormNodes), m->nc);
   if (diff) {
     if (m->dim == 2) hhg_launch(k_node_form<2, true>, grid, kBlock, 0, s, ctx(m, m->L), tab, a, b, contrib);
     else hhg_launch(k_node_form<3, true>, grid, kBlock, 0, s, ctx(m, m->L), tab, a, b, contrib);

@@ -7,7 +7,6 @@
 
 #include <utility>
 
-#include "bulk_copy.cuh"
 #include "device_common.cuh"
 
 namespace hhg {
@@ -238,9 +237,6 @@ __global__ void __launch_bounds__(kBlock) k_smooth_interior_multi(const int* __r
   for (int c = 0; c < CPB; ++c)
     if (c0 + c < ncells) u.set(g[c], acc[c]);
 }
-
-// bounded waits of the bulk-copy pipelines: polls of mbarrier.try_wait before giving up
-constexpr int kBulkWaitTries = 1 << 20;
 
 // macro vertices: never coupled to each other on levels >= 1, so one pass.  One warp per vertex,
 // lanes over the vertex's cell copies (scattered loads in parallel), fixed-order shuffle sums.
@@ -1034,56 +1030,63 @@ __device__ __forceinline__ double block_sum_fixed(double v, double* wsum) {
 // with x = y = a - b (b may be null) for the mass form, or x = a, y = b for a bilinear form.  Summed
 // over the closure this is x^T S_T y, because the partial stencil of a cell is symmetric (the entry
 // p->p+d seen from p equals the entry p+d->p seen from p+d: both sum the cell's elements on that
-// edge), so each lattice edge is visited once.  Each block sums its nodes' contributions in a fixed
-// order (block_sum_fixed) into part[cell][block]; k_cell_sum adds a cell's block sums.
+// edge), so each lattice edge is visited once.  Each thread adds the contributions of kFormNodes
+// nodes (block stride apart), each block sums its threads' values in a fixed order
+// (block_sum_fixed) into part[cell][block], and k_cell_sum adds a cell's block sums.
+constexpr int kFormNodes = 8;
+
 template <int DIM, bool DIFF>
 __global__ void __launch_bounds__(kBlock) k_node_form(LevelCtx lc, const double* __restrict__ tab,
                                                       const double* __restrict__ a, const double* __restrict__ b,
                                                       double* __restrict__ part) {
   grid_dependency_sync();
   __shared__ double wsum[kBlock / 32];
-  int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int T = blockIdx.y;
-  double sum = 0;
-  if (loc < lc.Nt) {
-    int i, j, k;
-    decode(lc.ijk[loc], i, j, k);
-    int t = boundary_type(DIM, lc.n, i, j, k);
-    int64_t g = (int64_t)T * lc.Nt + loc;
-    int64_t off[15];
-    neighbour_offsets(DIM, lc.n, j, k, off);
-    uint32_t vm = valid_dirs_tab(DIM, t);
-    mask_offsets(DIM, vm, off);
-    const double* s = tab + (size_t)T * kStencilStride + t * kMaxDirs;
-    double xp, yp;
-    if (DIFF) {
-      xp = a[g];
-      if (b) xp -= b[g];
-      yp = xp;
-    } else {
-      xp = a[g];
-      yp = b[g];
-    }
-    // x_p (M y)_p restricted to the half stencil: s0 x_p y_p + sum_{+d} s_d (x_p y_q + x_q y_p),
-    // grouped as x_p (s0 y_p + sum s_d y_q) + y_p sum s_d x_q (one accumulator when x = y)
-    double ay = 0, ax = 0;
-#pragma unroll
-    for (int q = 0; q < npairs<DIM>(); ++q) {
-      int d = 2 * q + 1;
-      if (!(vm >> d & 1)) continue;
-      if (HHG_OOB(loc + off[d], lc.Nt, 13)) continue;
+  double tsum = 0;
+  for (int r = 0; r < kFormNodes; ++r) {
+    const int64_t loc = ((int64_t)blockIdx.x * kFormNodes + r) * kBlock + threadIdx.x;
+    double sum = 0;
+    if (loc < lc.Nt) {
+      int i, j, k;
+      decode(lc.ijk[loc], i, j, k);
+      int t = boundary_type(DIM, lc.n, i, j, k);
+      int64_t g = (int64_t)T * lc.Nt + loc;
+      int64_t off[15];
+      neighbour_offsets(DIM, lc.n, j, k, off);
+      uint32_t vm = valid_dirs_tab(DIM, t);
+      mask_offsets(DIM, vm, off);
+      const double* s = tab + (size_t)T * kStencilStride + t * kMaxDirs;
+      double xp, yp;
       if (DIFF) {
-        double xq = a[g + off[d]];
-        if (b) xq -= b[g + off[d]];
-        ay += s[d] * xq;
+        xp = a[g];
+        if (b) xp -= b[g];
+        yp = xp;
       } else {
-        ay += s[d] * b[g + off[d]];
-        ax += s[d] * a[g + off[d]];
+        xp = a[g];
+        yp = b[g];
       }
+      // x_p (M y)_p restricted to the half stencil: s0 x_p y_p + sum_{+d} s_d (x_p y_q + x_q y_p),
+      // grouped as x_p (s0 y_p + sum s_d y_q) + y_p sum s_d x_q (one accumulator when x = y)
+      double ay = 0, ax = 0;
+#pragma unroll
+      for (int q = 0; q < npairs<DIM>(); ++q) {
+        int d = 2 * q + 1;
+        if (!(vm >> d & 1)) continue;
+        if (HHG_OOB(loc + off[d], lc.Nt, 13)) continue;
+        if (DIFF) {
+          double xq = a[g + off[d]];
+          if (b) xq -= b[g + off[d]];
+          ay += s[d] * xq;
+        } else {
+          ay += s[d] * b[g + off[d]];
+          ax += s[d] * a[g + off[d]];
+        }
+      }
+      sum = DIFF ? xp * (s[0] * xp + 2.0 * ay) : xp * (s[0] * yp + ay) + yp * ax;
     }
-    sum = DIFF ? xp * (s[0] * xp + 2.0 * ay) : xp * (s[0] * yp + ay) + yp * ax;
+    tsum += sum;
   }
-  const double tot = block_sum_fixed(sum, wsum);
+  const double tot = block_sum_fixed(tsum, wsum);
   if (threadIdx.x == 0) part[(int64_t)T * gridDim.x + blockIdx.x] = tot;
 }
 

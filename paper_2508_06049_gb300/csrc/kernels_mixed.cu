@@ -202,236 +202,6 @@ __global__ void __launch_bounds__(1024) k_coarse_mixed(int n0f, const int* __res
   }
 }
 
-// ---------------------------------------------------------------- fused interior sweep (3D)
-//
-// All interior colour stages of one Gauss-Seidel sweep (the last stages of the smoother of Alg. 4)
-// in one pass over each macro cell, one CTA per cell.  A node of plane k couples only with nodes of
-// planes k-1 .. k+1 (no lattice direction changes k by more than one) and never with a node of its
-// own colour, so the colour stages can be pipelined over the planes: at step p the CTA updates
-// colour 0 on plane p, colour 1 on plane p-1, ..., colour M-1 on plane p-M+1.  Every neighbour value
-// an update reads is then either still from the start of the sweep (a colour not yet updated there)
-// or already final (a colour updated before), exactly as in the stage-by-stage order, and each node
-// is computed with the list kernel's arithmetic in the same order, so the results are the same bits.
-// u and b are read once and u written once per sweep, instead of once per colour stage.
-// The cell's u planes p-M .. p+1 and b planes p-M+1 .. p sit in shared-memory rings (one slot per
-// plane, slot = plane index mod ring size).  During step p one thread brings u plane p+2 and b
-// plane p+1 in by bulk asynchronous copies (16-byte aligned windows around the planes, completing
-// on one of two mbarriers) and prefetches planes kSweepL2Ahead further ahead into L2.  The nodes of
-// one colour and plane are a contiguous range of the colour's list (entries: packed index, j | k << 16;
-// the ranges are tabulated per plane), one node per thread.  Updated values go to shared memory and
-// straight to global memory.  A copy that does not arrive within the bounded wait sets *err; the CTA
-// then waits (bounded) for its copies in flight and returns.
-constexpr int kSweepThreads = 256;
-constexpr int kSweepL2Ahead = 6;
-
-// elements of one ring slot: the largest plane (plane 0, side n) with its 16-byte rounding
-inline int sweep_slot_elems(int n, int esize) {
-  int64_t bytes = tri_size(n) * esize + 32;
-  bytes = (bytes + 15) & ~(int64_t)15;
-  return (int)(bytes / esize);
-}
-// bytes of the per-CTA tables (u and b plane windows: 8-byte start + 4-byte size each, u
-// shared-memory deltas with one spare row, colour-list plane ranges)
-inline int sweep_table_bytes(int n, int mcol) {
-  return (int)((24 * (n + 1) + 8 * (n + 1) + 4 * mcol * (n + 2) + 15) & ~15);
-}
-
-// plane k of stencil slot d's neighbour, relative to the node's plane
-__device__ constexpr int slot_dk(int d) {
-  return (d == 5 || d == 10 || d == 12 || d == 13) ? 1 : ((d == 6 || d == 9 || d == 11 || d == 14) ? -1 : 0);
-}
-
-// packed-index offset of 3D stencil slot d from a node in row j of a plane of side m (T(m), T(m+1):
-// the sizes of triangles of side m and m+1), in 32-bit arithmetic (dir_offset of the lattice)
-__device__ __forceinline__ int slot_offset(int d, int m, int j, int Tm, int Tm1) {
-  switch (d) {
-    case 1: return 1;
-    case 2: return -1;
-    case 3: return m + 1 - j;
-    case 4: return -(m + 2 - j);
-    case 5: return Tm - j;
-    case 6: return -Tm1 + j;
-    case 7: return -(m + 1 - j);
-    case 8: return m - j;
-    case 9: return 1 - Tm1 + j;
-    case 10: return -1 + Tm - j;
-    case 11: return -Tm1 + m + 2;
-    case 12: return Tm - m - 1;
-    case 13: return Tm - m;
-    default: return -Tm1 + m + 1;
-  }
-}
-
-// list entries per thread and colour phase kept in registers ahead (a phase with more nodes than
-// kSweepThreads * kSweepAhead reads the rest directly)
-constexpr int kSweepAhead = 4;
-
-template <int PM, int M, typename U>
-__global__ void __launch_bounds__(kSweepThreads) k_sweep_interior_fused(
-    const int* __restrict__ gcells, LevelCtx lc, const int2* __restrict__ icol, const int* __restrict__ pcol,
-    const float* __restrict__ tnorm, const float* __restrict__ invl, Vec<float, U> u, const float* __restrict__ b,
-    int slotU, int tbytes, int* __restrict__ err) {
-  grid_dependency_sync();
-  constexpr int NU = M + 4, K = kSweepAhead;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int n = lc.n;
-  const int T = gcells[blockIdx.x];
-  U* ug = u.p + (int64_t)T * lc.Nt;
-  const float* bg = b + (int64_t)T * lc.Nt;
-  // per-CTA tables: u plane windows (16-byte aligned start, bytes), b plane windows (for the L2
-  // prefetch), u shared-memory deltas, colour-list plane ranges
-  unsigned long long* wua = (unsigned long long*)(smem + 16);
-  unsigned long long* wba = wua + (n + 1);
-  uint32_t* wub = (uint32_t*)(wba + (n + 1));
-  uint32_t* wbb = wub + (n + 1);
-  int* sdu = (int*)(wbb + (n + 1));   // u: shared index of packed index p in plane k is p + sdu[k]
-  int* spc = sdu + 2 * (n + 1);       // colour-list plane ranges [c][k]
-  U* su = (U*)(smem + 16 + tbytes);
-  const uint32_t bar0 = smem_addr(smem);
-  const int last_u = n - 2, last_b = n - 3;  // planes read: u 0 .. n-2, b (updated planes) 1 .. n-3
-  if (threadIdx.x == 0) {
-    mbar_init(bar0, 1);
-    mbar_init(bar0 + 8, 1);
-  }
-  const int tn = (int)tet_size(n);
-  for (int k = threadIdx.x; k <= n; k += blockDim.x) {
-    const int P0 = tn - (n - k + 1) * (n - k + 2) * (n - k + 3) / 6;
-    const int P1 = tn - (n - k) * (n - k + 1) * (n - k + 2) / 6;  // start of plane k+1
-    const uintptr_t us = (uintptr_t)(ug + P0), ue = ((uintptr_t)(ug + P1) + 15) & ~(uintptr_t)15;
-    const uintptr_t bs = (uintptr_t)(bg + P0), be = ((uintptr_t)(bg + P1) + 15) & ~(uintptr_t)15;
-    wua[k] = us & ~(uintptr_t)15;
-    wub[k] = (uint32_t)(ue - (us & ~(uintptr_t)15));
-    wba[k] = bs & ~(uintptr_t)15;
-    wbb[k] = (uint32_t)(be - (bs & ~(uintptr_t)15));
-    sdu[k] = (k % NU) * slotU + (int)((us & 15) / sizeof(U)) - P0;
-  }
-  for (int q = threadIdx.x; q < M * (n + 2); q += blockDim.x) spc[q] = pcol[q];
-  float sc = 1.0f, isc = 1.0f;
-  if constexpr (IsNarrow<U>::value) {
-    sc = *u.scale;
-    isc = 1.0f / *u.scale;
-  }
-  float tv[15];
-#pragma unroll
-  for (int d = 1; d < 15; ++d) tv[d] = ((PM >> ((d - 1) >> 1)) & 1) ? tnorm[(size_t)T * 16 + d] : 0.0f;
-  const float il = invl[T];
-  __syncthreads();
-
-  // u copies issued at step s (s = 0: the prologue, planes 0..3; s >= 1: plane s+3) complete on
-  // barrier s & 1 and are first read at step s+2 (step 1 for the prologue); u and b planes further
-  // ahead are prefetched into L2
-  auto issue = [&](int s) {
-    const uint32_t bar = bar0 + 8u * (uint32_t)(s & 1);
-    const int u0 = s == 0 ? 0 : s + 3, u1 = min(s + 3, last_u);
-    uint32_t total = 0;
-    for (int q = u0; q <= u1; ++q) total += wub[q];
-    mbar_arrive_expect_tx(bar, total);
-    for (int q = u0; q <= u1; ++q) bulk_g2s(smem_addr(su + (q % NU) * slotU), (const void*)wua[q], wub[q], bar);
-    for (int q = (s == 0 ? 4 : s + 3 + kSweepL2Ahead); q <= min(s + 3 + kSweepL2Ahead, last_u); ++q)
-      bulk_prefetch_l2((const void*)wua[q], wub[q]);
-    for (int q = (s == 0 ? 1 : s + 2 + kSweepL2Ahead); q <= min(s + 2 + kSweepL2Ahead, last_b); ++q)
-      bulk_prefetch_l2((const void*)wba[q], wbb[q]);
-  };
-  // this thread's list entries of the colour phases of step p (colour c on plane p - c), packed as
-  // p | j << 16 (-1: none)
-  auto load_entries = [&](int p, int (&buf)[M][K]) {
-#pragma unroll
-    for (int c = 0; c < M; ++c) {
-      const int q = p - c;
-      const bool on = q >= 1 && q <= n - 3;
-      const int lo = on ? spc[c * (n + 2) + q] : 0, hi = on ? spc[c * (n + 2) + q + 1] : 0;
-#pragma unroll
-      for (int r = 0; r < K; ++r) {
-        const int e = lo + (int)threadIdx.x + r * kSweepThreads;
-        int v = -1;
-        if (e < hi) {
-          const int2 en = icol[e];
-          v = en.x | ((en.y & 0xffff) << 16);
-        }
-        buf[c][r] = v;
-      }
-    }
-  };
-  // the right-hand side at those entries (from global memory; the planes were prefetched into L2)
-  auto load_b = [&](const int (&ent)[M][K], float (&bv)[M][K]) {
-#pragma unroll
-    for (int c = 0; c < M; ++c)
-#pragma unroll
-      for (int r = 0; r < K; ++r) bv[c][r] = ent[c][r] >= 0 ? bg[ent[c][r] & 0xffff] : 0.0f;
-  };
-  // one node: packed index p, row j of plane q (side m = n - q), right-hand side bp
-  auto update = [&](int p, int j, float bp, int m, int Tm, int Tm1, int dm, int d0, int dp) {
-    float acc = bp * il;
-#pragma unroll
-    for (int qq = 0; qq < 7; ++qq) {
-      if (PM >> qq & 1) {
-        const int da = 2 * qq + 1, dbb = 2 * qq + 2;
-        const int sa = slot_dk(da) == 0 ? d0 : (slot_dk(da) > 0 ? dp : dm);
-        const int sbb = slot_dk(dbb) == 0 ? d0 : (slot_dk(dbb) > 0 ? dp : dm);
-        acc -= tv[da] * (Conv<float, U>::ld(su + (p + slot_offset(da, m, j, Tm, Tm1) + sa)) * isc);
-        acc -= tv[dbb] * (Conv<float, U>::ld(su + (p + slot_offset(dbb, m, j, Tm, Tm1) + sbb)) * isc);
-      }
-    }
-    U v;
-    Conv<float, U>::st(&v, IsNarrow<U>::value ? acc * sc : acc);
-    su[p + d0] = v;
-    ug[p] = v;
-  };
-
-  // entries two steps ahead, right-hand sides one step ahead
-  int e0[M][K], e1[M][K], e2[M][K];
-  float b0[M][K], b1[M][K];
-  if (threadIdx.x == 0) issue(0);
-  load_entries(1, e0);
-  load_entries(2, e1);
-  load_b(e0, b0);
-  int ok = __syncthreads_and(mbar_wait_bounded(bar0, 0, kBulkWaitTries));
-  const int p_end = n - 3 + M - 1;
-  int p = 1;
-  for (; ok && p <= p_end; ++p) {
-    if (threadIdx.x == 0) issue(p);  // after the last copy (s = n-5) only an arrival: the phase completes
-    if (p + 2 <= p_end) load_entries(p + 2, e2);
-    if (p + 1 <= p_end) load_b(e1, b1);
-#pragma unroll
-    for (int c = 0; c < M; ++c) {
-      const int q = p - c;
-      if (q >= 1 && q <= n - 3) {
-        const int dm = sdu[q - 1], d0 = sdu[q], dp = sdu[q + 1];
-        const int m = n - q, Tm = (m + 1) * (m + 2) / 2, Tm1 = (m + 2) * (m + 3) / 2;
-#pragma unroll
-        for (int r = 0; r < K; ++r)
-          if (e0[c][r] >= 0) update(e0[c][r] & 0xffff, e0[c][r] >> 16, b0[c][r], m, Tm, Tm1, dm, d0, dp);
-        const int hi = spc[c * (n + 2) + q + 1];
-        for (int e = spc[c * (n + 2) + q] + (int)threadIdx.x + K * kSweepThreads; e < hi; e += kSweepThreads) {
-          const int2 en = icol[e];
-          update(en.x, en.y & 0xffff, bg[en.x], m, Tm, Tm1, dm, d0, dp);
-        }
-      }
-      if (c < M - 1) __syncthreads();
-    }
-#pragma unroll
-    for (int c = 0; c < M; ++c)
-#pragma unroll
-      for (int r = 0; r < K; ++r) {
-        e0[c][r] = e1[c][r];
-        e1[c][r] = e2[c][r];
-        b0[c][r] = b1[c][r];
-      }
-    // the next step reads the u copies issued in the previous one (issue(0) for steps 1 and 2 was
-    // waited on before the loop: its phase has completed, so the wait at p = 1 returns at once)
-    const int s = p - 1;
-    const bool w = (p == p_end) || mbar_wait_bounded(bar0 + 8u * (uint32_t)(s & 1), (uint32_t)((s >> 1) & 1),
-                                                      kBulkWaitTries);
-    ok = __syncthreads_and(w);
-  }
-  if (!ok) {
-    if (threadIdx.x == 0) atomicOr(err, 1);
-    // copies issued in the last two steps may still be in flight: let them land before exiting
-    for (int s = max(0, p - 2); s <= p - 1; ++s)
-      mbar_wait_bounded(bar0 + 8u * (uint32_t)(s & 1), (uint32_t)((s >> 1) & 1), kBulkWaitTries);
-  }
-}
-
 // ---------------------------------------------------------------- launchers
 
 static LevelCtx ctx(const hhg_mesh_s* m, int l) {
@@ -459,44 +229,6 @@ static void interior32(hhg_mesh_s* m, int l, int gi, int colour, U* u, const flo
   hhg_launch(k_smooth_interior_multi<DIM, PM, CPB, float, U, float>, grid, kBlock, 0, s, G.d_cells,
              (int)G.cells.size(), Lv.d_icol + a, b - a, ctx(m, l), m->d_tnormf, Lv.d_invlf, vec_of<U>(m, l, u),
              CVec<float, float>{rhs, nullptr});
-}
-
-// the fused interior sweep of group gi on level l (3D): one CTA per cell, all colours in one pass
-// shared memory of the fused sweep on a level of side n with m colours and u stored in esize bytes
-inline size_t fused_smem(int n, int mcol, int esize) {
-  return 16 + (size_t)sweep_table_bytes(n, mcol) + (size_t)(mcol + 4) * sweep_slot_elems(n, esize) * esize;
-}
-
-template <int PM, int M, typename U>
-static void fused32(hhg_mesh_s* m, int l, int gi, U* u, const float* rhs, cudaStream_t s) {
-  const LevelData& Lv = m->lv[l];
-  const Group& G = m->groups[gi];
-  const int slotU = sweep_slot_elems(Lv.n, (int)sizeof(U));
-  const size_t smem = fused_smem(Lv.n, M, (int)sizeof(U));
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_sweep_interior_fused<PM, M, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  hhg_launch(k_sweep_interior_fused<PM, M, U>, (unsigned)G.cells.size(), kSweepThreads, smem, s, G.d_cells, ctx(m, l),
-             (const int2*)(Lv.d_icol + Lv.icol_off[gi][0]), (const int*)(Lv.d_pcol + Lv.pcol_off[gi]), m->d_tnormf,
-             Lv.d_invlf, vec_of<U>(m, l, u), rhs, slotU, sweep_table_bytes(Lv.n, M), m->d_err);
-}
-
-// The fused sweep is used on 3D levels with kFusedMinN <= n <= kFusedMaxN (its packed indices travel
-// in 16 bits) whose rings fit in shared memory; other levels run the colour stages as separate list
-// launches.
-constexpr int kFusedMinN = 8, kFusedMaxN = 64;
-template <typename U>
-static bool use_fused(const hhg_mesh_s* m, int l, int gi) {
-  const int n = m->lv[l].n;
-  return m->dim == 3 && n >= kFusedMinN && n <= kFusedMaxN &&
-         fused_smem(n, m->groups[gi].m, (int)sizeof(U)) <= kMaxTileSmem;
-}
-
-template <typename U>
-static void fused32_dispatch(hhg_mesh_s* m, int l, int gi, U* u, const float* rhs, cudaStream_t s) {
-  const Group& G = m->groups[gi];
-  if (G.pmask == 0x29 && G.m == 2) fused32<0x29, 2, U>(m, l, gi, u, rhs, s);
-  else if (G.m == 2) fused32<0x7f, 2, U>(m, l, gi, u, rhs, s);
-  else fused32<0x7f, 4, U>(m, l, gi, u, rhs, s);
 }
 
 template <int DIM, typename U>
@@ -550,13 +282,8 @@ static void sweep32(hhg_mesh_s* m, int l, U* u, const float* rhs, cudaStream_t s
                                          (float*)m->d_face_work, false, s);
     } else {
       int c = st - (DIM == 3 ? 4 : 3);
-      for (size_t gi = 0; gi < m->groups.size(); ++gi) {
-        if (use_fused<U>(m, l, (int)gi)) {
-          if (c == 0) fused32_dispatch<U>(m, l, (int)gi, u, rhs, s);  // every colour in one launch
-        } else if (c < m->groups[gi].m) {
-          interior32_dispatch<DIM, U>(m, l, (int)gi, c, u, rhs, s);
-        }
-      }
+      for (size_t gi = 0; gi < m->groups.size(); ++gi)
+        if (c < m->groups[gi].m) interior32_dispatch<DIM, U>(m, l, (int)gi, c, u, rhs, s);
     }
   }
 }
@@ -842,9 +569,7 @@ hhg_status mixed_prepare(hhg_mesh_s* m, int storage) {
     }
     if (!m->mixed_alloc) {
       cudaError_t e;
-      // kVecPad spare values: the fused sweep's bulk copies read 16-byte windows that may end past
-      // the last node
-      const size_t nb = sizeof(float) * (Lv.N + kVecPad);
+      const size_t nb = sizeof(float) * Lv.N;
       if ((e = cudaMalloc(&Lv.x32, nb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
       if ((e = cudaMalloc(&Lv.b32, nb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
       if ((e = cudaMalloc(&Lv.r32, nb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
@@ -861,34 +586,30 @@ hhg_status mixed_prepare(hhg_mesh_s* m, int storage) {
       cudaFree(Lv.c16);
       Lv.c16 = nullptr;
     }
-    cudaError_t e = cudaMalloc(&Lv.c16, esz * (Lv.N + kVecPad));
+    cudaError_t e = cudaMalloc(&Lv.c16, esz * Lv.N);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-    if ((e = cudaMemset(Lv.c16, 0, esz * (Lv.N + kVecPad))) != cudaSuccess) return cuda_fail(e, "cudaMemset");
+    if ((e = cudaMemset(Lv.c16, 0, esz * Lv.N)) != cudaSuccess) return cuda_fail(e, "cudaMemset");
   }
   m->mixed_alloc = true;
   m->last_storage = storage;
   return storage == 2 ? upload_ainv_inf(m) : HHG_OK;
 }
 
-// Profiling: the level-L interior stage of the first cell group as the solve runs it: the fused sweep
-// (all colours; algorithmic bytes = u of every closure node read once, b read and u written at the
-// interior nodes) or, where the fused sweep is not used, the colour-0 list stage (u of the group's
-// closures read once, b read and u written at the colour's nodes).
+// Profiling: the level-L interior stage of colour 0 for the first cell group, as the solve launches it
+// (algorithmic bytes: u of the group's closures read once, b read and u written at the colour's nodes)
 hhg_status mixed_profile_interior(hhg_mesh_s* m, int reps, cudaStream_t s, long long* units, double* bytes,
                                   double* flops) {
   const int L = m->L;
   LevelData& Lv = m->lv[L];
   const Group& G = m->groups[0];
-  const bool fused = use_fused<float>(m, L, 0);
-  int64_t len = fused ? Lv.icol_off[0][G.m] - Lv.icol_off[0][0] : Lv.icol_off[0][1] - Lv.icol_off[0][0];
+  int64_t len = Lv.icol_off[0][1] - Lv.icol_off[0][0];
   long long nodes = (long long)len * (long long)G.cells.size();
   int p = __builtin_popcount(G.pmask);
   *units = nodes;
   *bytes = 4.0 * ((double)Lv.Nt * G.cells.size() + 2.0 * nodes);
   *flops = (4.0 * p + 1.0) * nodes;
   for (int r = 0; r < reps; ++r) {
-    if (fused) fused32_dispatch<float>(m, L, 0, Lv.x32, Lv.b32, s);
-    else if (m->dim == 2) interior32_dispatch<2, float>(m, L, 0, 0, Lv.x32, Lv.b32, s);
+    if (m->dim == 2) interior32_dispatch<2, float>(m, L, 0, 0, Lv.x32, Lv.b32, s);
     else interior32_dispatch<3, float>(m, L, 0, 0, Lv.x32, Lv.b32, s);
   }
   return HHG_OK;

@@ -744,29 +744,6 @@ hhg_status build_mesh(hhg_mesh_s* m, const double* coords, const int* cells, con
       }
     }
     if ((st = upload(m, &Lv.d_icol, icol)) != HHG_OK) return st;
-    // plane ranges of the colour lists (3D, fused interior sweep): for group g, colour c and plane k
-    // = 0 .. n+1, the first entry of the colour-c list whose node lies in plane >= k, relative to the
-    // group's first entry; table [c][k] at d_pcol + pcol_off[g]
-    {
-      std::vector<int> pcol;
-      Lv.pcol_off.assign(m->groups.size(), 0);
-      if (d == 3) {
-        const int n = Lv.n;
-        for (size_t g = 0; g < m->groups.size(); ++g) {
-          Lv.pcol_off[g] = (int64_t)pcol.size();
-          for (int c = 0; c < m->groups[g].m; ++c) {
-            auto b0 = icol.begin() + Lv.icol_off[g][c], b1 = icol.begin() + Lv.icol_off[g][c + 1];
-            for (int k = 0; k <= n + 1; ++k) {
-              const int64_t P = k <= n ? tet_size(n) - tet_size(n - k) : tet_size(n);
-              auto it = std::lower_bound(b0, b1, P, [](const int2& e, int64_t q) { return (int64_t)e.x < q; });
-              pcol.push_back((int)(it - icol.begin() - Lv.icol_off[g][0]));
-            }
-          }
-        }
-      }
-      if (pcol.empty()) pcol.push_back(0);
-      if ((st = upload(m, &Lv.d_pcol, pcol)) != HHG_OK) return st;
-    }
     // boundary-type nodes, sorted by type (stable: packed order inside a type)
     std::vector<std::pair<int, int64_t>> bt;
     for (int64_t q = 0; q < Lv.Nt; ++q) {
@@ -809,7 +786,6 @@ hhg_status build_mesh(hhg_mesh_s* m, const double* coords, const int* cells, con
   if ((st = dalloc(m, &m->d_part, (size_t)m->part_len)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->d_red, (size_t)nc * 4)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->d_flag, 4)) != HHG_OK) return st;
-  if ((st = dalloc(m, &m->d_err, 4)) != HHG_OK) return st;
   if (d == 3 && m->faces.count) {  // face-block scratch where a face's values exceed shared memory
     int64_t nfL = m->lv[L].fcol_off[3];
     if (2 * nfL * (int64_t)sizeof(double) > (int64_t)kMaxTileSmem) {
@@ -854,10 +830,10 @@ void free_mesh(hhg_mesh_s* m) {
   for (auto& g : m->groups) F(g.d_cells);
   F(m->d_Ainv); F(m->d_cf_vert); F(m->d_rmax); F(m->d_ainv_inf);
   for (auto& Lv : m->lv) {
-    F(Lv.d_ijk); F(Lv.d_icol); F(Lv.d_pcol); F(Lv.d_bnd); F(Lv.d_invl); F(Lv.d_invlf); F(Lv.d_fcol); F(Lv.u); F(Lv.b); F(Lv.rc); F(Lv.w); F(Lv.tmp);
+    F(Lv.d_ijk); F(Lv.d_icol); F(Lv.d_bnd); F(Lv.d_invl); F(Lv.d_invlf); F(Lv.d_fcol); F(Lv.u); F(Lv.b); F(Lv.rc); F(Lv.w); F(Lv.tmp);
     F(Lv.c16); F(Lv.r32); F(Lv.t32); F(Lv.cscale); F(Lv.x32); F(Lv.b32);
   }
-  F(m->fL); F(m->gL); F(m->d_part); F(m->d_red); F(m->d_flag); F(m->d_err); F(m->d_face_work); F(m->d_scal32);
+  F(m->fL); F(m->gL); F(m->d_part); F(m->d_red); F(m->d_flag); F(m->d_face_work); F(m->d_scal32);
   if (m->h_red) cudaFreeHost(m->h_red);
   if (m->cap) cudaStreamDestroy(m->cap);
   if (m->own) cudaStreamDestroy(m->own);

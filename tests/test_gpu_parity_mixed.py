@@ -68,9 +68,9 @@ def _setup(P, name, L):
 @pytest.mark.parametrize("name,L", [("cube384_l6", 5), ("cube_pert_k", 4), ("cube162", 4), ("fichera336_l6", 4),
                                     ("lshape_pert", 4)])
 def test_binary32_sweeps_match_oracle(P, name, L):
-    """The mixed path's binary32 smoother (in 3D the interior colours of a sweep run as one fused
-    launch per group on levels with at least 8 intervals per macro edge, as separate colour stages
-    below) against the oracle's binary64 sweep on every level, 1 and 3 sweeps from a random start.
+    """The mixed path's binary32 smoother (the stage kernels of the binary32 V-cycles: vertex and edge
+    stages, face block, interior colour stages with four cells per thread) against the oracle's
+    binary64 sweep on every level, 1 and 3 sweeps from a random start.
     binary32 rounds each update to 2^-24 relative and the sweeps contract the error, so the result
     stays within 1e-5 of the largest value."""
     mesh, h, prob, idx = _setup(P, name, L)
