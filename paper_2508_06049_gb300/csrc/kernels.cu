@@ -22,12 +22,17 @@ __global__ void __launch_bounds__(kBlock) k_cell_sum(int64_t np, double scale, c
   if (threadIdx.x == 0) out[T] = scale * tot;
 }
 
-// x = a - b elementwise
+// x = a - b elementwise (level vectors, 256-byte aligned: two values per 16-byte access, the odd
+// tail by thread 0 of block 0)
 __global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ x,
                       int64_t n) {
   grid_dependency_sync();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] = a[i] - b[i];
+  const int64_t n2 = n / 2;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 p = reinterpret_cast<const double2*>(a)[i], q = reinterpret_cast<const double2*>(b)[i];
+    reinterpret_cast<double2*>(x)[i] = make_double2(p.x - q.x, p.y - q.y);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) x[n - 1] = a[n - 1] - b[n - 1];
 }
 
 // Level-l node coordinates x = x_0 + J p / n of every cell's closure lattice (hhg_level_coords into
@@ -268,7 +273,7 @@ void launch_prolong(hhg_mesh_s* m, int l, const double* coarse, double* fine, cu
 }
 
 void launch_sub(hhg_mesh_s* m, const double* a, const double* b, double* x, int64_t n, cudaStream_t s) {
-  hhg_launch(k_sub, 4 * m->sm_count, kBlock, 0, s, a, b, x, n);
+  hhg_launch(k_sub, 16 * m->sm_count, kBlock, 0, s, a, b, x, n);
 }
 
 void launch_level_coords(hhg_mesh_s* m, int l, const double* geom, double* xyz, cudaStream_t s) {

@@ -594,34 +594,43 @@ __global__ void k_face_ext(int nprim, int nf, const int32_t* __restrict__ fnodes
   if (active && lane == 0) E[(int64_t)e * nf + face_pos(lc.n, a, b)] = bs - sscale * acc;
 }
 
-// One CTA per face.  fcol: colour offsets of fnodes (colour c entries [fcol.c, fcol.c+1)); W: the
-// face's six in-plane couplings (unit level scale, summed over copies); pinv: 1 / diagonal (unit
-// scale); isscale = 1 / level scale.  work: 2 nf values of scratch per face when they do not fit
-// in shared memory (nullptr: shared memory).
-template <typename R, typename U>
-__global__ void __launch_bounds__(kBlock) k_face_gs(int nf, int4 fcol, const int32_t* __restrict__ fnodes,
+// FPC faces per CTA (FPC = 1: the CTA's kBlock threads sweep one face, synchronised by block
+// barriers; FPC = 8: one warp per face, warp barriers, for levels whose faces have few nodes).
+// fcol: colour offsets of fnodes (colour c entries [fcol.c, fcol.c+1)); W: the face's six in-plane
+// couplings (unit level scale, summed over copies); pinv: 1 / diagonal (unit scale); isscale = 1 /
+// level scale.  work: 2 nf values of scratch per face when they do not fit in shared memory
+// (nullptr: shared memory, 2 nf values per face of the CTA).
+template <int FPC, typename R, typename U>
+__global__ void __launch_bounds__(kBlock) k_face_gs(int nprim, int nf, int4 fcol, const int32_t* __restrict__ fnodes,
                                                     const int* __restrict__ ptr, const int* __restrict__ cell,
                                                     const int* __restrict__ locv, const unsigned char* __restrict__ dir,
                                                     LevelCtx lc, const R* __restrict__ W, const R* __restrict__ pinv,
                                                     R isscale, Vec<R, U> u, const R* __restrict__ E, R* work) {
   grid_dependency_sync();
+  static_assert(FPC == 1 || kBlock / FPC == 32, "one CTA or one warp per face");
+  constexpr int TPF = kBlock / FPC;  // threads per face
   extern __shared__ __align__(16) unsigned char smem[];
-  const int e = blockIdx.x;
-  if (dir[e]) return;  // uniform across the CTA
+  const int grp = (int)threadIdx.x / TPF, t = (int)threadIdx.x % TPF;
+  const int e = (int)blockIdx.x * FPC + grp;
+  if (e >= nprim || dir[e]) return;  // uniform across the face's threads (the CTA or the warp)
+  auto sync = [] {
+    if (FPC == 1) __syncthreads();
+    else __syncwarp();
+  };
   const int n = lc.n;
-  R* uf = work ? work + (int64_t)e * 2 * nf : (R*)smem;
+  R* uf = work ? work + (int64_t)e * 2 * nf : (R*)smem + (size_t)grp * 2 * nf;
   R* ef = uf + nf;
   const int c0 = ptr[e];
   const int loc0 = locv[c0];
   const int64_t base0 = (int64_t)cell[c0] * lc.Nt;
   // gather the face's values (copy 0) and outside sums, four per thread in flight
   constexpr int kUnroll = 4;
-  for (int q0 = threadIdx.x; q0 < nf; q0 += kUnroll * blockDim.x) {
+  for (int q0 = t; q0 < nf; q0 += kUnroll * TPF) {
     R uv[kUnroll], ev[kUnroll];
     int ps[kUnroll];
 #pragma unroll
     for (int r = 0; r < kUnroll; ++r) {
-      int q = q0 + r * blockDim.x;
+      int q = q0 + r * TPF;
       ps[r] = -1;
       if (q < nf) {
         int32_t ab = fnodes[q];
@@ -646,10 +655,10 @@ __global__ void __launch_bounds__(kBlock) k_face_gs(int nf, int4 fcol, const int
 #pragma unroll
   for (int q = 0; q < 6; ++q) w[q] = W[(int64_t)e * 8 + q];
   const R pv = pinv[e];
-  __syncthreads();
+  sync();
   const int cb[4] = {fcol.x, fcol.y, fcol.z, fcol.w};
   for (int col = 0; col < 3; ++col) {
-    for (int q = cb[col] + threadIdx.x; q < cb[col + 1]; q += blockDim.x) {
+    for (int q = cb[col] + t; q < cb[col + 1]; q += TPF) {
       int32_t ab = fnodes[q];
       int a = ab & 0xffff, b = ab >> 16;
       int pos = face_pos(n, a, b);
@@ -662,12 +671,12 @@ __global__ void __launch_bounds__(kBlock) k_face_gs(int nf, int4 fcol, const int
       }
       uf[pos] = v * pv;
     }
-    __syncthreads();
+    sync();
   }
   for (int c = c0; c < ptr[e + 1]; ++c) {
     const int loc = locv[c];
     const int64_t base = (int64_t)cell[c] * lc.Nt;
-    for (int q = threadIdx.x; q < nf; q += blockDim.x) {
+    for (int q = t; q < nf; q += TPF) {
       int32_t ab = fnodes[q];
       int a = ab & 0xffff, b = ab >> 16;
       int i, j, k;
@@ -704,6 +713,10 @@ void launch_vertex_edge_even(const Prims& V, const Prims& Ed, int n, LevelCtx lc
 #undef HHG_VE
 }
 
+inline int4 fcol4(const LevelData& Lv) {
+  return make_int4((int)Lv.fcol_off[0], (int)Lv.fcol_off[1], (int)Lv.fcol_off[2], (int)Lv.fcol_off[3]);
+}
+
 // Launch the face block on one level: E in `E` (P.count x nf values), the per-face sweeps in shared
 // memory when 2 nf values fit (else in `work`, P.count x 2 nf values).
 template <typename R, typename U, typename B>
@@ -725,13 +738,21 @@ void launch_face_block(const Prims& P, const LevelData& Lv, LevelCtx lc, const R
     else HHG_FACE_EXT(2, false);
   }
 #undef HHG_FACE_EXT
+  // faces with few nodes: one warp per face, eight faces per CTA
+  constexpr int kFacesPerWarpCta = kBlock / 32;
+  if (nf <= 64) {
+    const size_t smem8 = (size_t)kFacesPerWarpCta * 2 * nf * sizeof(R);
+    hhg_launch(k_face_gs<kFacesPerWarpCta, R, U>, (unsigned)((P.count + kFacesPerWarpCta - 1) / kFacesPerWarpCta),
+               kBlock, smem8, s, P.count, nf, fcol4(Lv), Lv.d_fcol, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, lc, W, pinv,
+               (R)1 / ss, u, (const R*)E, (R*)nullptr);
+    return;
+  }
   const size_t smem = 2 * (size_t)nf * sizeof(R);
   const bool fits = smem <= kMaxTileSmem;
   if (fits && smem > 48 * 1024)
-    cudaFuncSetAttribute(k_face_gs<R, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxTileSmem);
-  int4 fcol = make_int4((int)Lv.fcol_off[0], (int)Lv.fcol_off[1], (int)Lv.fcol_off[2], (int)Lv.fcol_off[3]);
-  hhg_launch(k_face_gs<R, U>, (unsigned)P.count, kBlock, fits ? smem : 0, s, nf, fcol, Lv.d_fcol, P.d_ptr, P.d_cell,
-             P.d_loc, P.d_dir, lc, W, pinv, (R)1 / ss, u, (const R*)E, fits ? (R*)nullptr : work);
+    cudaFuncSetAttribute(k_face_gs<1, R, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxTileSmem);
+  hhg_launch(k_face_gs<1, R, U>, (unsigned)P.count, kBlock, fits ? smem : 0, s, P.count, nf, fcol4(Lv), Lv.d_fcol,
+             P.d_ptr, P.d_cell, P.d_loc, P.d_dir, lc, W, pinv, (R)1 / ss, u, (const R*)E, fits ? (R*)nullptr : work);
 }
 
 // ---------------------------------------------------------------- residual, restriction (V-cycle of Alg. 4; transfers of Sec. 4.4)

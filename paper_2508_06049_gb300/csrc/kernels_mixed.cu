@@ -22,10 +22,17 @@ namespace hhg {
 
 // ---------------------------------------------------------------- elementwise kernels
 
+// Elementwise kernels over whole level vectors (cudaMalloc'd, so 256-byte aligned): four values per
+// thread and step through 16-byte vector accesses, grid-stride, the n % 4 tail by thread 0 of block 0.
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
   grid_dependency_sync();
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = (float)a[i];
+  const int64_t n4 = n / 4;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 x = reinterpret_cast<const double2*>(a)[2 * i], y = reinterpret_cast<const double2*>(a)[2 * i + 1];
+    reinterpret_cast<float4*>(b)[i] = make_float4((float)x.x, (float)x.y, (float)y.x, (float)y.y);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    for (int64_t i = 4 * n4; i < n; ++i) b[i] = (float)a[i];
 }
 
 __global__ void k_to_f64(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
@@ -50,11 +57,28 @@ __global__ void k_to_f64_level(LevelCtx lc, const uint16_t* __restrict__ dirmask
   u[g] = (dirmask[T] >> t & 1) ? gL[g] : (double)x[g];
 }
 
-// u += c (binary64 accumulate of a binary32 correction; c is zero on Dirichlet nodes)
+// u += c (binary64 accumulate of a binary32 correction; c is zero on Dirichlet nodes); vectorised
+// like k_to_f32
 __global__ void k_add_f32(const float* __restrict__ c, double* __restrict__ u, int64_t n) {
   grid_dependency_sync();
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) u[i] += (double)c[i];
+  const int64_t n4 = n / 4;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 d = reinterpret_cast<const float4*>(c)[i];
+    double2 x = reinterpret_cast<double2*>(u)[2 * i], y = reinterpret_cast<double2*>(u)[2 * i + 1];
+    x.x += (double)d.x;
+    x.y += (double)d.y;
+    y.x += (double)d.z;
+    y.y += (double)d.w;
+    reinterpret_cast<double2*>(u)[2 * i] = x;
+    reinterpret_cast<double2*>(u)[2 * i + 1] = y;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    for (int64_t i = 4 * n4; i < n; ++i) u[i] += (double)c[i];
+}
+
+// grid of the vectorised elementwise kernels: enough blocks to fill the GPU several times over
+inline unsigned elementwise_blocks(const hhg_mesh_s* m, int64_t n) {
+  return std::max(1u, std::min<unsigned>(blocks_for((n + 3) / 4), (unsigned)(16 * m->sm_count)));
 }
 
 // ---- binary16 correction storage: per-level power-of-two scale ----
@@ -377,7 +401,7 @@ void launch_build_rhs32(hhg_mesh_s* m, int l, cudaStream_t s);
 void launch_residual(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s);
 
 void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
-  hhg_launch(k_to_f32, blocks_for(n), kBlock, 0, s, a, b, n);
+  hhg_launch(k_to_f32, std::max(1u, std::min<unsigned>(blocks_for((n + 3) / 4), 16u * 152u)), kBlock, 0, s, a, b, n);
 }
 void launch_to_f64(const float* a, double* b, int64_t n, cudaStream_t s) {
   hhg_launch(k_to_f64, blocks_for(n), kBlock, 0, s, a, b, n);
@@ -404,7 +428,7 @@ static void ir_residual(hhg_mesh_s* m, cudaStream_t s) {
   if (DIM == 3 && PF.count && nf > 0)
     hhg_launch(k_owner_collect<DIM>, blocks_for((int64_t)PF.count * nf), kBlock, 0, s, 
         PF.count, 3, (int)nf, LL.d_fcol, PF.d_ptr, PF.d_cell, PF.d_loc, ctx(m, L), LL.tmp);
-  hhg_launch(k_to_f32, blocks_for(LL.N), kBlock, 0, s, LL.tmp, LL.r32, LL.N);
+  hhg_launch(k_to_f32, elementwise_blocks(m, LL.N), kBlock, 0, s, LL.tmp, LL.r32, LL.N);
 }
 void launch_finite_check(hhg_mesh_s* m, const double* v, int64_t n, cudaStream_t s);
 
@@ -415,7 +439,7 @@ static void mixed_solve_t(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t
   // binary64 b_L (the refinement's residual right-hand side) and its binary32 copy for the binary32
   // FMG's top level; the coarser right-hand sides only serve the binary32 FMG: built in binary32
   launch_build_rhs(m, L, s);
-  hhg_launch(k_to_f32, blocks_for(LL.N), kBlock, 0, s, LL.b, LL.b32, LL.N);
+  hhg_launch(k_to_f32, elementwise_blocks(m, LL.N), kBlock, 0, s, LL.b, LL.b32, LL.N);
   if (p.rhs == 0) {
     for (int l = 0; l < L; ++l) launch_build_rhs32(m, l, s);
   } else {  // b_{l-1} = I^T b_l from the binary32 copy of b_L
@@ -449,13 +473,13 @@ static void mixed_solve_t(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t
     ir_residual<DIM>(m, s);
     cudaMemsetAsync(LL.x32, 0, sizeof(float) * (size_t)LL.N, s);
     for (int q = 0; q < p.ir_vcycles; ++q) vcycle32<DIM, S, float>(m, L, LL.x32, LL.r32, p, s);
-    hhg_launch(k_add_f32, blocks_for(LL.N), kBlock, 0, s, LL.x32, LL.u, LL.N);
+    hhg_launch(k_add_f32, elementwise_blocks(m, LL.N), kBlock, 0, s, LL.x32, LL.u, LL.N);
   }
   for (int q = 0; q < p.n_extra; ++q) {
     ir_residual<DIM>(m, s);
     cudaMemsetAsync(LL.x32, 0, sizeof(float) * (size_t)LL.N, s);
     vcycle32<DIM, S, float>(m, L, LL.x32, LL.r32, p, s);
-    hhg_launch(k_add_f32, blocks_for(LL.N), kBlock, 0, s, LL.x32, LL.u, LL.N);
+    hhg_launch(k_add_f32, elementwise_blocks(m, LL.N), kBlock, 0, s, LL.x32, LL.u, LL.N);
   }
   cudaMemsetAsync(m->d_flag, 0, sizeof(int), s);
   launch_finite_check(m, LL.u, LL.N, s);
@@ -469,7 +493,7 @@ static void ir_step(hhg_mesh_s* m, int nv, const hhg_solve_params& p, cudaStream
   ir_residual<DIM>(m, s);
   cudaMemsetAsync(LL.x32, 0, sizeof(float) * (size_t)LL.N, s);
   for (int q = 0; q < nv; ++q) vcycle32<DIM, S, float>(m, m->L, LL.x32, LL.r32, p, s);
-  hhg_launch(k_add_f32, blocks_for(LL.N), kBlock, 0, s, LL.x32, LL.u, LL.N);
+  hhg_launch(k_add_f32, elementwise_blocks(m, LL.N), kBlock, 0, s, LL.x32, LL.u, LL.N);
 }
 
 // Mixed-precision adjoint solve A lam = b_L, where b_L holds the adjoint right-hand side and the
