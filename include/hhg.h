@@ -146,7 +146,10 @@ hhg_status hhg_fmg_solve(hhg_mesh mesh, const hhg_solve_params* params, double* 
 /* ErrorEstimate of Alg. 4 with offset j (1 <= j <= L-1) on the last solve.
  * eta_T: host, n_cells (may be NULL): ||u_L - w_{L-1}||_{L2(T)} over the micro elements of
  * macro T including its boundary (eta'_{1,T}, Eq. 4.14).  eta_jT: host, n_cells (may be NULL):
- * scaled local estimate theta~_{l,T}^j ||e~_l||_T (Eq. 4.10).  out: host, global values. */
+ * scaled local estimate theta~_{l,T}^j ||e~_l||_T (Eq. 4.10).  out: host, global values.
+ * Arithmetic: each difference u_L - I w is formed in binary64; the per-cell quadratic forms are
+ * evaluated in binary32 hi/lo pairs with exact products and sums (about 2^-44 relative per node),
+ * the per-cell sums in binary64 in a fixed order (deterministic). */
 hhg_status hhg_estimate(hhg_mesh mesh, int j, double* eta_T, double* eta_jT, hhg_estimate_out* out);
 
 /* hhg_estimate in another norm (Remark in Sec. 4).  norm 0: L2 (= hhg_estimate).  norm 1: energy,
@@ -244,12 +247,13 @@ int hhg_lattice_selfcheck(int dim, int n);
 
 /* Profiling support (no counterpart in the paper).  Enqueue `reps` launches of one kernel of the solve on the mesh's stream,
  * exactly as the solve launches it, without synchronising (bracket it with events on that stream).
- * kernel 0: the macro-interior smoothing of level L for the first cell group: precision 0, the
- * binary64 colour-0 stage; precision 1, the binary32 interior sweep as the mixed solve runs it (in 3D
- * one launch for all colours where it fits in shared memory, else the colour-0 stage);
+ * kernel 0: the macro-interior smoothing of level L for the first cell group, the colour-0 stage:
+ * precision 0 binary64, precision 1 binary32 as the mixed solve runs it (four cells per thread);
  * kernel 1 (3D, binary64): the level-L macro-face stage (units only; bytes = flops = 0);
- * kernels 2, 3, 4 (binary64): the level-L prolongation-add, residual (every node computed) and
- * estimator mass form of one vector (units = level-L nodes).
+ * kernels 2, 3 (binary64): the level-L prolongation-add and residual (every node computed);
+ * kernel 4: the estimator's per-cell L2 form of one level-L vector, evaluated in binary32 hi/lo
+ * pairs as hhg_estimate does (the vector is split into pairs once, before the launches);
+ * units of kernels 2-4 = level-L nodes.
  * precision 1 allocates the mixed path's buffers on first use.  units: nodes updated per launch;
  * bytes / flops: algorithmic bytes and floating-point operations of one launch (the model is stated
  * in the library's design notes).  The launches modify the level-L iterate: run a solve again before

@@ -440,6 +440,7 @@ static hhg_status estimate_impl(hhg_mesh m, int j, int norm, const double* wts, 
   CHECK_PTR(m->lv[l - 1].w);
   CHECK_PTR(m->d_part);
   CHECK_PTR(m->dM);
+  CHECK_PTR(m->dMp);
   CHECK_PTR(m->dS);
   CHECK_PTR(m->lv[L].d_ijk);
   CHECK_PTR(m->lv[L].tmp);
@@ -451,31 +452,43 @@ static hhg_status estimate_impl(hhg_mesh m, int j, int norm, const double* wts, 
     else launch_mass_norm_sq(m, x, nullptr, dst, cs);
   };
   // The differences are formed once into level-L scratch (rc is never a coarse-grid rhs on level L,
-  // tmp is free after the solve), so the per-cell form reads one vector.
+  // tmp is free after the solve), so the per-cell form reads one vector.  The L2 forms take the
+  // difference in binary64 and evaluate the quadratic form in binary32 hi/lo pairs (the mass
+  // stencil's couplings would otherwise keep GB300's binary64 pipe busy); the energy form stays in
+  // binary64.
   double* xa = m->lv[L].rc;
   double* xb = m->lv[L].tmp;
+  auto diff = [&](const double* v, double* x, cudaStream_t cs) {  // x = u_L - v on level L
+    if (energy) launch_sub(m, uL, v, x, m->lv[L].N, cs);
+    else launch_sub_pair(m, uL, v, (float2*)x, m->lv[L].N, cs);
+  };
+  auto form_x = [&](const double* x, double* dst, cudaStream_t cs) {
+    if (energy) form(x, dst, cs);
+    else launch_mass_norm_sq_pair(m, (const float2*)x, dst, cs);
+  };
+  // x_L = u_L - I^(L-l0) v for v on level l0 < L (the intermediate levels in binary64)
+  auto diff_prolonged = [&](const double* v, int l0, double* x, cudaStream_t cs) {
+    for (int q = l0 + 1; q < L; ++q) {
+      launch_prolong(m, q, v, m->lv[q].tmp, cs, nullptr);
+      v = m->lv[q].tmp;
+    }
+    if (energy) launch_prolong(m, L, v, x, cs, uL);
+    else launch_prolong_diff_pair(m, v, uL, (float2*)x, cs);
+  };
   hhg_status st = run_graph(m, "est:" + std::to_string(jj) + (energy ? ":energy" : ""), [&](cudaStream_t cs) {
     // e~_{L-1} = u_L - w_{L-1} (eta_T)
-    launch_sub(m, uL, m->lv[L - 1].w, xa, m->lv[L].N, cs);
-    form(xa, red, cs);
+    diff(m->lv[L - 1].w, xa, cs);
+    form_x(xa, red, cs);
     // e~_l = u_L - I w_l (w_l lives on level l+1); for j = 1 it is e~_{L-1} again
     if (l == L - 1) {
       cudaMemcpyAsync(red + nc, red, sizeof(double) * nc, cudaMemcpyDeviceToDevice, cs);
     } else {
-      const double* v = m->lv[l].w;
-      for (int q = l + 2; q <= L; ++q) {
-        launch_prolong(m, q, v, m->lv[q].tmp, cs, q == L ? uL : nullptr);
-        v = m->lv[q].tmp;
-      }
-      form(xb, red + nc, cs);
+      diff_prolonged(m->lv[l].w, l + 1, xb, cs);
+      form_x(xb, red + nc, cs);
     }
     // e~_{l-1} = u_L - I w_{l-1} (w_{l-1} lives on level l)
-    const double* v = m->lv[l - 1].w;
-    for (int q = l + 1; q <= L; ++q) {
-      launch_prolong(m, q, v, m->lv[q].tmp, cs, q == L ? uL : nullptr);
-      v = m->lv[q].tmp;
-    }
-    form(xb, red + 2 * nc, cs);
+    diff_prolonged(m->lv[l - 1].w, l, xb, cs);
+    form_x(xb, red + 2 * nc, cs);
   });
   if (st != HHG_OK) return st;
   DBG_SYNC("estimator graph");

@@ -97,6 +97,8 @@ struct hhg_mesh_s {
   double* dM = nullptr;           // mass stencils (unit level scale)
   float* dS32 = nullptr;
   float* dM32 = nullptr;
+  float2* dMp = nullptr;          // mass stencils as binary32 hi/lo pairs (estimator, mixed b_L)
+  float2* dSp = nullptr;          // stiffness stencils with k_T as hi/lo pairs (mixed refinement)
   double* d_inv0 = nullptr;       // 1 / interior diagonal per cell (unit level scale, with k_T)
   float* d_inv0f = nullptr;
   double* d_tnorm = nullptr;      // per cell: interior stencil divided by its diagonal [cell][16]
@@ -165,6 +167,10 @@ void launch_level_coords(hhg_mesh_s* m, int l, const double* geom, double* xyz, 
 void launch_finite_check(hhg_mesh_s* m, const double* v, int64_t n, cudaStream_t s);
 // per-cell reductions on level L: out[T] = (a-b)^T M_T (a-b), b may be null
 void launch_mass_norm_sq(hhg_mesh_s* m, const double* a, const double* b, double* out, cudaStream_t s);
+// the estimator's pair form: x as binary32 hi/lo pairs (k_sub_pair / k_prolong_diff_pair)
+void launch_mass_norm_sq_pair(hhg_mesh_s* m, const float2* x, double* out, cudaStream_t s);
+void launch_sub_pair(hhg_mesh_s* m, const double* a, const double* b, float2* x, int64_t n, cudaStream_t s);
+void launch_prolong_diff_pair(hhg_mesh_s* m, const double* coarse, const double* minuend, float2* x, cudaStream_t s);
 // out[T] = (a-b)^T A_T (a-b) with the cell's stiffness (k_T included), b may be null
 void launch_energy_norm_sq(hhg_mesh_s* m, const double* a, const double* b, double* out, cudaStream_t s);
 // out[T] = x^T A_T^(1) y (unit-coefficient partial stiffness of cell T), level L

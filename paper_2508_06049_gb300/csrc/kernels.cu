@@ -35,6 +35,25 @@ __global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b
   if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) x[n - 1] = a[n - 1] - b[n - 1];
 }
 
+// x = a - b (b may be null: x = a) in binary64, stored as its binary32 hi/lo pair (df_split) in the
+// same 8 bytes per value: the estimator's difference vector for k_node_form_pair
+__global__ void k_sub_pair(const double* __restrict__ a, const double* __restrict__ b, float2* __restrict__ x,
+                           int64_t n) {
+  grid_dependency_sync();
+  const int64_t n2 = n / 2;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+    double2 p = reinterpret_cast<const double2*>(a)[i];
+    if (b) {
+      const double2 q = reinterpret_cast<const double2*>(b)[i];
+      p.x -= q.x;
+      p.y -= q.y;
+    }
+    const float2 h0 = df_split(p.x), h1 = df_split(p.y);
+    reinterpret_cast<float4*>(x)[i] = make_float4(h0.x, h0.y, h1.x, h1.y);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) x[n - 1] = df_split(b ? a[n - 1] - b[n - 1] : a[n - 1]);
+}
+
 // Level-l node coordinates x = x_0 + J p / n of every cell's closure lattice (hhg_level_coords into
 // device memory).  geom: per cell x_0 (3) and J row-major (3 x 3).  The products and sums are
 // rounded separately, in the host path's order, so both paths give the same bits.
@@ -313,6 +332,27 @@ static void cell_form(hhg_mesh_s* m, bool diff, const double* tab, double scale,
   hhg_launch(k_cell_sum, m->nc, kBlock, 0, s, (int64_t)grid.x, scale, contrib, out);
 }
 
+// Per-cell squared mass norm of a difference vector held as binary32 hi/lo pairs on level L.
+void launch_mass_norm_sq_pair(hhg_mesh_s* m, const float2* x, double* out, cudaStream_t s) {
+  const LevelData& Lv = m->lv[m->L];
+  dim3 grid(blocks_for(Lv.Nt, kBlock * kFormNodes), m->nc);
+  if (m->dim == 2) hhg_launch(k_node_form_pair<2>, grid, kBlock, 0, s, ctx(m, m->L), (const float2*)m->dMp, x, m->d_part);
+  else hhg_launch(k_node_form_pair<3>, grid, kBlock, 0, s, ctx(m, m->L), (const float2*)m->dMp, x, m->d_part);
+  hhg_launch(k_cell_sum, m->nc, kBlock, 0, s, (int64_t)grid.x, mass_scale(m->dim, Lv.n), m->d_part, out);
+}
+
+void launch_sub_pair(hhg_mesh_s* m, const double* a, const double* b, float2* x, int64_t n, cudaStream_t s) {
+  hhg_launch(k_sub_pair, 16 * m->sm_count, kBlock, 0, s, a, b, x, n);
+}
+
+// x_L = minuend - I v on level L (v on level L-1) as binary32 hi/lo pairs
+void launch_prolong_diff_pair(hhg_mesh_s* m, const double* coarse, const double* minuend, float2* x, cudaStream_t s) {
+  const int l = m->L;
+  const LevelData& F = m->lv[l];
+  dim3 grid(blocks_for(F.Nt), m->nc);
+  DISPATCH_DIM(m, k_prolong_diff_pair, grid, kBlock, 0, s, ctx(m, l), ctx(m, l - 1), coarse, minuend, x);
+}
+
 void launch_mass_norm_sq(hhg_mesh_s* m, const double* a, const double* b, double* out, cudaStream_t s) {
   cell_form(m, true, m->dM, mass_scale(m->dim, m->lv[m->L].n), a, b, out, s);
 }
@@ -398,13 +438,15 @@ void launch_profile_level(hhg_mesh_s* m, int kernel, int reps, cudaStream_t s, l
     *bytes = 8.0 * 3.0 * N;
     *flops = (2.0 * (1 + 2 * __builtin_popcount(m->groups[0].pmask)) + 2.0) * N;
   } else {
-    *bytes = 8.0 * 2.0 * N;
+    // the pair form reads x once (8 bytes per node); flops: the form's binary64-equivalent count
+    *bytes = 8.0 * N;
     *flops = 2.0 * (ndirs_of(m->dim) + 1) / 2 * N + 2.0 * N;
+    launch_sub_pair(m, Lv.u, nullptr, (float2*)Lv.tmp, Lv.N, s);
   }
   for (int r = 0; r < reps; ++r) {
     if (kernel == 2) launch_prolong_add(m, L, s);
     else if (kernel == 3) launch_residual(m, L, Lv.b, s);
-    else launch_mass_norm_sq(m, Lv.u, nullptr, m->d_red, s);
+    else launch_mass_norm_sq_pair(m, (const float2*)Lv.tmp, m->d_red, s);
   }
 }
 
@@ -437,7 +479,8 @@ hhg_status preload_kernels() {
       (const void*)k_node_form<2, true>, (const void*)k_node_form<3, true>, (const void*)k_node_form<2, false>,
       (const void*)k_node_form<3, false>, (const void*)k_cell_sum, (const void*)k_apply_partial<2>,
       (const void*)k_apply_partial<3>, (const void*)k_sum_prims<2>, (const void*)k_sum_prims<3>,
-      (const void*)k_finite, (const void*)k_sub};
+      (const void*)k_finite, (const void*)k_sub, (const void*)k_sub_pair, (const void*)k_node_form_pair<2>,
+      (const void*)k_node_form_pair<3>, (const void*)k_prolong_diff_pair<2>, (const void*)k_prolong_diff_pair<3>};
   for (const void* f : fns) {
     cudaError_t e = cudaFuncGetAttributes(&fa, f);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");

@@ -8,6 +8,7 @@
 #include <utility>
 
 #include "device_common.cuh"
+#include "dfloat.cuh"
 
 namespace hhg {
 
@@ -958,6 +959,22 @@ __global__ void k_fmg_prolong(LevelCtx fc, LevelCtx cc, int nL, int64_t NtL, int
   if (w) w[g] = v;
 }
 
+// the estimator's difference u_L - I w_c in binary64, stored as its binary32 hi/lo pair (df_split)
+// for k_node_form_pair
+template <int DIM>
+__global__ void k_prolong_diff_pair(LevelCtx fc, LevelCtx cc, const double* __restrict__ vc,
+                                    const double* __restrict__ minuend, float2* __restrict__ xf) {
+  grid_dependency_sync();
+  int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (loc >= fc.Nt) return;
+  int T = blockIdx.y;
+  int i, j, k;
+  decode(fc.ijk[loc], i, j, k);
+  int64_t g = (int64_t)T * fc.Nt + loc;
+  double v = interp<DIM, double>(cc, T, i, j, k, CVec<double, double>{vc, nullptr});
+  xf[g] = df_split(minuend[g] - v);
+}
+
 // plain interpolation v_f = I v_c (all nodes)
 template <int DIM>
 // vf = I vc, or vf = minuend - I vc when minuend is given (the estimator's difference u_L - I w)
@@ -1108,6 +1125,51 @@ __global__ void __launch_bounds__(kBlock) k_node_form(LevelCtx lc, const double*
     tsum += sum;
   }
   const double tot = block_sum_fixed(tsum, wsum);
+  if (threadIdx.x == 0) part[(int64_t)T * gridDim.x + blockIdx.x] = tot;
+}
+
+// The estimator's squared mass norm of a difference vector x per cell, in binary32 pairs: x is read
+// as the hi/lo pairs written by k_sub_pair / k_prolong_diff_pair, the mass stencil as hi/lo pairs
+// of its binary64 values, and x_p (s0 x_p + 2 sum s_d x_q) over the half stencil is accumulated with
+// exact products and sums (dfloat.cuh), about 2^-44 relative per node.  Same blocking and block
+// sums as k_node_form (one binary64 value per block, fixed order).
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_node_form_pair(LevelCtx lc, const float2* __restrict__ tab,
+                                                           const float2* __restrict__ x, double* __restrict__ part) {
+  grid_dependency_sync();
+  __shared__ double wsum[kBlock / 32];
+  const int T = blockIdx.y;
+  DfAcc tsum;
+  for (int r = 0; r < kFormNodes; ++r) {
+    const int64_t loc = ((int64_t)blockIdx.x * kFormNodes + r) * kBlock + threadIdx.x;
+    if (loc < lc.Nt) {
+      int i, j, k;
+      decode(lc.ijk[loc], i, j, k);
+      const int t = boundary_type(DIM, lc.n, i, j, k);
+      const int64_t g = (int64_t)T * lc.Nt + loc;
+      int64_t off[15];
+      neighbour_offsets(DIM, lc.n, j, k, off);
+      const uint32_t vm = valid_dirs_tab(DIM, t);
+      mask_offsets(DIM, vm, off);
+      const float2* s = tab + (size_t)T * kStencilStride + t * kMaxDirs;
+      const float2 xp = x[g];
+      float2 xq[npairs<DIM>()];
+#pragma unroll
+      for (int q = 0; q < npairs<DIM>(); ++q) {
+        const int d = 2 * q + 1;
+        const bool ok = (vm >> d & 1) && !HHG_OOB(loc + off[d], lc.Nt, 13);
+        xq[q] = ok ? x[g + off[d]] : make_float2(0.f, 0.f);
+      }
+      DfAcc ay;
+#pragma unroll
+      for (int q = 0; q < npairs<DIM>(); ++q) ay.add_prod(s[2 * q + 1], xq[q]);
+      ay.hi = __fmul_rn(ay.hi, 2.f);  // exact
+      ay.lo = __fmul_rn(ay.lo, 2.f);
+      ay.add_prod(s[0], xp);
+      tsum.add_prod(xp, ay.value());
+    }
+  }
+  const double tot = block_sum_fixed(df_to_double(tsum.value()), wsum);
   if (threadIdx.x == 0) part[(int64_t)T * gridDim.x + blockIdx.x] = tot;
 }
 

@@ -346,6 +346,15 @@ hhg_status upload_coefficient(hhg_mesh_s* m) {
   }
   CK(cudaMemcpy(m->dS32, S32.data(), S32.size() * sizeof(float), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(m->dM32, M32.data(), M32.size() * sizeof(float), cudaMemcpyHostToDevice));
+  {
+    // hi = the binary32 rounding of the entry, lo = the binary32 rounding of the rest
+    std::vector<float2> Sp(S.size());
+    for (size_t q = 0; q < S.size(); ++q) {
+      const float h = (float)S[q];
+      Sp[q] = make_float2(h, (float)(S[q] - (double)h));
+    }
+    CK(cudaMemcpy(m->dSp, Sp.data(), Sp.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  }
   // inverse assembled diagonal of each primitive's interior nodes: the sum over its cell copies of
   // the centre entry of the copy's partial stencil (the copy's boundary type is the same for all
   // interior nodes of the primitive)
@@ -675,7 +684,17 @@ hhg_status build_mesh(hhg_mesh_s* m, const double* coords, const int* cells, con
   if ((st = dalloc(m, &m->dS, (size_t)nc * NS)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->d_nzs, (size_t)nc * kMaxTypes)) != HHG_OK) return st;
   if ((st = upload(m, &m->dM, m->hM)) != HHG_OK) return st;
+  {
+    // hi = the binary32 rounding of the entry, lo = the binary32 rounding of the rest
+    std::vector<float2> Mp(m->hM.size());
+    for (size_t q = 0; q < m->hM.size(); ++q) {
+      const float h = (float)m->hM[q];
+      Mp[q] = make_float2(h, (float)(m->hM[q] - (double)h));
+    }
+    if ((st = upload(m, &m->dMp, Mp)) != HHG_OK) return st;
+  }
   if ((st = dalloc(m, &m->dS32, (size_t)nc * NS)) != HHG_OK) return st;
+  if ((st = dalloc(m, &m->dSp, (size_t)nc * NS)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->dM32, (size_t)nc * NS)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->d_inv0, (size_t)nc)) != HHG_OK) return st;
   if ((st = dalloc(m, &m->d_inv0f, (size_t)nc)) != HHG_OK) return st;
@@ -822,7 +841,7 @@ void free_mesh(hhg_mesh_s* m) {
   };
   for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second);
   m->graphs.clear();
-  F(m->dS); F(m->dM); F(m->dS32); F(m->dM32); F(m->d_inv0); F(m->d_inv0f); F(m->d_tnorm); F(m->d_tnormf);
+  F(m->dS); F(m->dM); F(m->dMp); F(m->dSp); F(m->dS32); F(m->dM32); F(m->d_inv0); F(m->d_inv0f); F(m->d_tnorm); F(m->d_tnormf);
   F(m->d_dirmask); F(m->d_nzs);
   for (hhg::Prims* P : {&m->verts, &m->edges, &m->faces}) {
     F(P->d_ptr); F(P->d_cell); F(P->d_loc); F(P->d_dir); F(P->d_pinv); F(P->d_pinvf); F(P->d_fw); F(P->d_fwf);

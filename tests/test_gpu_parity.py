@@ -410,6 +410,33 @@ def _sampled_estimator_parity(P, co, ce, L, f, g, n_sample=4):
     mesh.close()
 
 
+@pytest.mark.parametrize("name", ["lshape_pert", "cube_pert_k"])
+def test_estimator_pair_form_against_binary64_forms(P, name):
+    """hhg_estimate evaluates its per-cell L2 forms in binary32 hi/lo pairs.  Against the binary64
+    form e^T M_T e of the library's own u_L and w_{L-1} (e = u_L - w_{L-1} on each cell's closure,
+    M_T from a one-cell oracle hierarchy), every cell agrees to 1e-12 relative: the pair arithmetic
+    keeps about 2^-44 per node, far inside the 1e-10 of the oracle comparisons."""
+    co, ce, L, k, h, mesh, maps = setup_case(P, name)
+    f, g = fg(co.shape[1])
+    x = mesh.level_coords(L)
+    mesh.set_data(np.ascontiguousarray(f(x)), np.ascontiguousarray(g(x)))
+    u = mesh.solve(nu=2, pre=2, post=1, n_extra=1)
+    w = mesh.get_vector(1, L - 1)
+    est = mesh.estimate(1)
+    nc, dim = len(ce), co.shape[1]
+    Nt = len(x) // nc
+    worst = 0.0
+    for T in range(nc):
+        lev = O.Hierarchy(co[ce[T]], np.arange(dim + 1)[None, :], L).levels[L]
+        sl = slice(T * Nt, (T + 1) * Nt)
+        dist, idx = cKDTree(x[sl]).query(lev.x)
+        assert dist.max() < 1e-9
+        e = (u[sl] - w[sl])[idx]
+        ref = float(e @ (lev.M @ e))
+        worst = max(worst, abs(est["eta_T"][T] ** 2 - ref) / ref)
+    assert worst <= 1e-12, worst
+
+
 @pytest.mark.parametrize("name", ["lshape", "cube"])
 def test_level_coords_device_path_matches_host_path(P, name):
     """hhg_level_coords into device memory (one kernel) gives the host path's coordinates bit for
