@@ -28,7 +28,8 @@
  *     mesh creates its own non-blocking stream and, at every entry point, orders it after the work
  *     the caller queued on the legacy default stream.  Functions that return host results (and
  *     hhg_fmg_solve, which checks its result for NaN/Inf) synchronise that stream before returning.
- *   - Floating-point is IEEE binary64 unless the solve parameters select the mixed mode.
+ *   - Floating-point is IEEE binary64 unless the solve parameters select the mixed mode, except
+ *     the L2 forms of hhg_estimate (binary32 hi/lo pairs, see there).
  */
 #ifndef HHG_H
 #define HHG_H
@@ -57,8 +58,11 @@ typedef enum {
  * before/after the coarse correction; n_extra: extra V-cycles on level L after FMG (they do
  * not update w_l, Sec. 5).
  * precision = 0: every step in binary64.
- * precision = 1 (mixed, no counterpart in the paper): iterative refinement whose residual
- *   r = b - A u and update u += c are binary64 on level L; the correction c solves A c = r with
+ * precision = 1 (mixed, no counterpart in the paper): iterative refinement whose level-L right-hand
+ *   side b_L = M_L f_L, residual r = b - A u and iterate u (updated u += c) are carried as pairs of
+ *   binary32 values with exact products and sums (about 2^-46 relative per operation, which bounds
+ *   the attainable algebraic accuracy near 4^L * 2^-46 relative; u_L is returned in binary64,
+ *   b_L kept in binary64); the correction c solves A c = r with
  *   FMG (first step) or ir_vcycles V-cycles (later steps) computed in binary32, with the level
  *   vectors of the correction stored as `storage` (0 = binary32, 1 = bfloat16, 2 = binary16) and
  *   accumulated in binary32.  ir_steps refinement steps follow the first one.
@@ -227,7 +231,8 @@ hhg_status hhg_rg3d_mark_refine(hhg_rg3d rg, const double* eta_T, double fractio
  * M_S the mass matrix of the micro elements inside the macro cells flagged in in_S, on the
  * solution of the last hhg_fmg_solve, solve A lambda = 2 M_S u (lambda = 0 on Dirichlet nodes)
  * and return the results below.  params->precision = 0: FMG + params->n_extra V-cycles in binary64.
- * precision = 1: binary64 refinement from lambda = 0 whose corrections come from binary32
+ * precision = 1: refinement on binary32 pairs (as in hhg_fmg_solve) from lambda = 0 whose
+ * corrections come from binary32
  * V-cycles stored as params->storage (as in hhg_fmg_solve): a first step of ir_vcycles V-cycles
  * (the adjoint right-hand side is given on level L only, so there is no binary32 FMG step), then
  * ir_steps steps of ir_vcycles V-cycles and n_extra steps of one.  The results are

@@ -7,8 +7,11 @@
 //         binary16 has five exponent bits, so each level's correction is stored times a power of two
 //         chosen, after the restriction, from max |r| of its right-hand side and a bound of
 //         |A_l^{-1}|_inf (k_set_scale16).
-// Steps 2..: r = b_L - A_L u_L and u_L += c in binary64 on level L; the correction c solves
-//         A_L c = r with V-cycles computed in binary32 (same storage rule for the coarse levels).
+// Steps 2..: r = b_L - A_L u_L and u_L += c on level L, carried in pairs of binary32 values with
+//         exact products and sums (about 2^-46 relative per operation, against binary64's 2^-53;
+//         GB300 runs binary32 at 64 times its binary64 rate); the correction c solves A_L c = r with
+//         V-cycles computed in binary32 (same storage rule for the coarse levels).  u_L is returned
+//         in binary64.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -41,11 +44,30 @@ __global__ void k_to_f64(const float* __restrict__ a, double* __restrict__ b, in
   if (i < n) b[i] = (double)a[i];
 }
 
-// level-L binary64 iterate from the binary32 FMG result; Dirichlet nodes take the exact binary64 g
-// (the binary32 copy of g would perturb the boundary data the refinement converges to)
+// grid of the vectorised elementwise kernels: enough blocks to fill the GPU several times over
+inline unsigned elementwise_blocks(const hhg_mesh_s* m, int64_t n) {
+  return std::max(1u, std::min<unsigned>(blocks_for((n + 3) / 4), (unsigned)(16 * m->sm_count)));
+}
+// the same for the kernels that take two values per access
+inline unsigned pair_blocks(const hhg_mesh_s* m, int64_t n) {
+  return std::max(1u, std::min<unsigned>(blocks_for((n + 1) / 2), (unsigned)(16 * m->sm_count)));
+}
+
+// ---- refinement on level L in binary32 hi/lo pairs ----
+// The level-L iterate u_L, the right-hand side b_L and the residual of the refinement steps need
+// more than binary32; GB300 runs binary64 at 2 FMA per SM and clock against 128 for binary32, so
+// they are carried as pairs of binary32 values with exact products and sums (dfloat.cuh): u_L as a
+// pair per node (in the 8 bytes of its binary64 slot), b_L formed from pairs and stored in binary64,
+// the residual as pairs until its interface partials are collected.  At the end u_L is written back
+// in binary64.
+
+// b_L = M_L f_L from f_L as pairs (fp, split once by k_sub_pair) and the mass stencils as pairs;
+// stored in binary64 (b) and rounded to binary32 (b32); zero on Dirichlet rows.  mscale: the level's
+// mass scale, a power of two (exact on pairs).
 template <int DIM>
-__global__ void k_to_f64_level(LevelCtx lc, const uint16_t* __restrict__ dirmask, const double* __restrict__ gL,
-                               const float* __restrict__ x, double* __restrict__ u) {
+__global__ void k_build_rhs_pair(LevelCtx lc, const float2* __restrict__ fp, const float2* __restrict__ Mp,
+                                 float mscale, const uint16_t* __restrict__ dirmask, double* __restrict__ b,
+                                 float* __restrict__ b32) {
   grid_dependency_sync();
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (loc >= lc.Nt) return;
@@ -54,31 +76,154 @@ __global__ void k_to_f64_level(LevelCtx lc, const uint16_t* __restrict__ dirmask
   decode(lc.ijk[loc], i, j, k);
   int t = boundary_type(DIM, lc.n, i, j, k);
   int64_t g = (int64_t)T * lc.Nt + loc;
-  u[g] = (dirmask[T] >> t & 1) ? gL[g] : (double)x[g];
-}
-
-// u += c (binary64 accumulate of a binary32 correction; c is zero on Dirichlet nodes); vectorised
-// like k_to_f32
-__global__ void k_add_f32(const float* __restrict__ c, double* __restrict__ u, int64_t n) {
-  grid_dependency_sync();
-  const int64_t n4 = n / 4;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-    const float4 d = reinterpret_cast<const float4*>(c)[i];
-    double2 x = reinterpret_cast<double2*>(u)[2 * i], y = reinterpret_cast<double2*>(u)[2 * i + 1];
-    x.x += (double)d.x;
-    x.y += (double)d.y;
-    y.x += (double)d.z;
-    y.y += (double)d.w;
-    reinterpret_cast<double2*>(u)[2 * i] = x;
-    reinterpret_cast<double2*>(u)[2 * i + 1] = y;
+  if (dirmask[T] >> t & 1) {
+    b[g] = 0.0;
+    b32[g] = 0.f;
+    return;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0)
-    for (int64_t i = 4 * n4; i < n; ++i) u[i] += (double)c[i];
+  const uint32_t vm = valid_dirs_tab(DIM, t);
+  const float2* sm = Mp + (size_t)T * kStencilStride + t * kMaxDirs;
+  int64_t off[15];
+  neighbour_offsets(DIM, lc.n, j, k, off);
+  mask_offsets(DIM, vm, off);
+  float2 f[ndirs<DIM>()];
+#pragma unroll
+  for (int d = 0; d < ndirs<DIM>(); ++d) {
+    const bool ok = (vm >> d & 1) && !HHG_OOB(loc + off[d], lc.Nt, 71);
+    f[d] = ok ? fp[g + off[d]] : make_float2(0.f, 0.f);
+  }
+  DfAcc acc;
+#pragma unroll
+  for (int d = 0; d < ndirs<DIM>(); ++d) acc.add_prod(sm[d], f[d]);
+  float2 v = acc.value();
+  v.x = __fmul_rn(v.x, mscale);
+  v.y = __fmul_rn(v.y, mscale);
+  b[g] = df_to_double(v);
+  b32[g] = __fadd_rn(v.x, v.y);
 }
 
-// grid of the vectorised elementwise kernels: enough blocks to fill the GPU several times over
-inline unsigned elementwise_blocks(const hhg_mesh_s* m, int64_t n) {
-  return std::max(1u, std::min<unsigned>(blocks_for((n + 3) / 4), (unsigned)(16 * m->sm_count)));
+// u_L as pairs from the binary32 FMG result; Dirichlet nodes take the binary64 g split into a pair
+template <int DIM>
+__global__ void k_to_pair_level(LevelCtx lc, const uint16_t* __restrict__ dirmask, const double* __restrict__ gL,
+                                const float* __restrict__ x, float2* __restrict__ up) {
+  grid_dependency_sync();
+  int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (loc >= lc.Nt) return;
+  int T = blockIdx.y;
+  int i, j, k;
+  decode(lc.ijk[loc], i, j, k);
+  int t = boundary_type(DIM, lc.n, i, j, k);
+  int64_t g = (int64_t)T * lc.Nt + loc;
+  up[g] = (dirmask[T] >> t & 1) ? df_split(gL[g]) : make_float2(x[g], 0.f);
+}
+
+// partial residual r = b - ss A_T u of every closure node (cell copy), u and r as pairs, b in
+// binary64 (split per node); zero on Dirichlet rows.  ss: the level's stiffness scale, a power of two.
+template <int DIM>
+__global__ void k_residual_pair(LevelCtx lc, const float2* __restrict__ Sp, const uint16_t* __restrict__ dirmask,
+                                float ss, const double* __restrict__ b, const float2* __restrict__ up,
+                                float2* __restrict__ r) {
+  grid_dependency_sync();
+  int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (loc >= lc.Nt) return;
+  int T = blockIdx.y;
+  int i, j, k;
+  decode(lc.ijk[loc], i, j, k);
+  int t = boundary_type(DIM, lc.n, i, j, k);
+  int64_t g = (int64_t)T * lc.Nt + loc;
+  if (dirmask[T] >> t & 1) {
+    r[g] = make_float2(0.f, 0.f);
+    return;
+  }
+  const uint32_t vm = valid_dirs_tab(DIM, t) & lc.nzs[T * kMaxTypes + t];
+  const float2* st = Sp + (size_t)T * kStencilStride + t * kMaxDirs;
+  int64_t off[15];
+  neighbour_offsets(DIM, lc.n, j, k, off);
+  mask_offsets(DIM, vm, off);
+  float2 uq[ndirs<DIM>()];
+#pragma unroll
+  for (int d = 0; d < ndirs<DIM>(); ++d) {
+    const bool ok = (vm >> d & 1) && !HHG_OOB(loc + off[d], lc.Nt, 72);
+    uq[d] = ok ? up[g + off[d]] : make_float2(0.f, 0.f);
+  }
+  DfAcc acc;
+#pragma unroll
+  for (int d = 0; d < ndirs<DIM>(); ++d)
+    if (vm >> d & 1) acc.add_prod(st[d], uq[d]);
+  const float2 au = acc.value();
+  DfAcc res;
+  res.add(df_split(b[g]));
+  res.add(make_float2(-__fmul_rn(au.x, ss), -__fmul_rn(au.y, ss)));
+  r[g] = res.value();
+}
+
+// the pair partials of each interface node summed into its first copy, the other copies set to 0
+// (k_owner_collect on pairs)
+template <int DIM>
+__global__ void k_owner_collect_pair(int nprim, int nverts, int cnt, const int32_t* __restrict__ flist,
+                                     const int* __restrict__ ptr, const int* __restrict__ cell,
+                                     const int* __restrict__ locv, LevelCtx lc, float2* __restrict__ v) {
+  grid_dependency_sync();
+  int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)nprim * cnt) return;
+  int e = (int)(tid / cnt), q = (int)(tid % cnt);
+  int s = 0, t = 0;
+  if (nverts == 2) s = q + 1;
+  else if (nverts == 3) {
+    s = flist[q] & 0xffff;
+    t = flist[q] >> 16;
+  }
+  DfAcc sum;
+  for (int c = ptr[e]; c < ptr[e + 1]; ++c) {
+    int i, j, k;
+    prim_position(locv[c], nverts, lc.n, s, t, i, j, k);
+    sum.add(v[(int64_t)cell[c] * lc.Nt + packed_index(DIM, lc.n, i, j, k)]);
+  }
+  const float2 tot = sum.value();
+  for (int c = ptr[e]; c < ptr[e + 1]; ++c) {
+    int i, j, k;
+    prim_position(locv[c], nverts, lc.n, s, t, i, j, k);
+    v[(int64_t)cell[c] * lc.Nt + packed_index(DIM, lc.n, i, j, k)] = (c == ptr[e]) ? tot : make_float2(0.f, 0.f);
+  }
+}
+
+// r32 = hi + lo rounded to binary32 (two pairs per 16-byte access, grid-stride)
+__global__ void k_pair_to_f32(const float2* __restrict__ r, float* __restrict__ r32, int64_t n) {
+  grid_dependency_sync();
+  const int64_t n2 = n / 2;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 p = reinterpret_cast<const float4*>(r)[i];
+    reinterpret_cast<float2*>(r32)[i] = make_float2(__fadd_rn(p.x, p.y), __fadd_rn(p.z, p.w));
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) r32[n - 1] = __fadd_rn(r[n - 1].x, r[n - 1].y);
+}
+
+// u + c on pairs (c binary32), renormalised
+__device__ __forceinline__ float2 df_add_f(float2 u, float c) {
+  const float2 s = df_two_sum(u.x, c);
+  return df_fast_two_sum(s.x, __fadd_rn(u.y, s.y));
+}
+
+// u += c (c zero on Dirichlet nodes), two values per access, grid-stride
+__global__ void k_add_pair(const float* __restrict__ c, float2* __restrict__ u, int64_t n) {
+  grid_dependency_sync();
+  const int64_t n2 = n / 2;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 d = reinterpret_cast<const float2*>(c)[i];
+    const float4 p = reinterpret_cast<const float4*>(u)[i];
+    const float2 a = df_add_f(make_float2(p.x, p.y), d.x), b = df_add_f(make_float2(p.z, p.w), d.y);
+    reinterpret_cast<float4*>(u)[i] = make_float4(a.x, a.y, b.x, b.y);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) u[n - 1] = df_add_f(u[n - 1], c[n - 1]);
+}
+
+// u_L back to binary64 in place (each thread rewrites the 8 bytes it read)
+__global__ void k_pair_to_f64(void* __restrict__ u, int64_t n) {
+  grid_dependency_sync();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 p = reinterpret_cast<const float2*>(u)[i];
+    reinterpret_cast<double*>(u)[i] = df_to_double(p);
+  }
 }
 
 // ---- binary16 correction storage: per-level power-of-two scale ----
@@ -398,7 +543,6 @@ static void vcycle32(hhg_mesh_s* m, int l, U* x, const float* rhs, const hhg_sol
 
 void launch_build_rhs(hhg_mesh_s* m, int l, cudaStream_t s);
 void launch_build_rhs32(hhg_mesh_s* m, int l, cudaStream_t s);
-void launch_residual(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s);
 
 void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
   hhg_launch(k_to_f32, std::max(1u, std::min<unsigned>(blocks_for((n + 3) / 4), 16u * 152u)), kBlock, 0, s, a, b, n);
@@ -407,28 +551,45 @@ void launch_to_f64(const float* a, double* b, int64_t n, cudaStream_t s) {
   hhg_launch(k_to_f64, blocks_for(n), kBlock, 0, s, a, b, n);
 }
 
-// binary64 level-L residual of the refinement, interface partials collected in binary64, then
-// narrowed to binary32 (r32_L)
+// level-L residual of the refinement on pairs (u_L as pairs in LL.u), interface partials collected
+// on pairs, then rounded to binary32 (r32_L)
 template <int DIM>
 static void ir_residual(hhg_mesh_s* m, cudaStream_t s) {
   const int L = m->L;
   LevelData& LL = m->lv[L];
-  launch_residual(m, L, LL.b, s);  // partial binary64 residual of u_L into LL.tmp
+  float2* rp = (float2*)LL.tmp;
+  {
+    dim3 gl(blocks_for(LL.Nt), m->nc);
+    hhg_launch(k_residual_pair<DIM>, gl, kBlock, 0, s, ctx(m, L), (const float2*)m->dSp, m->d_dirmask,
+               (float)stiff_scale(DIM, LL.n), (const double*)LL.b, (const float2*)LL.u, rp);
+  }
   int n = LL.n;
   const Prims& PV = m->verts;
   if (PV.count)
-    hhg_launch(k_owner_collect<DIM>, blocks_for(PV.count), kBlock, 0, s, PV.count, 1, 1, nullptr, PV.d_ptr, PV.d_cell,
-                                                                 PV.d_loc, ctx(m, L), LL.tmp);
+    hhg_launch(k_owner_collect_pair<DIM>, blocks_for(PV.count), kBlock, 0, s, PV.count, 1, 1, nullptr, PV.d_ptr,
+               PV.d_cell, PV.d_loc, ctx(m, L), rp);
   const Prims& PE = m->edges;
   if (PE.count && n >= 2)
-    hhg_launch(k_owner_collect<DIM>, blocks_for((int64_t)PE.count * (n - 1)), kBlock, 0, s, 
-        PE.count, 2, n - 1, nullptr, PE.d_ptr, PE.d_cell, PE.d_loc, ctx(m, L), LL.tmp);
+    hhg_launch(k_owner_collect_pair<DIM>, blocks_for((int64_t)PE.count * (n - 1)), kBlock, 0, s, PE.count, 2, n - 1,
+               nullptr, PE.d_ptr, PE.d_cell, PE.d_loc, ctx(m, L), rp);
   const Prims& PF = m->faces;
   int64_t nf = LL.fcol_off[3];
   if (DIM == 3 && PF.count && nf > 0)
-    hhg_launch(k_owner_collect<DIM>, blocks_for((int64_t)PF.count * nf), kBlock, 0, s, 
-        PF.count, 3, (int)nf, LL.d_fcol, PF.d_ptr, PF.d_cell, PF.d_loc, ctx(m, L), LL.tmp);
-  hhg_launch(k_to_f32, elementwise_blocks(m, LL.N), kBlock, 0, s, LL.tmp, LL.r32, LL.N);
+    hhg_launch(k_owner_collect_pair<DIM>, blocks_for((int64_t)PF.count * nf), kBlock, 0, s, PF.count, 3, (int)nf,
+               LL.d_fcol, PF.d_ptr, PF.d_cell, PF.d_loc, ctx(m, L), rp);
+  hhg_launch(k_pair_to_f32, pair_blocks(m, LL.N), kBlock, 0, s, (const float2*)rp, LL.r32, LL.N);
+}
+
+// u_L (pairs) += the binary32 correction x32_L
+static void ir_update(hhg_mesh_s* m, cudaStream_t s) {
+  LevelData& LL = m->lv[m->L];
+  hhg_launch(k_add_pair, pair_blocks(m, LL.N), kBlock, 0, s, (const float*)LL.x32, (float2*)LL.u, LL.N);
+}
+
+// u_L from pairs back to binary64, in place
+static void ir_finish(hhg_mesh_s* m, cudaStream_t s) {
+  LevelData& LL = m->lv[m->L];
+  hhg_launch(k_pair_to_f64, elementwise_blocks(m, LL.N), kBlock, 0, s, (void*)LL.u, LL.N);
 }
 void launch_finite_check(hhg_mesh_s* m, const double* v, int64_t n, cudaStream_t s);
 
@@ -436,10 +597,15 @@ template <int DIM, typename S>
 static void mixed_solve_t(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t s) {
   const int L = m->L;
   const LevelData& LL = m->lv[L];
-  // binary64 b_L (the refinement's residual right-hand side) and its binary32 copy for the binary32
-  // FMG's top level; the coarser right-hand sides only serve the binary32 FMG: built in binary32
-  launch_build_rhs(m, L, s);
-  hhg_launch(k_to_f32, elementwise_blocks(m, LL.N), kBlock, 0, s, LL.b, LL.b32, LL.N);
+  // b_L (the refinement's residual right-hand side) from pairs, stored in binary64 and as the binary32
+  // FMG's top-level right-hand side; the coarser right-hand sides only serve the binary32 FMG: built
+  // in binary32
+  launch_sub_pair(m, m->fL, nullptr, (float2*)LL.tmp, LL.N, s);
+  {
+    dim3 gl(blocks_for(LL.Nt), m->nc);
+    hhg_launch(k_build_rhs_pair<DIM>, gl, kBlock, 0, s, ctx(m, L), (const float2*)LL.tmp, (const float2*)m->dMp,
+               (float)mass_scale(DIM, LL.n), m->d_dirmask, LL.b, LL.b32);
+  }
   if (p.rhs == 0) {
     for (int l = 0; l < L; ++l) launch_build_rhs32(m, l, s);
   } else {  // b_{l-1} = I^T b_l from the binary32 copy of b_L
@@ -466,21 +632,22 @@ static void mixed_solve_t(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t
   }
   {
     dim3 gl(blocks_for(LL.Nt), m->nc);
-    hhg_launch(k_to_f64_level<DIM>, gl, kBlock, 0, s, ctx(m, L), m->d_dirmask, m->gL, LL.x32, LL.u);
+    hhg_launch(k_to_pair_level<DIM>, gl, kBlock, 0, s, ctx(m, L), m->d_dirmask, m->gL, LL.x32, (float2*)LL.u);
   }
-  // refinement steps: binary64 residual and update, binary32 V-cycles on the correction
+  // refinement steps: residual and update on pairs, binary32 V-cycles on the correction
   for (int it = 0; it < p.ir_steps; ++it) {
     ir_residual<DIM>(m, s);
     cudaMemsetAsync(LL.x32, 0, sizeof(float) * (size_t)LL.N, s);
     for (int q = 0; q < p.ir_vcycles; ++q) vcycle32<DIM, S, float>(m, L, LL.x32, LL.r32, p, s);
-    hhg_launch(k_add_f32, elementwise_blocks(m, LL.N), kBlock, 0, s, LL.x32, LL.u, LL.N);
+    ir_update(m, s);
   }
   for (int q = 0; q < p.n_extra; ++q) {
     ir_residual<DIM>(m, s);
     cudaMemsetAsync(LL.x32, 0, sizeof(float) * (size_t)LL.N, s);
     vcycle32<DIM, S, float>(m, L, LL.x32, LL.r32, p, s);
-    hhg_launch(k_add_f32, elementwise_blocks(m, LL.N), kBlock, 0, s, LL.x32, LL.u, LL.N);
+    ir_update(m, s);
   }
+  ir_finish(m, s);
   cudaMemsetAsync(m->d_flag, 0, sizeof(int), s);
   launch_finite_check(m, LL.u, LL.N, s);
 }
@@ -493,7 +660,7 @@ static void ir_step(hhg_mesh_s* m, int nv, const hhg_solve_params& p, cudaStream
   ir_residual<DIM>(m, s);
   cudaMemsetAsync(LL.x32, 0, sizeof(float) * (size_t)LL.N, s);
   for (int q = 0; q < nv; ++q) vcycle32<DIM, S, float>(m, m->L, LL.x32, LL.r32, p, s);
-  hhg_launch(k_add_f32, elementwise_blocks(m, LL.N), kBlock, 0, s, LL.x32, LL.u, LL.N);
+  ir_update(m, s);
 }
 
 // Mixed-precision adjoint solve A lam = b_L, where b_L holds the adjoint right-hand side and the
@@ -504,9 +671,10 @@ static void ir_step(hhg_mesh_s* m, int nv, const hhg_solve_params& p, cudaStream
 template <int DIM, typename S>
 static void mixed_adjoint_t(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t s) {
   LevelData& LL = m->lv[m->L];
-  cudaMemsetAsync(LL.u, 0, sizeof(double) * (size_t)LL.N, s);
+  cudaMemsetAsync(LL.u, 0, sizeof(double) * (size_t)LL.N, s);  // all-zero bits: the pair (0, 0)
   for (int it = 0; it <= p.ir_steps; ++it) ir_step<DIM, S>(m, p.ir_vcycles, p, s);
   for (int q = 0; q < p.n_extra; ++q) ir_step<DIM, S>(m, 1, p, s);
+  ir_finish(m, s);
   cudaMemsetAsync(m->d_flag, 0, sizeof(int), s);
   launch_finite_check(m, LL.u, LL.N, s);
 }
