@@ -144,6 +144,33 @@ static void interior_stage(hhg_mesh_s* m, int l, int gi, int colour, double* u, 
       CVec<double, double>{rhs, nullptr});
 }
 
+// all interior colours of a group at once, one CTA per cell (levels with short colour lists)
+template <int DIM, int PM>
+static void interior_cells(hhg_mesh_s* m, int l, int gi, double* u, const double* rhs, cudaStream_t s) {
+  const LevelData& Lv = m->lv[l];
+  const Group& G = m->groups[gi];
+  if (G.cells.empty() || Lv.icol_off[gi][G.m] <= Lv.icol_off[gi][0]) return;
+  hhg_launch(k_smooth_interior_cell<DIM, PM, double, double, double>, (unsigned)G.cells.size(), kBlock, 0, s,
+             G.d_cells, Lv.d_icol + Lv.icol_off[gi][0], colour_offsets(Lv, gi, G.m), ctx(m, l), m->d_tnorm, Lv.d_invl,
+             Vec<double, double>{u, nullptr}, CVec<double, double>{rhs, nullptr});
+}
+
+template <int DIM>
+static void interior_cells_dispatch(hhg_mesh_s* m, int l, int gi, double* u, const double* rhs, cudaStream_t s) {
+  int pm = m->groups[gi].pmask;
+  if (DIM == 2) {
+    switch (pm) {
+      case 0x3: interior_cells<DIM, 0x3>(m, l, gi, u, rhs, s); return;
+      case 0x5: interior_cells<DIM, 0x5>(m, l, gi, u, rhs, s); return;
+      case 0x6: interior_cells<DIM, 0x6>(m, l, gi, u, rhs, s); return;
+      default: interior_cells<DIM, 0x7>(m, l, gi, u, rhs, s); return;
+    }
+  } else {
+    if (pm == 0x29) interior_cells<DIM, 0x29>(m, l, gi, u, rhs, s);
+    else interior_cells<DIM, 0x7f>(m, l, gi, u, rhs, s);
+  }
+}
+
 // compile-time stencil patterns: the full stencil and the Kuhn / right-isosceles patterns
 template <int DIM>
 static void interior_stage_dispatch(hhg_mesh_s* m, int l, int gi, int colour, double* u, const double* rhs,
@@ -209,6 +236,11 @@ static void sweep_impl(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s) 
                                                 (double*)m->d_face_work, sparse, s);
     } else {
       int c = st - (DIM == 3 ? 4 : 3);
+      if (interior_per_cell(Lv, m->groups)) {  // short lists: every colour in one launch per group
+        if (c == 0)
+          for (size_t gi = 0; gi < m->groups.size(); ++gi) interior_cells_dispatch<DIM>(m, l, (int)gi, u, rhs, s);
+        continue;
+      }
       for (size_t gi = 0; gi < m->groups.size(); ++gi)
         if (c < m->groups[gi].m) interior_stage_dispatch<DIM>(m, l, (int)gi, c, u, rhs, s);
     }

@@ -239,6 +239,67 @@ __global__ void __launch_bounds__(kBlock) k_smooth_interior_multi(const int* __r
     if (c0 + c < ncells) u.set(g[c], acc[c]);
 }
 
+// Colour offsets of one group's interior lists on one level (m <= 4 colours).
+struct ColourOffsets {
+  int64_t off[5];
+  int m;
+};
+
+// Every interior colour of a small cell in one launch: one CTA per cell of the group runs the colours
+// in order, each as the list stage above, with a block barrier between colours.  The interior nodes
+// of a cell couple only with nodes of the same cell, and the barrier makes a colour's writes visible
+// to the CTA before the next colour reads them, so this equals the colour stages one by one.  For
+// levels whose per-cell colour lists are short (a few entries per thread).
+template <int DIM, int PM, typename R, typename U, typename B>
+__global__ void __launch_bounds__(kBlock) k_smooth_interior_cell(const int* __restrict__ gcells,
+                                                                 const int2* __restrict__ list, ColourOffsets co,
+                                                                 LevelCtx lc, const R* __restrict__ tnorm,
+                                                                 const R* __restrict__ invl, Vec<R, U> u,
+                                                                 CVec<R, B> rhs) {
+  grid_dependency_sync();
+  const int T = gcells[blockIdx.x];
+  const R* t = tnorm + (size_t)T * 16;
+  const R inv = invl[T];
+  const int64_t base = (int64_t)T * lc.Nt;
+  for (int c = 0; c < co.m; ++c) {
+    for (int64_t pos = co.off[c] + threadIdx.x; pos < co.off[c + 1]; pos += blockDim.x) {
+      const int2 e = list[pos];
+      if (HHG_OOB(e.x, lc.Nt, 43)) continue;
+      const int j = e.y & 0xffff, k = e.y >> 16;
+      int64_t off[15];
+      neighbour_offsets(DIM, lc.n, j, k, off);
+      const int64_t g = base + e.x;
+      R acc = rhs.get(g) * inv;
+#pragma unroll
+      for (int q = 0; q < npairs<DIM>(); ++q) {
+        if (PM >> q & 1) {
+          acc -= t[2 * q + 1] * u.get(g + off[2 * q + 1]);
+          acc -= t[2 * q + 2] * u.get(g + off[2 * q + 2]);
+        }
+      }
+      u.set(g, acc);
+    }
+    __syncthreads();
+  }
+}
+
+// the per-cell launch pays off while every colour list of every group has at most this many entries
+constexpr int64_t kCellInteriorMax = 2 * kBlock;
+
+inline bool interior_per_cell(const LevelData& Lv, const std::vector<Group>& groups) {
+  for (size_t gi = 0; gi < groups.size(); ++gi)
+    for (int c = 0; c < groups[gi].m; ++c)
+      if (Lv.icol_off[gi][c + 1] - Lv.icol_off[gi][c] > kCellInteriorMax) return false;
+  return true;
+}
+
+inline ColourOffsets colour_offsets(const LevelData& Lv, int gi, int m) {
+  ColourOffsets co{};
+  co.m = m;
+  for (int c = 0; c <= m && c < 5; ++c) co.off[c] = Lv.icol_off[gi][c] - Lv.icol_off[gi][0];
+  return co;
+}
+
 // macro vertices: never coupled to each other on levels >= 1, so one pass.  One warp per vertex,
 // lanes over the vertex's cell copies (scattered loads in parallel), fixed-order shuffle sums.
 template <int DIM, typename R, typename U, typename B>

@@ -400,6 +400,33 @@ static void interior32(hhg_mesh_s* m, int l, int gi, int colour, U* u, const flo
              CVec<float, float>{rhs, nullptr});
 }
 
+// all interior colours of a group at once, one CTA per cell (levels with short colour lists)
+template <int DIM, int PM, typename U>
+static void interior32_cells(hhg_mesh_s* m, int l, int gi, U* u, const float* rhs, cudaStream_t s) {
+  const LevelData& Lv = m->lv[l];
+  const Group& G = m->groups[gi];
+  if (G.cells.empty() || Lv.icol_off[gi][G.m] <= Lv.icol_off[gi][0]) return;
+  hhg_launch(k_smooth_interior_cell<DIM, PM, float, U, float>, (unsigned)G.cells.size(), kBlock, 0, s, G.d_cells,
+             Lv.d_icol + Lv.icol_off[gi][0], colour_offsets(Lv, gi, G.m), ctx(m, l), m->d_tnormf, Lv.d_invlf,
+             vec_of<U>(m, l, u), CVec<float, float>{rhs, nullptr});
+}
+
+template <int DIM, typename U>
+static void interior32_cells_dispatch(hhg_mesh_s* m, int l, int gi, U* u, const float* rhs, cudaStream_t s) {
+  int pm = m->groups[gi].pmask;
+  if (DIM == 2) {
+    switch (pm) {
+      case 0x3: interior32_cells<DIM, 0x3, U>(m, l, gi, u, rhs, s); return;
+      case 0x5: interior32_cells<DIM, 0x5, U>(m, l, gi, u, rhs, s); return;
+      case 0x6: interior32_cells<DIM, 0x6, U>(m, l, gi, u, rhs, s); return;
+      default: interior32_cells<DIM, 0x7, U>(m, l, gi, u, rhs, s); return;
+    }
+  } else {
+    if (pm == 0x29) interior32_cells<DIM, 0x29, U>(m, l, gi, u, rhs, s);
+    else interior32_cells<DIM, 0x7f, U>(m, l, gi, u, rhs, s);
+  }
+}
+
 template <int DIM, typename U>
 static void interior32_dispatch(hhg_mesh_s* m, int l, int gi, int colour, U* u, const float* rhs, cudaStream_t s) {
   int pm = m->groups[gi].pmask;
@@ -451,6 +478,11 @@ static void sweep32(hhg_mesh_s* m, int l, U* u, const float* rhs, cudaStream_t s
                                          (float*)m->d_face_work, false, s);
     } else {
       int c = st - (DIM == 3 ? 4 : 3);
+      if (interior_per_cell(Lv, m->groups)) {  // short lists: every colour in one launch per group
+        if (c == 0)
+          for (size_t gi = 0; gi < m->groups.size(); ++gi) interior32_cells_dispatch<DIM, U>(m, l, (int)gi, u, rhs, s);
+        continue;
+      }
       for (size_t gi = 0; gi < m->groups.size(); ++gi)
         if (c < m->groups[gi].m) interior32_dispatch<DIM, U>(m, l, (int)gi, c, u, rhs, s);
     }
