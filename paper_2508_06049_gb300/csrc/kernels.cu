@@ -233,7 +233,7 @@ static void sweep_impl(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s) 
       bool sparse = (int64_t)m->faces.count * Lv.fcol_off[3] >= kSparseFaceNodes;
       launch_face_block<double, double, double>(m->faces, Lv, ctx(m, l), m->dS, ss, m->faces.d_fw, m->faces.d_pinv,
                                                 Vec<double, double>{u, nullptr}, CVec<double, double>{rhs, nullptr},
-                                                (double*)m->d_face_work, sparse, s);
+                                                Lv.tmp, (double*)m->d_face_work, sparse, s);
     } else {
       int c = st - (DIM == 3 ? 4 : 3);
       if (interior_per_cell(Lv, m->groups)) {  // short lists: every colour in one launch per group
@@ -449,7 +449,7 @@ void launch_profile_face(hhg_mesh_s* m, int reps, cudaStream_t s, long long* uni
   for (int r = 0; r < reps; ++r)
     launch_face_block<double, double, double>(m->faces, Lv, ctx(m, L), m->dS, stiff_scale(3, Lv.n), m->faces.d_fw,
                                               m->faces.d_pinv, Vec<double, double>{Lv.u, nullptr},
-                                              CVec<double, double>{Lv.b, nullptr}, (double*)m->d_face_work,
+                                              CVec<double, double>{Lv.b, nullptr}, Lv.tmp, (double*)m->d_face_work,
                                               sparse, s);
 }
 

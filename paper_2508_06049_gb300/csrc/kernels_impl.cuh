@@ -587,27 +587,91 @@ __device__ __forceinline__ int face_dir_slot(int loc, int q) {
   return slot_of_vec(da * (x1 - x0) + db * (x2 - x0), da * (y1 - y0) + db * (y2 - y0), da * (z1 - z0) + db * (z2 - z0));
 }
 
-// One CTA (FPC = 1: kBlock threads, block barriers) or one warp (FPC = 8: eight faces per CTA, warp
-// barriers, for levels whose faces have few nodes) per face.  Phase 1: per face-interior node the
-// sum over the face's cell copies of b - A u over the couplings that leave the face (dense slot
-// loop, or with SPARSE a loop over the nonzero slots for the binary64 pipe), and the node's value;
-// phase 2: the three colour sweeps on the face's values in shared memory with the face's six
-// in-plane couplings W (unit level scale, summed over copies) and 1 / diagonal pinv; phase 3: the
-// result written to every copy.  work: 2 nf values of scratch per face where they do not fit in
-// shared memory (nullptr: shared memory, 2 nf values per face of the CTA).
-template <int FPC, bool SPARSE, typename R, typename U, typename B>
-__global__ void __launch_bounds__(kBlock) k_face_block(int nprim, int nf, int4 fcol, const int32_t* __restrict__ fnodes,
-                                                       const int* __restrict__ ptr, const int* __restrict__ cell,
-                                                       const int* __restrict__ locv,
-                                                       const unsigned char* __restrict__ dir, LevelCtx lc,
-                                                       const R* __restrict__ S, R sscale, const R* __restrict__ W,
-                                                       const R* __restrict__ pinv, R isscale, Vec<R, U> u,
-                                                       CVec<R, B> rhs, R* work) {
+template <int G, bool SPARSE, typename R, typename U, typename B>
+__global__ void k_face_ext(int nprim, int nf, const int32_t* __restrict__ fnodes, const int* __restrict__ ptr,
+                           const int* __restrict__ cell, const int* __restrict__ locv,
+                           const unsigned char* __restrict__ dir, LevelCtx lc, const R* __restrict__ S, R sscale,
+                           CVec<R, U> u, CVec<R, B> rhs, R* __restrict__ E) {
+  grid_dependency_sync();
+  int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int lane = (int)(gid & (G - 1));
+  int64_t tid = gid / G;
+  bool active = tid < (int64_t)nprim * nf;
+  int e = 0, a = 0, b = 0;
+  if (active) {
+    e = (int)(tid / nf);
+    int32_t ab = fnodes[tid % nf];
+    a = ab & 0xffff;
+    b = ab >> 16;
+    if (dir[e]) active = false;
+  }
+  R acc = 0, bs = 0;
+  if (active) {
+    const int n = lc.n;
+    for (int c = ptr[e] + lane; c < ptr[e + 1]; c += G) {
+      int loc = locv[c];
+      int i, j, k;
+      prim_position(loc, 3, n, a, b, i, j, k);
+      // leave out the node itself and its in-plane neighbours that are face-interior nodes
+      uint32_t excl = 1u;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        int da, db;
+        face_dir(q, da, db);
+        if (face_interior(n, a + da, b + db)) excl |= 1u << face_dir_slot(loc, q);
+      }
+      const int T = cell[c];
+      int t = boundary_type(3, n, i, j, k);
+      int64_t p = packed_index(3, n, i, j, k);
+      if (HHG_OOB(p, lc.Nt, 33)) continue;
+      int64_t g = (int64_t)T * lc.Nt + p;
+      uint32_t vm = valid_dirs_tab(3, t) & lc.nzs[T * kMaxTypes + t] & ~excl;
+      const R* s = S + (size_t)T * kStencilStride + t * kMaxDirs;
+      R x = 0;
+      if (SPARSE) {
+        PlaneBasis pb = plane_basis(3, n, k);
+        for (uint32_t mm = vm; mm; mm &= mm - 1) {
+          int d = __ffs(mm) - 1;
+          int64_t o = dir_offset(3, d, pb.m, j, pb.Tm, pb.Tm1);
+          if (HHG_OOB(p + o, lc.Nt, 34)) continue;
+          x += s[d] * u.get(g + o);
+        }
+      } else {
+        int64_t off[15];
+        neighbour_offsets(3, n, j, k, off);
+        mask_offsets(3, vm, off);
+#pragma unroll
+        for (int d = 1; d < 15; ++d)
+          if ((vm >> d & 1) && !HHG_OOB(p + off[d], lc.Nt, 34)) x += s[d] * u.get(g + off[d]);
+      }
+      acc += x;
+      bs += rhs.get(g);
+    }
+  }
+#pragma unroll
+  for (int w = 1; w < G; w <<= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, w);
+    bs += __shfl_xor_sync(0xffffffffu, bs, w);
+  }
+  if (active && lane == 0) E[(int64_t)e * nf + face_pos(lc.n, a, b)] = bs - sscale * acc;
+}
+
+// FPC faces per CTA (FPC = 1: the CTA's kBlock threads sweep one face, synchronised by block
+// barriers; FPC = 8: one warp per face, warp barriers, for levels whose faces have few nodes).
+// fcol: colour offsets of fnodes (colour c entries [fcol.c, fcol.c+1)); W: the face's six in-plane
+// couplings (unit level scale, summed over copies); pinv: 1 / diagonal (unit scale); isscale = 1 /
+// level scale.  work: 2 nf values of scratch per face when they do not fit in shared memory
+// (nullptr: shared memory, 2 nf values per face of the CTA).
+template <int FPC, typename R, typename U>
+__global__ void __launch_bounds__(kBlock) k_face_gs(int nprim, int nf, int4 fcol, const int32_t* __restrict__ fnodes,
+                                                    const int* __restrict__ ptr, const int* __restrict__ cell,
+                                                    const int* __restrict__ locv, const unsigned char* __restrict__ dir,
+                                                    LevelCtx lc, const R* __restrict__ W, const R* __restrict__ pinv,
+                                                    R isscale, Vec<R, U> u, const R* __restrict__ E, R* work) {
   grid_dependency_sync();
   static_assert(FPC == 1 || kBlock / FPC == 32, "one CTA or one warp per face");
   constexpr int TPF = kBlock / FPC;  // threads per face
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned char fslot[FPC][2][6];  // cell slot of in-plane direction q, first two copies
   const int grp = (int)threadIdx.x / TPF, t = (int)threadIdx.x % TPF;
   const int e = (int)blockIdx.x * FPC + grp;
   if (e >= nprim || dir[e]) return;  // uniform across the face's threads (the CTA or the warp)
@@ -618,67 +682,36 @@ __global__ void __launch_bounds__(kBlock) k_face_block(int nprim, int nf, int4 f
   const int n = lc.n;
   R* uf = work ? work + (int64_t)e * 2 * nf : (R*)smem + (size_t)grp * 2 * nf;
   R* ef = uf + nf;
-  const int c0 = ptr[e], c1 = ptr[e + 1];
-  if (t < 12 && c0 + t / 6 < c1) fslot[grp][t / 6][t % 6] = (unsigned char)face_dir_slot(locv[c0 + t / 6], t % 6);
-  sync();
-  CVec<R, U> uc{u.p, u.scale};
-  // outside part of one copy c (index cc among the face's copies) of face node (a, b)
-  auto outside = [&](int c, int cc, int a, int b, unsigned inpl, R& x, R& bv, R& own) {
-    const int loc = locv[c];
-    int i, j, k;
-    prim_position(loc, 3, n, a, b, i, j, k);
-    uint32_t excl = 1u;  // the node itself and its face-interior in-plane neighbours
+  const int c0 = ptr[e];
+  const int loc0 = locv[c0];
+  const int64_t base0 = (int64_t)cell[c0] * lc.Nt;
+  // gather the face's values (copy 0) and outside sums, four per thread in flight
+  constexpr int kUnroll = 4;
+  for (int q0 = t; q0 < nf; q0 += kUnroll * TPF) {
+    R uv[kUnroll], ev[kUnroll];
+    int ps[kUnroll];
 #pragma unroll
-    for (int q = 0; q < 6; ++q)
-      if (inpl >> q & 1) excl |= 1u << (cc < 2 ? (int)fslot[grp][cc][q] : face_dir_slot(loc, q));
-    const int T = cell[c];
-    const int ty = boundary_type(3, n, i, j, k);
-    const int64_t p = packed_index(3, n, i, j, k);
-    x = 0;
-    bv = 0;
-    if (HHG_OOB(p, lc.Nt, 33)) return;
-    const int64_t g = (int64_t)T * lc.Nt + p;
-    if (cc == 0) own = uc.get(g);
-    const uint32_t vm = valid_dirs_tab(3, ty) & lc.nzs[T * kMaxTypes + ty] & ~excl;
-    const R* s = S + (size_t)T * kStencilStride + ty * kMaxDirs;
-    if (SPARSE) {
-      PlaneBasis pb = plane_basis(3, n, k);
-      for (uint32_t mm = vm; mm; mm &= mm - 1) {
-        int d = __ffs(mm) - 1;
-        int64_t o = dir_offset(3, d, pb.m, j, pb.Tm, pb.Tm1);
-        if (HHG_OOB(p + o, lc.Nt, 34)) continue;
-        x += s[d] * uc.get(g + o);
+    for (int r = 0; r < kUnroll; ++r) {
+      int q = q0 + r * TPF;
+      ps[r] = -1;
+      if (q < nf) {
+        int32_t ab = fnodes[q];
+        int a = ab & 0xffff, b = ab >> 16;
+        int i, j, k;
+        prim_position(loc0, 3, n, a, b, i, j, k);
+        int pos = face_pos(n, a, b);
+        int64_t p = packed_index(3, n, i, j, k);
+        ps[r] = pos;
+        uv[r] = HHG_OOB(p, lc.Nt, 35) ? (R)0 : u.get(base0 + p);
+        ev[r] = E[(int64_t)e * nf + pos];
       }
-    } else {
-      int64_t off[15];
-      neighbour_offsets(3, n, j, k, off);
-      mask_offsets(3, vm, off);
+    }
 #pragma unroll
-      for (int d = 1; d < 15; ++d)
-        if ((vm >> d & 1) && !HHG_OOB(p + off[d], lc.Nt, 34)) x += s[d] * uc.get(g + off[d]);
-    }
-    bv = rhs.get(g);
-  };
-  for (int q = t; q < nf; q += TPF) {
-    const int32_t ab = fnodes[q];
-    const int a = ab & 0xffff, b = ab >> 16;
-    unsigned inpl = 0;
-#pragma unroll
-    for (int d = 0; d < 6; ++d) {
-      int da, db;
-      face_dir(d, da, db);
-      if (face_interior(n, a + da, b + db)) inpl |= 1u << d;
-    }
-    R acc = 0, bs = 0, own = 0;
-    for (int c = c0; c < c1; ++c) {
-      R x, bv;
-      outside(c, c - c0, a, b, inpl, x, bv, own);
-      acc += x;
-      bs += bv;
-    }
-    const int pos = face_pos(n, a, b);
-    uf[pos] = own;
-    ef[pos] = (bs - sscale * acc) * isscale;
+    for (int r = 0; r < kUnroll; ++r)
+      if (ps[r] >= 0) {
+        uf[ps[r]] = uv[r];
+        ef[ps[r]] = ev[r] * isscale;
+      }
   }
   R w[6];
 #pragma unroll
@@ -686,7 +719,6 @@ __global__ void __launch_bounds__(kBlock) k_face_block(int nprim, int nf, int4 f
   const R pv = pinv[e];
   sync();
   const int cb[4] = {fcol.x, fcol.y, fcol.z, fcol.w};
-#pragma unroll
   for (int col = 0; col < 3; ++col) {
     for (int q = cb[col] + t; q < cb[col + 1]; q += TPF) {
       int32_t ab = fnodes[q];
@@ -703,7 +735,7 @@ __global__ void __launch_bounds__(kBlock) k_face_block(int nprim, int nf, int4 f
     }
     sync();
   }
-  for (int c = c0; c < c1; ++c) {
+  for (int c = c0; c < ptr[e + 1]; ++c) {
     const int loc = locv[c];
     const int64_t base = (int64_t)cell[c] * lc.Nt;
     for (int q = t; q < nf; q += TPF) {
@@ -747,43 +779,42 @@ inline int4 fcol4(const LevelData& Lv) {
   return make_int4((int)Lv.fcol_off[0], (int)Lv.fcol_off[1], (int)Lv.fcol_off[2], (int)Lv.fcol_off[3]);
 }
 
-// Launch the face block on one level (one launch): the per-face sweeps in shared memory when 2 nf
-// values fit (else in `work`, P.count x 2 nf values).
+// Launch the face block on one level: E in `E` (P.count x nf values), the per-face sweeps in shared
+// memory when 2 nf values fit (else in `work`, P.count x 2 nf values).
 template <typename R, typename U, typename B>
 void launch_face_block(const Prims& P, const LevelData& Lv, LevelCtx lc, const R* S, R ss, const R* W,
-                       const R* pinv, Vec<R, U> u, CVec<R, B> rhs, R* work, bool sparse, cudaStream_t s) {
+                       const R* pinv, Vec<R, U> u, CVec<R, B> rhs, R* E, R* work, bool sparse, cudaStream_t s) {
   const int nf = (int)Lv.fcol_off[3];
   if (P.count == 0 || nf == 0) return;
+  const int64_t nodes = (int64_t)P.count * nf;
+  CVec<R, U> uc{u.p, u.scale};
+  const int G = iface_lanes(P.max_copies);
+#define HHG_FACE_EXT(GL, SP)                                                                                       \
+  hhg_launch(k_face_ext<GL, SP, R, U, B>, blocks_for(nodes * GL), kBlock, 0, s, P.count, nf, Lv.d_fcol, P.d_ptr, \
+             P.d_cell, P.d_loc, P.d_dir, lc, S, ss, uc, rhs, E)
+  if (G == 1) {
+    if (sparse) HHG_FACE_EXT(1, true);
+    else HHG_FACE_EXT(1, false);
+  } else {
+    if (sparse) HHG_FACE_EXT(2, true);
+    else HHG_FACE_EXT(2, false);
+  }
+#undef HHG_FACE_EXT
   // faces with few nodes: one warp per face, eight faces per CTA
   constexpr int kFacesPerWarpCta = kBlock / 32;
   if (nf <= 64) {
     const size_t smem8 = (size_t)kFacesPerWarpCta * 2 * nf * sizeof(R);
-    const unsigned grid = (unsigned)((P.count + kFacesPerWarpCta - 1) / kFacesPerWarpCta);
-    if (sparse)
-      hhg_launch(k_face_block<kFacesPerWarpCta, true, R, U, B>, grid, kBlock, smem8, s, P.count, nf, fcol4(Lv),
-                 Lv.d_fcol, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, lc, S, ss, W, pinv, (R)1 / ss, u, rhs, (R*)nullptr);
-    else
-      hhg_launch(k_face_block<kFacesPerWarpCta, false, R, U, B>, grid, kBlock, smem8, s, P.count, nf, fcol4(Lv),
-                 Lv.d_fcol, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, lc, S, ss, W, pinv, (R)1 / ss, u, rhs, (R*)nullptr);
+    hhg_launch(k_face_gs<kFacesPerWarpCta, R, U>, (unsigned)((P.count + kFacesPerWarpCta - 1) / kFacesPerWarpCta),
+               kBlock, smem8, s, P.count, nf, fcol4(Lv), Lv.d_fcol, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, lc, W, pinv,
+               (R)1 / ss, u, (const R*)E, (R*)nullptr);
     return;
   }
   const size_t smem = 2 * (size_t)nf * sizeof(R);
   const bool fits = smem <= kMaxTileSmem;
-  R* wk = fits ? (R*)nullptr : work;
-  const size_t dyn = fits ? smem : 0;
-  if (sparse) {
-    if (fits && smem > 48 * 1024)
-      cudaFuncSetAttribute(k_face_block<1, true, R, U, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kMaxTileSmem);
-    hhg_launch(k_face_block<1, true, R, U, B>, (unsigned)P.count, kBlock, dyn, s, P.count, nf, fcol4(Lv), Lv.d_fcol,
-               P.d_ptr, P.d_cell, P.d_loc, P.d_dir, lc, S, ss, W, pinv, (R)1 / ss, u, rhs, wk);
-  } else {
-    if (fits && smem > 48 * 1024)
-      cudaFuncSetAttribute(k_face_block<1, false, R, U, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kMaxTileSmem);
-    hhg_launch(k_face_block<1, false, R, U, B>, (unsigned)P.count, kBlock, dyn, s, P.count, nf, fcol4(Lv),
-               Lv.d_fcol, P.d_ptr, P.d_cell, P.d_loc, P.d_dir, lc, S, ss, W, pinv, (R)1 / ss, u, rhs, wk);
-  }
+  if (fits && smem > 48 * 1024)
+    cudaFuncSetAttribute(k_face_gs<1, R, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxTileSmem);
+  hhg_launch(k_face_gs<1, R, U>, (unsigned)P.count, kBlock, fits ? smem : 0, s, P.count, nf, fcol4(Lv), Lv.d_fcol,
+             P.d_ptr, P.d_cell, P.d_loc, P.d_dir, lc, W, pinv, (R)1 / ss, u, (const R*)E, fits ? (R*)nullptr : work);
 }
 
 // ---------------------------------------------------------------- residual, restriction (V-cycle of Alg. 4; transfers of Sec. 4.4)

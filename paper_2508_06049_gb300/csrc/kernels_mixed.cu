@@ -474,7 +474,7 @@ static void sweep32(hhg_mesh_s* m, int l, U* u, const float* rhs, cudaStream_t s
       iface32<DIM, U>(m, l, m->edges, 2, 1, cnt_rim, cnt_inner, nullptr, nullptr, u, rhs, s);
     } else if (DIM == 3 && st == 3) {
       launch_face_block<float, U, float>(m->faces, Lv, ctx(m, l), m->dS32, ss, m->faces.d_fwf, m->faces.d_pinvf,
-                                         vec_of<U>(m, l, u), CVec<float, float>{rhs, nullptr},
+                                         vec_of<U>(m, l, u), CVec<float, float>{rhs, nullptr}, Lv.t32,
                                          (float*)m->d_face_work, false, s);
     } else {
       int c = st - (DIM == 3 ? 4 : 3);
