@@ -1230,8 +1230,24 @@ __global__ void __launch_bounds__(kBlock) k_node_form_pair(LevelCtx lc, const fl
       tsum.add_prod(xp, ay.value());
     }
   }
-  const double tot = block_sum_fixed(df_to_double(tsum.value()), wsum);
-  if (threadIdx.x == 0) part[(int64_t)T * gridDim.x + blockIdx.x] = tot;
+  // warp butterflies on pairs (binary32 pipe), one binary64 value per warp, then as block_sum_fixed
+  float2 v = tsum.value();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DfAcc a;
+    a.hi = v.x;
+    a.lo = v.y;
+    a.add(make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)));
+    v = a.value();
+  }
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = df_to_double(v);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < kBlock / 32 ? wsum[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = kBlock / 64; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) part[(int64_t)T * gridDim.x + blockIdx.x] = t;
+  }
 }
 
 // ---------------------------------------------------------------- operators for testing / adjoint
