@@ -117,8 +117,7 @@ void enqueue_vcycle(hhg_mesh_s* m, int l, const double* rhs, const hhg_solve_par
   }
   for (int q = 0; q < p.pre; ++q) launch_sweep(m, l, rhs, s);
   launch_residual_after(m, l, rhs, s, p.pre > 0);
-  launch_restrict(m, l, m->lv[l].tmp, m->lv[l - 1].rc, s);
-  cudaMemsetAsync(m->lv[l - 1].u, 0, sizeof(double) * (size_t)m->lv[l - 1].N, s);
+  launch_restrict(m, l, m->lv[l].tmp, m->lv[l - 1].rc, s, m->lv[l - 1].u);  // and u_{l-1} = 0
   enqueue_vcycle(m, l - 1, m->lv[l - 1].rc, p, s);
   launch_prolong_add(m, l, s);
   for (int q = 0; q < p.post; ++q) launch_sweep(m, l, rhs, s);

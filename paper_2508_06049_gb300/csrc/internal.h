@@ -154,7 +154,9 @@ void launch_sweep(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s);
 void launch_residual(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s);
 // the same directly after a Gauss-Seidel sweep (last interior colour has zero residual)
 void launch_residual_after(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t s, bool after_sweep);
-void launch_restrict(hhg_mesh_s* m, int l, const double* fine, double* coarse, cudaStream_t s);
+// coarse = P^T fine on level l-1; zero (may be null): a level-(l-1) vector set to 0 in the same launch
+void launch_restrict(hhg_mesh_s* m, int l, const double* fine, double* coarse, cudaStream_t s,
+                     double* zero = nullptr);
 void launch_prolong_add(hhg_mesh_s* m, int l, cudaStream_t s);
 void launch_fmg_prolong(hhg_mesh_s* m, int l, cudaStream_t s);
 void launch_coarse_solve(hhg_mesh_s* m, const double* rhs, cudaStream_t s);

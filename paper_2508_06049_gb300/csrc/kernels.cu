@@ -287,13 +287,15 @@ void launch_residual_after(hhg_mesh_s* m, int l, const double* rhs, cudaStream_t
   }
 }
 
-void launch_restrict(hhg_mesh_s* m, int l, const double* fine, double* coarse, cudaStream_t s) {
+void launch_restrict(hhg_mesh_s* m, int l, const double* fine, double* coarse, cudaStream_t s, double* zero) {
   const LevelData& C = m->lv[l - 1];
   dim3 grid(blocks_for(C.Nt), m->nc);
   if (m->dim == 2)
-    hhg_launch(k_restrict<2, double, double, double>, grid, kBlock, 0, s, ctx(m, l), ctx(m, l - 1), m->d_dirmask, fine, coarse);
+    hhg_launch(k_restrict<2, double, double, double>, grid, kBlock, 0, s, ctx(m, l), ctx(m, l - 1), m->d_dirmask, fine,
+               coarse, zero);
   else
-    hhg_launch(k_restrict<3, double, double, double>, grid, kBlock, 0, s, ctx(m, l), ctx(m, l - 1), m->d_dirmask, fine, coarse);
+    hhg_launch(k_restrict<3, double, double, double>, grid, kBlock, 0, s, ctx(m, l), ctx(m, l - 1), m->d_dirmask, fine,
+               coarse, zero);
 }
 
 void launch_prolong_add(hhg_mesh_s* m, int l, cudaStream_t s) {

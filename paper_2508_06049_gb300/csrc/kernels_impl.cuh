@@ -934,14 +934,17 @@ __global__ void __launch_bounds__(kBlock) k_residual_list(const int* __restrict_
   }
 }
 
-// coarse partial rhs = P^T (fine partial residual), per cell: r_c(q) = r_f(2q) + 1/2 sum_d r_f(2q+d)
-template <int DIM, typename R, typename I, typename O>
+// coarse partial rhs = P^T (fine partial residual), per cell: r_c(q) = r_f(2q) + 1/2 sum_d r_f(2q+d).
+// zero (may be null): a coarse-level vector set to 0 at every node on the way (the coarse
+// correction's starting value, which would otherwise take a memset of its own).
+template <int DIM, typename R, typename I, typename O, typename Z = O>
 __global__ void k_restrict(LevelCtx fc, LevelCtx cc, const uint16_t* __restrict__ dirmask, const I* __restrict__ rf,
-                           O* __restrict__ rcv) {
+                           O* __restrict__ rcv, Z* __restrict__ zero = nullptr) {
   grid_dependency_sync();
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (loc >= cc.Nt) return;
   int T = blockIdx.y;
+  if (zero) zero[(int64_t)T * cc.Nt + loc] = Z(0.0f);
   int i, j, k;
   decode(cc.ijk[loc], i, j, k);
   int t = boundary_type(DIM, cc.n, i, j, k);

@@ -562,10 +562,11 @@ static void vcycle32(hhg_mesh_s* m, int l, U* x, const float* rhs, const hhg_sol
   residual_t<DIM, float, U, float>(m, l, cvec_of<U>(m, l, x), CVec<float, float>{rhs, nullptr}, m->dS32, Lv.t32, s,
                                    false);
   dim3 gr(blocks_for(C.Nt), m->nc);
-  hhg_launch(k_restrict<DIM, float, float, float>, gr, kBlock, 0, s, ctx(m, l), ctx(m, l - 1), m->d_dirmask, Lv.t32, C.r32);
-  if constexpr (std::is_same<S, __half>::value) set_scale16<DIM>(m, l - 1, s);
   S* c = (S*)C.c16;
-  cudaMemsetAsync(c, 0, sizeof(S) * (size_t)C.N, s);
+  // restriction, and the coarse correction's starting value c = 0 in the same launch
+  hhg_launch(k_restrict<DIM, float, float, float, S>, gr, kBlock, 0, s, ctx(m, l), ctx(m, l - 1), m->d_dirmask,
+             (const float*)Lv.t32, C.r32, c);
+  if constexpr (std::is_same<S, __half>::value) set_scale16<DIM>(m, l - 1, s);
   vcycle32<DIM, S, S>(m, l - 1, c, C.r32, p, s);
   dim3 gf(blocks_for(Lv.Nt), m->nc);
   hhg_launch(k_prolong_add<DIM, float, S, U>, gf, kBlock, 0, s, ctx(m, l), ctx(m, l - 1), m->d_dirmask,
@@ -644,7 +645,7 @@ static void mixed_solve_t(hhg_mesh_s* m, const hhg_solve_params& p, cudaStream_t
     for (int l = L; l >= 1; --l) {
       dim3 gr(blocks_for(m->lv[l - 1].Nt), m->nc);
       hhg_launch(k_restrict<DIM, float, float, float>, gr, kBlock, 0, s, ctx(m, l), ctx(m, l - 1), m->d_dirmask,
-                 (const float*)m->lv[l].b32, m->lv[l - 1].b32);
+                 (const float*)m->lv[l].b32, m->lv[l - 1].b32, (float*)nullptr);
     }
   }
   {
