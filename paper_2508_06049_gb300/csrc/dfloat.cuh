@@ -48,6 +48,27 @@ struct DfAcc {
   __device__ __forceinline__ float2 value() const { return df_fast_two_sum(hi, lo); }
 };
 
+// The conversion instructions between binary32 and binary64 run on GB300's binary64 pipe, so the
+// common cases below use integer operations, and the rare ones call these (never inlined, so the
+// compiler cannot evaluate them speculatively on every call).
+static __device__ __noinline__ float2 df_split_slow(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+static __device__ __noinline__ double df_widen_slow(float f) { return (double)f; }
+
+// binary32 -> binary64 exactly: exponent re-biased, significand shifted (zero and normal values;
+// subnormals, infinities and NaN take the conversion instruction)
+__device__ __forceinline__ double df_widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  const unsigned long long sg = (unsigned long long)(u & 0x80000000u) << 32;
+  if ((u << 1) == 0u) return __longlong_as_double((long long)sg);
+  if (ex == 0u || ex == 0xffu) return df_widen_slow(f);
+  return __longlong_as_double(
+      (long long)(sg | ((unsigned long long)(ex + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
 // Split a binary64 value into hi + lo, both binary32: hi is x with its significand cut to 24 bits,
 // lo the next 24 bits of the rest (bits below are dropped: |x - hi - lo| < 2^-47 |x|).  Integer
 // operations only for binary64 values whose hi is a normal binary32 (2^-126 <= |x| < 2^128); zero
@@ -58,10 +79,7 @@ __device__ __forceinline__ float2 df_split(double x) {
   const int e = (int)((top >> 20) & 0x7ffu);  // biased binary64 exponent
   const int eh = e - 1023 + 127;              // biased binary32 exponent of hi
   if (e == 0 && (b << 1) == 0ull) return make_float2(0.f, 0.f);
-  if (eh <= 0 || eh >= 255) {
-    const float h = __double2float_rn(x);
-    return make_float2(h, __double2float_rn(x - (double)h));
-  }
+  if (eh <= 0 || eh >= 255) return df_split_slow(x);
   const unsigned sgn = top & 0x80000000u;
   const unsigned long long mant = b & 0xfffffffffffffull;  // 52 significand bits
   const float h = __uint_as_float(sgn | ((unsigned)eh << 23) | (unsigned)(mant >> 29));
@@ -76,7 +94,7 @@ __device__ __forceinline__ float2 df_split(double x) {
   return make_float2(h, __uint_as_float(sgn | ((unsigned)el << 23) | (m24 & 0x7fffffu)));
 }
 
-// hi + lo in binary64 (exact when the pair came from df_split)
-__device__ __forceinline__ double df_to_double(float2 a) { return (double)a.x + (double)a.y; }
+// hi + lo in binary64 (one binary64 addition; exact when the pair came from df_split)
+__device__ __forceinline__ double df_to_double(float2 a) { return df_widen(a.x) + df_widen(a.y); }
 
 }  // namespace hhg

@@ -117,44 +117,103 @@ __global__ void k_to_pair_level(LevelCtx lc, const uint16_t* __restrict__ dirmas
   up[g] = (dirmask[T] >> t & 1) ? df_split(gL[g]) : make_float2(x[g], 0.f);
 }
 
-// partial residual r = b - ss A_T u of every closure node (cell copy), u and r as pairs, b in
-// binary64 (split per node); zero on Dirichlet rows.  ss: the level's stiffness scale, a power of two.
-template <int DIM>
-__global__ void k_residual_pair(LevelCtx lc, const float2* __restrict__ Sp, const uint16_t* __restrict__ dirmask,
-                                float ss, const double* __restrict__ b, const float2* __restrict__ up,
-                                float2* __restrict__ r) {
-  grid_dependency_sync();
-  int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (loc >= lc.Nt) return;
-  int T = blockIdx.y;
-  int i, j, k;
-  decode(lc.ijk[loc], i, j, k);
-  int t = boundary_type(DIM, lc.n, i, j, k);
-  int64_t g = (int64_t)T * lc.Nt + loc;
-  if (dirmask[T] >> t & 1) {
-    r[g] = make_float2(0.f, 0.f);
-    return;
-  }
-  const uint32_t vm = valid_dirs_tab(DIM, t) & lc.nzs[T * kMaxTypes + t];
-  const float2* st = Sp + (size_t)T * kStencilStride + t * kMaxDirs;
-  int64_t off[15];
-  neighbour_offsets(DIM, lc.n, j, k, off);
-  mask_offsets(DIM, vm, off);
-  float2 uq[ndirs<DIM>()];
-#pragma unroll
-  for (int d = 0; d < ndirs<DIM>(); ++d) {
-    const bool ok = (vm >> d & 1) && !HHG_OOB(loc + off[d], lc.Nt, 72);
-    uq[d] = ok ? up[g + off[d]] : make_float2(0.f, 0.f);
-  }
+// r = b - ss A u for one node of one cell copy on pairs: terms (stencil pair, value pair) already
+// gathered, b in binary64 split here; ss: the level's stiffness scale, a power of two (exact)
+template <int N>
+__device__ __forceinline__ float2 pair_residual(const float2 (&s)[N], const float2 (&v)[N], double b, float ss) {
   DfAcc acc;
 #pragma unroll
-  for (int d = 0; d < ndirs<DIM>(); ++d)
-    if (vm >> d & 1) acc.add_prod(st[d], uq[d]);
+  for (int d = 0; d < N; ++d) acc.add_prod(s[d], v[d]);
   const float2 au = acc.value();
   DfAcc res;
-  res.add(df_split(b[g]));
+  res.add(df_split(b));
   res.add(make_float2(-__fmul_rn(au.x, ss), -__fmul_rn(au.y, ss)));
-  r[g] = res.value();
+  return res.value();
+}
+
+// Partial residual r = b - ss A_T u on pairs (u and r as pairs, b in binary64) for every closure node
+// of the group's cells, zero on Dirichlet rows, from the node lists of k_residual_list: blocks
+// [0, bcomp) take the interior list entries [0, ncomp) with the compile-time stencil pattern PM
+// (one cell per grid row), the remaining blocks the boundary-type nodes (every valid slot, the
+// zero ones masked).
+template <int DIM, int PM>
+__global__ void __launch_bounds__(kBlock) k_residual_pair(const int* __restrict__ gcells, int ncells, LevelCtx lc,
+                                                          const float2* __restrict__ Sp,
+                                                          const uint16_t* __restrict__ dirmask, float ss,
+                                                          const double* __restrict__ b, const float2* __restrict__ up,
+                                                          float2* __restrict__ r, const int2* __restrict__ ilist,
+                                                          int64_t ncomp, const int2* __restrict__ blist, int64_t nbnd,
+                                                          unsigned bcomp) {
+  grid_dependency_sync();
+  constexpr int CPB = 1;
+  constexpr int NT = 1 + 2 * __builtin_popcount(PM);  // centre + the coupled directions
+  const int c0 = CPB * blockIdx.y;
+  int Ts[CPB];
+#pragma unroll
+  for (int c = 0; c < CPB; ++c) Ts[c] = gcells[min(c0 + c, ncells - 1)];  // a short last group repeats
+  const unsigned bx = blockIdx.x;
+  if (bx < bcomp) {
+    const int64_t pos = (int64_t)bx * blockDim.x + threadIdx.x;
+    if (pos >= ncomp) return;
+    const int2 e = ilist[pos];
+    if (HHG_OOB(e.x, lc.Nt, 56)) return;
+    const int j = e.y & 0xffff, k = e.y >> 16;
+    int64_t off[15];
+    neighbour_offsets(DIM, lc.n, j, k, off);
+    float2 sv[CPB][NT], uv[CPB][NT];
+    int64_t g[CPB];
+#pragma unroll
+    for (int c = 0; c < CPB; ++c) {
+      g[c] = (int64_t)Ts[c] * lc.Nt + e.x;
+      const float2* st = Sp + (size_t)Ts[c] * kStencilStride;  // interior type 0
+      int n = 0;
+      sv[c][n] = st[0];
+      uv[c][n++] = up[g[c]];
+#pragma unroll
+      for (int q = 0; q < npairs<DIM>(); ++q)
+        if (PM >> q & 1) {
+          sv[c][n] = st[2 * q + 1];
+          uv[c][n++] = up[g[c] + off[2 * q + 1]];
+          sv[c][n] = st[2 * q + 2];
+          uv[c][n++] = up[g[c] + off[2 * q + 2]];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < CPB; ++c)
+      if (c0 + c < ncells)
+        r[g[c]] = (dirmask[Ts[c]] & 1) ? make_float2(0.f, 0.f) : pair_residual(sv[c], uv[c], b[g[c]], ss);
+  } else {
+    const int64_t pos = (int64_t)(bx - bcomp) * blockDim.x + threadIdx.x;
+    if (pos >= nbnd) return;
+    const int2 e = blist[pos];
+    if (HHG_OOB(e.x, lc.Nt, 57)) return;
+    int i, j, k;
+    decode(e.y, i, j, k);
+    const int t = boundary_type(DIM, lc.n, i, j, k);
+    int64_t off[15];
+    neighbour_offsets(DIM, lc.n, j, k, off);
+    const uint32_t vt = valid_dirs_tab(DIM, t);
+#pragma unroll
+    for (int c = 0; c < CPB; ++c) {
+      if (c0 + c >= ncells) continue;
+      const int T = Ts[c];
+      const int64_t g = (int64_t)T * lc.Nt + e.x;
+      if (dirmask[T] >> t & 1) {
+        r[g] = make_float2(0.f, 0.f);
+        continue;
+      }
+      const uint32_t vm = vt & lc.nzs[T * kMaxTypes + t];
+      const float2* st = Sp + (size_t)T * kStencilStride + t * kMaxDirs;
+      float2 sv[ndirs<DIM>()], uv[ndirs<DIM>()];
+#pragma unroll
+      for (int d = 0; d < ndirs<DIM>(); ++d) {
+        const bool ok = (vm >> d & 1) && !HHG_OOB(e.x + off[d], lc.Nt, 58);
+        sv[d] = ok ? st[d] : make_float2(0.f, 0.f);
+        uv[d] = ok ? up[g + off[d]] : make_float2(0.f, 0.f);
+      }
+      r[g] = pair_residual(sv, uv, b[g], ss);
+    }
+  }
 }
 
 // the pair partials of each interface node summed into its first copy, the other copies set to 0
@@ -591,10 +650,28 @@ static void ir_residual(hhg_mesh_s* m, cudaStream_t s) {
   const int L = m->L;
   LevelData& LL = m->lv[L];
   float2* rp = (float2*)LL.tmp;
-  {
-    dim3 gl(blocks_for(LL.Nt), m->nc);
-    hhg_launch(k_residual_pair<DIM>, gl, kBlock, 0, s, ctx(m, L), (const float2*)m->dSp, m->d_dirmask,
-               (float)stiff_scale(DIM, LL.n), (const double*)LL.b, (const float2*)LL.u, rp);
+  for (size_t gi = 0; gi < m->groups.size(); ++gi) {
+    const Group& G = m->groups[gi];
+    if (G.cells.empty()) continue;
+    ResidualSegments rs = residual_segments(LL, G, (int)gi, false);
+    dim3 grid(rs.bcomp + blocks_for(LL.nbnd), (unsigned)G.cells.size());
+    const float ss = (float)stiff_scale(DIM, LL.n);
+#define HHG_RP(PM)                                                                                                    \
+  hhg_launch(k_residual_pair<DIM, PM>, grid, kBlock, 0, s, G.d_cells, (int)G.cells.size(), ctx(m, L),                 \
+             (const float2*)m->dSp, m->d_dirmask, ss, (const double*)LL.b, (const float2*)LL.u, rp, rs.ilist, rs.ncomp, \
+             LL.d_bnd, LL.nbnd, rs.bcomp)
+    if constexpr (DIM == 2) {
+      switch (G.pmask) {
+        case 0x3: HHG_RP(0x3); break;
+        case 0x5: HHG_RP(0x5); break;
+        case 0x6: HHG_RP(0x6); break;
+        default: HHG_RP(0x7); break;
+      }
+    } else {
+      if (G.pmask == 0x29) HHG_RP(0x29);
+      else HHG_RP(0x7f);
+    }
+#undef HHG_RP
   }
   int n = LL.n;
   const Prims& PV = m->verts;
