@@ -300,7 +300,7 @@ void launch_restrict(hhg_mesh_s* m, int l, const double* fine, double* coarse, c
 
 void launch_prolong_add(hhg_mesh_s* m, int l, cudaStream_t s) {
   const LevelData& F = m->lv[l];
-  dim3 grid(blocks_for(F.Nt, kBlock * kProlongNodes), m->nc);
+  dim3 grid(blocks_for(F.Nt), m->nc);
   CVec<double, double> uc{m->lv[l - 1].u, nullptr};
   Vec<double, double> uf{F.u, nullptr};
   if (m->dim == 2)
@@ -383,7 +383,7 @@ void launch_sub_pair(hhg_mesh_s* m, const double* a, const double* b, float2* x,
 void launch_prolong_diff_pair(hhg_mesh_s* m, const double* coarse, const double* minuend, float2* x, cudaStream_t s) {
   const int l = m->L;
   const LevelData& F = m->lv[l];
-  dim3 grid(blocks_for(F.Nt, kBlock * kProlongNodes), m->nc);
+  dim3 grid(blocks_for(F.Nt), m->nc);
   DISPATCH_DIM(m, k_prolong_diff_pair, grid, kBlock, 0, s, ctx(m, l), ctx(m, l - 1), coarse, minuend, x);
 }
 

@@ -982,36 +982,20 @@ __device__ __forceinline__ R interp(LevelCtx cc, int T, int i, int j, int k, con
   return (R)0.5 * (a + b);
 }
 
-// u_f += I u_c on free nodes.  kProlongNodes nodes per thread (a block stride apart), their table,
-// coarse and fine loads issued together: one node per thread leaves the kernel bound by the
-// latency of its dependent loads (decode table -> coarse values -> store) times the number of waves.
-constexpr int kProlongNodes = 4;
-
+// u_f += I u_c on free nodes
 template <int DIM, typename R, typename UC, typename UF>
-__global__ void __launch_bounds__(kBlock) k_prolong_add(LevelCtx fc, LevelCtx cc, const uint16_t* __restrict__ dirmask,
-                                                        CVec<R, UC> uc, Vec<R, UF> uf) {
+__global__ void k_prolong_add(LevelCtx fc, LevelCtx cc, const uint16_t* __restrict__ dirmask, CVec<R, UC> uc,
+                              Vec<R, UF> uf) {
   grid_dependency_sync();
-  const int T = blockIdx.y;
-  const uint16_t dm = dirmask[T];
-  R v[kProlongNodes];
-  int64_t g[kProlongNodes];
-  bool act[kProlongNodes];
-#pragma unroll
-  for (int r = 0; r < kProlongNodes; ++r) {
-    const int64_t loc = ((int64_t)blockIdx.x * kProlongNodes + r) * blockDim.x + threadIdx.x;
-    act[r] = loc < fc.Nt;
-    g[r] = (int64_t)T * fc.Nt + loc;
-    v[r] = 0;
-    if (act[r]) {
-      int i, j, k;
-      decode(fc.ijk[loc], i, j, k);
-      act[r] = !(dm >> boundary_type(DIM, fc.n, i, j, k) & 1);
-      if (act[r]) v[r] = uf.get(g[r]) + interp<DIM, R>(cc, T, i, j, k, uc);
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < kProlongNodes; ++r)
-    if (act[r]) uf.set(g[r], v[r]);
+  int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (loc >= fc.Nt) return;
+  int T = blockIdx.y;
+  int i, j, k;
+  decode(fc.ijk[loc], i, j, k);
+  int t = boundary_type(DIM, fc.n, i, j, k);
+  if (dirmask[T] >> t & 1) return;
+  int64_t g = (int64_t)T * fc.Nt + loc;
+  uf.set(g, uf.get(g) + interp<DIM, R>(cc, T, i, j, k, uc));
 }
 
 // FMG transition: u_{l+1} = I u_l (Dirichlet nodes from g_L, or 0 if gL is null), w_l = u_{l+1}
@@ -1041,29 +1025,18 @@ __global__ void k_fmg_prolong(LevelCtx fc, LevelCtx cc, int nL, int64_t NtL, int
 
 // the estimator's difference u_L - I w_c in binary64, stored as its binary32 hi/lo pair (df_split)
 // for k_node_form_pair
-// (kProlongNodes nodes per thread, as k_prolong_add)
 template <int DIM>
-__global__ void __launch_bounds__(kBlock) k_prolong_diff_pair(LevelCtx fc, LevelCtx cc, const double* __restrict__ vc,
-                                                              const double* __restrict__ minuend,
-                                                              float2* __restrict__ xf) {
+__global__ void k_prolong_diff_pair(LevelCtx fc, LevelCtx cc, const double* __restrict__ vc,
+                                    const double* __restrict__ minuend, float2* __restrict__ xf) {
   grid_dependency_sync();
-  const int T = blockIdx.y;
-  double v[kProlongNodes];
-#pragma unroll
-  for (int r = 0; r < kProlongNodes; ++r) {
-    const int64_t loc = ((int64_t)blockIdx.x * kProlongNodes + r) * blockDim.x + threadIdx.x;
-    v[r] = 0.0;
-    if (loc < fc.Nt) {
-      int i, j, k;
-      decode(fc.ijk[loc], i, j, k);
-      v[r] = minuend[(int64_t)T * fc.Nt + loc] - interp<DIM, double>(cc, T, i, j, k, CVec<double, double>{vc, nullptr});
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < kProlongNodes; ++r) {
-    const int64_t loc = ((int64_t)blockIdx.x * kProlongNodes + r) * blockDim.x + threadIdx.x;
-    if (loc < fc.Nt) xf[(int64_t)T * fc.Nt + loc] = df_split(v[r]);
-  }
+  int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (loc >= fc.Nt) return;
+  int T = blockIdx.y;
+  int i, j, k;
+  decode(fc.ijk[loc], i, j, k);
+  int64_t g = (int64_t)T * fc.Nt + loc;
+  double v = interp<DIM, double>(cc, T, i, j, k, CVec<double, double>{vc, nullptr});
+  xf[g] = df_split(minuend[g] - v);
 }
 
 // plain interpolation v_f = I v_c (all nodes)

@@ -554,9 +554,8 @@ static void residual_group_t(hhg_mesh_s* m, int l, int gi, CVec<R, U> u, CVec<R,
   const LevelData& Lv = m->lv[l];
   const Group& G = m->groups[gi];
   ResidualSegments rs = residual_segments(Lv, G, gi, after_sweep);
-  // binary32: four cells per thread sharing a list entry, every boundary slot unrolled (latency, not
-  // arithmetic, bounds it)
-  constexpr int CPB = 4;
+  // binary32: two cells per thread, every boundary slot unrolled (latency, not arithmetic, bounds it)
+  constexpr int CPB = 2;
   dim3 grid(rs.bcomp + rs.bzero + blocks_for(Lv.nbnd), (unsigned)((G.cells.size() + CPB - 1) / CPB));
   hhg_launch(k_residual_list<DIM, PM, CPB, false, R, U, B, float>, grid, kBlock, 0, s, G.d_cells,
              (int)G.cells.size(), ctx(m, l), S, m->d_dirmask, (R)stiff_scale(DIM, Lv.n), u, rhs, out, rs.ilist,
@@ -628,7 +627,7 @@ static void vcycle32(hhg_mesh_s* m, int l, U* x, const float* rhs, const hhg_sol
              (const float*)Lv.t32, C.r32, c);
   if constexpr (std::is_same<S, __half>::value) set_scale16<DIM>(m, l - 1, s);
   vcycle32<DIM, S, S>(m, l - 1, c, C.r32, p, s);
-  dim3 gf(blocks_for(Lv.Nt, kBlock * kProlongNodes), m->nc);
+  dim3 gf(blocks_for(Lv.Nt), m->nc);
   hhg_launch(k_prolong_add<DIM, float, S, U>, gf, kBlock, 0, s, ctx(m, l), ctx(m, l - 1), m->d_dirmask,
                                                          cvec_of<S>(m, l - 1, c), vec_of<U>(m, l, x));
   for (int q = 0; q < p.post; ++q) sweep32<DIM, U>(m, l, x, rhs, s);
