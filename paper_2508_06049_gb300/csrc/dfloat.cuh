@@ -78,8 +78,11 @@ __device__ __forceinline__ float2 df_split(double x) {
   const unsigned top = (unsigned)(b >> 32);
   const int e = (int)((top >> 20) & 0x7ffu);  // biased binary64 exponent
   const int eh = e - 1023 + 127;              // biased binary32 exponent of hi
-  if (e == 0 && (b << 1) == 0ull) return make_float2(0.f, 0.f);
-  if (eh <= 0 || eh >= 255) return df_split_slow(x);
+  if (eh <= 0 || eh >= 255) {
+    // zero (tested on the two 32-bit words: a comparison of x with 0.0 would be a binary64 instruction)
+    if (((top & 0x7fffffffu) | (unsigned)b) == 0u) return make_float2(0.f, 0.f);
+    return df_split_slow(x);
+  }
   const unsigned sgn = top & 0x80000000u;
   const unsigned long long mant = b & 0xfffffffffffffull;  // 52 significand bits
   const float h = __uint_as_float(sgn | ((unsigned)eh << 23) | (unsigned)(mant >> 29));

@@ -132,11 +132,11 @@ __device__ __forceinline__ float2 pair_residual(const float2 (&s)[N], const floa
 }
 
 // Partial residual r = b - ss A_T u on pairs (u and r as pairs, b in binary64) for every closure node
-// of the group's cells, zero on Dirichlet rows, from the node lists of k_residual_list: blocks
-// [0, bcomp) take the interior list entries [0, ncomp) with the compile-time stencil pattern PM
-// (one cell per grid row), the remaining blocks the boundary-type nodes (every valid slot, the
-// zero ones masked).
-template <int DIM, int PM>
+// of the group's cells, zero on Dirichlet rows, from the node lists of k_residual_list (one cell per
+// grid row): BND = false takes the interior list entries [0, ncomp) with the compile-time stencil
+// pattern PM, BND = true the boundary-type nodes (every valid slot, the zero ones masked).  Two
+// launches, so that the interior one keeps few registers (its occupancy hides the load latency).
+template <int DIM, int PM, bool BND>
 __global__ void __launch_bounds__(kBlock) k_residual_pair(const int* __restrict__ gcells, int ncells, LevelCtx lc,
                                                           const float2* __restrict__ Sp,
                                                           const uint16_t* __restrict__ dirmask, float ss,
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kBlock) k_residual_pair(const int* __restrict_
 #pragma unroll
   for (int c = 0; c < CPB; ++c) Ts[c] = gcells[min(c0 + c, ncells - 1)];  // a short last group repeats
   const unsigned bx = blockIdx.x;
-  if (bx < bcomp) {
+  if (!BND) {
     const int64_t pos = (int64_t)bx * blockDim.x + threadIdx.x;
     if (pos >= ncomp) return;
     const int2 e = ilist[pos];
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kBlock) k_residual_pair(const int* __restrict_
       if (c0 + c < ncells)
         r[g[c]] = (dirmask[Ts[c]] & 1) ? make_float2(0.f, 0.f) : pair_residual(sv[c], uv[c], b[g[c]], ss);
   } else {
-    const int64_t pos = (int64_t)(bx - bcomp) * blockDim.x + threadIdx.x;
+    const int64_t pos = (int64_t)bx * blockDim.x + threadIdx.x;
     if (pos >= nbnd) return;
     const int2 e = blist[pos];
     if (HHG_OOB(e.x, lc.Nt, 57)) return;
@@ -654,12 +654,19 @@ static void ir_residual(hhg_mesh_s* m, cudaStream_t s) {
     const Group& G = m->groups[gi];
     if (G.cells.empty()) continue;
     ResidualSegments rs = residual_segments(LL, G, (int)gi, false);
-    dim3 grid(rs.bcomp + blocks_for(LL.nbnd), (unsigned)G.cells.size());
+    dim3 gi_(rs.bcomp, (unsigned)G.cells.size()), gb_(blocks_for(LL.nbnd), (unsigned)G.cells.size());
     const float ss = (float)stiff_scale(DIM, LL.n);
 #define HHG_RP(PM)                                                                                                    \
-  hhg_launch(k_residual_pair<DIM, PM>, grid, kBlock, 0, s, G.d_cells, (int)G.cells.size(), ctx(m, L),                 \
-             (const float2*)m->dSp, m->d_dirmask, ss, (const double*)LL.b, (const float2*)LL.u, rp, rs.ilist, rs.ncomp, \
-             LL.d_bnd, LL.nbnd, rs.bcomp)
+  do {                                                                                                                \
+  if (rs.bcomp)                                                                                                       \
+    hhg_launch(k_residual_pair<DIM, PM, false>, gi_, kBlock, 0, s, G.d_cells, (int)G.cells.size(), ctx(m, L),        \
+               (const float2*)m->dSp, m->d_dirmask, ss, (const double*)LL.b, (const float2*)LL.u, rp, rs.ilist,       \
+               rs.ncomp, LL.d_bnd, LL.nbnd, rs.bcomp);                                                                \
+  if (LL.nbnd)                                                                                                        \
+    hhg_launch(k_residual_pair<DIM, PM, true>, gb_, kBlock, 0, s, G.d_cells, (int)G.cells.size(), ctx(m, L),         \
+               (const float2*)m->dSp, m->d_dirmask, ss, (const double*)LL.b, (const float2*)LL.u, rp, rs.ilist,       \
+               rs.ncomp, LL.d_bnd, LL.nbnd, rs.bcomp);                                                                \
+  } while (0)
     if constexpr (DIM == 2) {
       switch (G.pmask) {
         case 0x3: HHG_RP(0x3); break;
