@@ -558,20 +558,6 @@ __device__ __forceinline__ int face_pos(int n, int a, int b) {
 
 __device__ __forceinline__ bool face_interior(int n, int a, int b) { return a >= 1 && b >= 1 && a + b <= n - 1; }
 
-// inverse of face_pos: the face-interior node at position pos (rows b = 1, 2, .. of n - 1 - b nodes
-// a = 1, 2, ..).  Row r = b - 1 starts at S(r) = r m - r (r - 1) / 2 with m = n - 2: the row is
-// estimated from that quadratic and corrected in integers.
-__device__ __forceinline__ void face_ab(int n, int pos, int& a, int& b) {
-  const int m = n - 2;
-  const float q = (float)(2 * m + 1);
-  int r = (int)((q - sqrtf(fmaxf(q * q - 8.0f * (float)pos, 0.0f))) * 0.5f);
-  r = max(0, min(r, m - 1));
-  while (r > 0 && r * m - r * (r - 1) / 2 > pos) --r;
-  while (r + 1 < m && (r + 1) * m - (r + 1) * r / 2 <= pos) ++r;
-  b = r + 1;
-  a = pos - (r * m - r * (r - 1) / 2) + 1;
-}
-
 // in-plane directions of a face in its local (a, b) coordinates
 __device__ __forceinline__ void face_dir(int q, int& da, int& db) {
   da = (q == 0 || q == 4) ? 1 : ((q == 1 || q == 5) ? -1 : 0);
@@ -613,10 +599,10 @@ __global__ void k_face_ext(int nprim, int nf, const int32_t* __restrict__ fnodes
   bool active = tid < (int64_t)nprim * nf;
   int e = 0, a = 0, b = 0;
   if (active) {
-    // nodes in row-major face order (face_pos), so that the threads of a warp take neighbouring
-    // nodes of a face row (fnodes lists them by colour, every third node of a row)
     e = (int)(tid / nf);
-    face_ab(lc.n, (int)(tid % nf), a, b);
+    int32_t ab = fnodes[tid % nf];
+    a = ab & 0xffff;
+    b = ab >> 16;
     if (dir[e]) active = false;
   }
   R acc = 0, bs = 0;
