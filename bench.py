@@ -972,7 +972,7 @@ def main():
         line = {"metric": "FMG DoF/s (FMG + estimator + marking per step, equal error)", "value": head["value"],
                 "unit": "DoF/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if arms[-1] == "fp64" else "f32+f64-refinement", "data": "synthetic",
+                "dtype": "f64" if arms[-1] == "fp64" else "f32+f32pair-refinement", "data": "synthetic",
                 "config": config, "unknowns": head["unknowns"], "error": head["err"],
                 "clocks": head["clocks"], "e2e": head["e2e"], "roofline": head["roofline"], "cpu_baseline": cpu,
                 "gpu_launches": head["launches"] * args.steps, "arms": {a: arm_summary(res[a]) for a in arms}}
