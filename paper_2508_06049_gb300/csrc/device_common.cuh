@@ -79,6 +79,7 @@ struct LevelCtx {
   int64_t Nt;        // closure nodes per macro cell
   const int32_t* ijk;  // decode table: packed index -> i | j<<10 | k<<20
   const uint16_t* nzs;  // [cell][type]: stiffness slots with a nonzero entry (nullptr: all)
+  const int2* itab;     // levels >= 1: interpolation end points and boundary type per node
 };
 
 __device__ __forceinline__ void decode(int32_t c, int& i, int& j, int& k) {

@@ -51,6 +51,9 @@ struct LevelData {
   int l = 0, n = 1;
   int64_t Nt = 0, N = 0;
   int32_t* d_ijk = nullptr;
+  // levels >= 1, per closure node: the level-(l-1) packed indices of its two interpolation end points
+  // (equal for a node that is also a coarse node) and its boundary type: x = ia | t << 27, y = ib
+  int2* d_itab = nullptr;
   // interior colour lists: for group g and colour c, entries [icol_off[g][c], icol_off[g][c+1]) of
   // (packed local index, j | k << 16)
   std::vector<std::vector<int64_t>> icol_off;

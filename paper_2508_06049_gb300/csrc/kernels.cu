@@ -85,7 +85,7 @@ __global__ void k_finite(const double* __restrict__ v, int64_t n, int* __restric
 
 static LevelCtx ctx(const hhg_mesh_s* m, int l) {
   const LevelData& Lv = m->lv[l];
-  return LevelCtx{Lv.n, Lv.Nt, Lv.d_ijk, m->d_nzs};
+  return LevelCtx{Lv.n, Lv.Nt, Lv.d_ijk, m->d_nzs, Lv.d_itab};
 }
 
 #define DISPATCH_DIM(m, KER, ...)                 \

@@ -982,7 +982,9 @@ __device__ __forceinline__ R interp(LevelCtx cc, int T, int i, int j, int k, con
   return (R)0.5 * (a + b);
 }
 
-// u_f += I u_c on free nodes
+// u_f += I u_c on free nodes.  The end points and the boundary type come from the level's
+// interpolation table (the index arithmetic per node kept the kernel issue-bound): I u_c at a node
+// is (u_c[a] + u_c[b]) / 2, with a = b at a coarse node (exact: (x + x) / 2 = x).
 template <int DIM, typename R, typename UC, typename UF>
 __global__ void k_prolong_add(LevelCtx fc, LevelCtx cc, const uint16_t* __restrict__ dirmask, CVec<R, UC> uc,
                               Vec<R, UF> uf) {
@@ -990,12 +992,12 @@ __global__ void k_prolong_add(LevelCtx fc, LevelCtx cc, const uint16_t* __restri
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (loc >= fc.Nt) return;
   int T = blockIdx.y;
-  int i, j, k;
-  decode(fc.ijk[loc], i, j, k);
-  int t = boundary_type(DIM, fc.n, i, j, k);
+  const int2 e = fc.itab[loc];
+  const int t = e.x >> 27, ia = e.x & 0x7ffffff, ib = e.y;
   if (dirmask[T] >> t & 1) return;
-  int64_t g = (int64_t)T * fc.Nt + loc;
-  uf.set(g, uf.get(g) + interp<DIM, R>(cc, T, i, j, k, uc));
+  if (HHG_OOB(ia, cc.Nt, 23) || HHG_OOB(ib, cc.Nt, 24)) return;
+  const int64_t g = (int64_t)T * fc.Nt + loc, gc = (int64_t)T * cc.Nt;
+  uf.set(g, uf.get(g) + (R)0.5 * (uc.get(gc + ia) + uc.get(gc + ib)));
 }
 
 // FMG transition: u_{l+1} = I u_l (Dirichlet nodes from g_L, or 0 if gL is null), w_l = u_{l+1}

@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(1024) k_coarse_mixed(int n0f, const int* __res
 
 static LevelCtx ctx(const hhg_mesh_s* m, int l) {
   const LevelData& Lv = m->lv[l];
-  return LevelCtx{Lv.n, Lv.Nt, Lv.d_ijk, m->d_nzs};
+  return LevelCtx{Lv.n, Lv.Nt, Lv.d_ijk, m->d_nzs, Lv.d_itab};
 }
 
 template <typename U> static Vec<float, U> vec_of(hhg_mesh_s* m, int l, U* p) {

@@ -746,6 +746,27 @@ hhg_status build_mesh(hhg_mesh_s* m, const double* coords, const int* cells, con
       for (int j = 0; j <= Lv.n - k; ++j)
         for (int i = 0; i <= Lv.n - k - j; ++i) ijk[packed_index(d, Lv.n, i, j, k)] = i | (j << 10) | (k << 20);
     if ((st = upload(m, &Lv.d_ijk, ijk)) != HHG_OK) return st;
+    if (l >= 1) {
+      // interpolation from level l-1: a node with all-even lattice coordinates is a coarse node;
+      // any other is the midpoint of the coarse edge in the direction of its odd coordinates
+      const int nc_ = Lv.n / 2;
+      std::vector<int2> itab(Lv.Nt);
+      for (int64_t q = 0; q < Lv.Nt; ++q) {
+        const int i = ijk[q] & 1023, j = (ijk[q] >> 10) & 1023, k = ijk[q] >> 20;
+        const int t = boundary_type(d, Lv.n, i, j, k);
+        int64_t ia, ib;
+        if (!((i | j | k) & 1)) {
+          ia = ib = packed_index(d, nc_, i >> 1, j >> 1, k >> 1);
+        } else {
+          int di, dj, dk;
+          dir_vec(d, parity_dir_slot(d, i & 1, j & 1, k & 1), di, dj, dk);
+          ia = packed_index(d, nc_, (i - di) >> 1, (j - dj) >> 1, (k - dk) >> 1);
+          ib = packed_index(d, nc_, (i + di) >> 1, (j + dj) >> 1, (k + dk) >> 1);
+        }
+        itab[q] = make_int2((int)(ia | ((int64_t)t << 27)), (int)ib);
+      }
+      if ((st = upload(m, &Lv.d_itab, itab)) != HHG_OK) return st;
+    }
     // interior colour lists per group
     std::vector<int2> icol;
     Lv.icol_off.assign(m->groups.size(), {});
@@ -849,7 +870,7 @@ void free_mesh(hhg_mesh_s* m) {
   for (auto& g : m->groups) F(g.d_cells);
   F(m->d_Ainv); F(m->d_cf_vert); F(m->d_rmax); F(m->d_ainv_inf);
   for (auto& Lv : m->lv) {
-    F(Lv.d_ijk); F(Lv.d_icol); F(Lv.d_bnd); F(Lv.d_invl); F(Lv.d_invlf); F(Lv.d_fcol); F(Lv.u); F(Lv.b); F(Lv.rc); F(Lv.w); F(Lv.tmp);
+    F(Lv.d_ijk); F(Lv.d_itab); F(Lv.d_icol); F(Lv.d_bnd); F(Lv.d_invl); F(Lv.d_invlf); F(Lv.d_fcol); F(Lv.u); F(Lv.b); F(Lv.rc); F(Lv.w); F(Lv.tmp);
     F(Lv.c16); F(Lv.r32); F(Lv.t32); F(Lv.cscale); F(Lv.x32); F(Lv.b32);
   }
   F(m->fL); F(m->gL); F(m->d_part); F(m->d_red); F(m->d_flag); F(m->d_face_work); F(m->d_scal32);
