@@ -968,18 +968,18 @@ __global__ void k_restrict(LevelCtx fc, LevelCtx cc, const uint16_t* __restrict_
 
 // ---------------------------------------------------------------- prolongation, FMG transition (Alg. 4; interpolation of Sec. 4.4)
 
-template <int DIM, typename R, typename C>
-__device__ __forceinline__ R interp(LevelCtx cc, int T, int i, int j, int k, const C& uc) {
-  int pi = i & 1, pj = j & 1, pk = k & 1;
-  if (!(pi | pj | pk)) return uc.get((int64_t)T * cc.Nt + packed_index(DIM, cc.n, i >> 1, j >> 1, k >> 1));
-  int di, dj, dk;
-  dir_vec(DIM, parity_dir_slot(DIM, pi, pj, pk), di, dj, dk);
-  int64_t ia = packed_index(DIM, cc.n, (i - di) >> 1, (j - dj) >> 1, (k - dk) >> 1);
-  int64_t ib = packed_index(DIM, cc.n, (i + di) >> 1, (j + dj) >> 1, (k + dk) >> 1);
-  if (HHG_OOB(ia, cc.Nt, 21) || HHG_OOB(ib, cc.Nt, 22)) return (R)0;
-  R a = uc.get((int64_t)T * cc.Nt + ia);
-  R b = uc.get((int64_t)T * cc.Nt + ib);
-  return (R)0.5 * (a + b);
+
+// I u_c at fine node loc of cell T from the level's interpolation table (fc.itab), and the node's
+// boundary type: (u_c[a] + u_c[b]) / 2, with a = b at a coarse node (exact: (x + x) / 2 = x)
+template <typename R, typename C>
+__device__ __forceinline__ R interp_tab(const LevelCtx& fc, const LevelCtx& cc, int T, int64_t loc, const C& uc,
+                                        int& t) {
+  const int2 e = fc.itab[loc];
+  t = e.x >> 27;
+  const int ia = e.x & 0x7ffffff, ib = e.y;
+  if (HHG_OOB(ia, cc.Nt, 23) || HHG_OOB(ib, cc.Nt, 24)) return (R)0;
+  const int64_t gc = (int64_t)T * cc.Nt;
+  return (R)0.5 * (uc.get(gc + ia) + uc.get(gc + ib));
 }
 
 // u_f += I u_c on free nodes.  The end points and the boundary type come from the level's
@@ -992,12 +992,11 @@ __global__ void k_prolong_add(LevelCtx fc, LevelCtx cc, const uint16_t* __restri
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (loc >= fc.Nt) return;
   int T = blockIdx.y;
-  const int2 e = fc.itab[loc];
-  const int t = e.x >> 27, ia = e.x & 0x7ffffff, ib = e.y;
+  int t;
+  const R v = interp_tab<R>(fc, cc, T, loc, uc, t);
   if (dirmask[T] >> t & 1) return;
-  if (HHG_OOB(ia, cc.Nt, 23) || HHG_OOB(ib, cc.Nt, 24)) return;
-  const int64_t g = (int64_t)T * fc.Nt + loc, gc = (int64_t)T * cc.Nt;
-  uf.set(g, uf.get(g) + (R)0.5 * (uc.get(gc + ia) + uc.get(gc + ib)));
+  const int64_t g = (int64_t)T * fc.Nt + loc;
+  uf.set(g, uf.get(g) + v);
 }
 
 // FMG transition: u_{l+1} = I u_l (Dirichlet nodes from g_L, or 0 if gL is null), w_l = u_{l+1}
@@ -1009,17 +1008,15 @@ __global__ void k_fmg_prolong(LevelCtx fc, LevelCtx cc, int nL, int64_t NtL, int
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (loc >= fc.Nt) return;
   int T = blockIdx.y;
-  int i, j, k;
-  decode(fc.ijk[loc], i, j, k);
-  int t = boundary_type(DIM, fc.n, i, j, k);
-  double v;
+  int t;
+  double v = interp_tab<double>(fc, cc, T, loc, CVec<double, double>{uc, nullptr}, t);
   if (dirmask[T] >> t & 1) {
+    int i, j, k;
+    decode(fc.ijk[loc], i, j, k);
     int64_t q = packed_index(DIM, nL, (int64_t)i << shift, (int64_t)j << shift, (int64_t)k << shift);
     if (HHG_OOB(q, NtL, 81)) return;
     v = gL ? gL[(int64_t)T * NtL + q] : 0.0;
   }
-  else
-    v = interp<DIM, double>(cc, T, i, j, k, CVec<double, double>{uc, nullptr});
   int64_t g = (int64_t)T * fc.Nt + loc;
   uf[g] = v;
   if (w) w[g] = v;
@@ -1034,10 +1031,9 @@ __global__ void k_prolong_diff_pair(LevelCtx fc, LevelCtx cc, const double* __re
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (loc >= fc.Nt) return;
   int T = blockIdx.y;
-  int i, j, k;
-  decode(fc.ijk[loc], i, j, k);
+  int t;
   int64_t g = (int64_t)T * fc.Nt + loc;
-  double v = interp<DIM, double>(cc, T, i, j, k, CVec<double, double>{vc, nullptr});
+  double v = interp_tab<double>(fc, cc, T, loc, CVec<double, double>{vc, nullptr}, t);
   xf[g] = df_split(minuend[g] - v);
 }
 
@@ -1050,10 +1046,9 @@ __global__ void k_prolong(LevelCtx fc, LevelCtx cc, const double* __restrict__ v
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (loc >= fc.Nt) return;
   int T = blockIdx.y;
-  int i, j, k;
-  decode(fc.ijk[loc], i, j, k);
+  int t;
   int64_t g = (int64_t)T * fc.Nt + loc;
-  double v = interp<DIM, double>(cc, T, i, j, k, CVec<double, double>{vc, nullptr});
+  double v = interp_tab<double>(fc, cc, T, loc, CVec<double, double>{vc, nullptr}, t);
   vf[g] = minuend ? minuend[g] - v : v;
 }
 

@@ -354,11 +354,12 @@ __global__ void k_fmg_prolong32(LevelCtx fc, LevelCtx cc, int nL, int64_t NtL, i
   int64_t loc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (loc >= fc.Nt) return;
   int T = blockIdx.y;
-  int i, j, k;
-  decode(fc.ijk[loc], i, j, k);
-  int t = boundary_type(DIM, fc.n, i, j, k);
+  int t;
+  const float v = interp_tab<float>(fc, cc, T, loc, CVec<float, float>{xc, nullptr}, t);
   int64_t g = (int64_t)T * fc.Nt + loc;
   if (dirmask[T] >> t & 1) {
+    int i, j, k;
+    decode(fc.ijk[loc], i, j, k);
     int64_t q = packed_index(DIM, nL, (int64_t)i << shift, (int64_t)j << shift, (int64_t)k << shift);
     if (HHG_OOB(q, NtL, 81)) return;
     double gv = gL[(int64_t)T * NtL + q];
@@ -366,9 +367,8 @@ __global__ void k_fmg_prolong32(LevelCtx fc, LevelCtx cc, int nL, int64_t NtL, i
     w[g] = gv;
     return;
   }
-  float v = interp<DIM, float>(cc, T, i, j, k, CVec<float, float>{xc, nullptr});
   xf[g] = v;
-  w[g] = (double)v;
+  w[g] = df_widen(v);  // exact, without the conversion instruction (binary64 pipe)
 }
 
 // Direct coarse solve for the binary32 path: residual and A_ff^{-1} r in binary64, the update is
