@@ -246,7 +246,9 @@ hhg_status hhg_adjoint_l2(hhg_mesh mesh, const hhg_solve_params* params, const u
                           double* J, double* grad_f, double* grad_k);
 
 /* Host self-check of the lattice index arithmetic (the structured level-l lattice of a macro cell,
- * Sec. 2) against brute force (no GPU needed).
+ * Sec. 2) against brute force (no GPU needed): packed indices, neighbour offsets, valid directions
+ * and, for even n, the interpolation end points from the side-n/2 lattice (Sec. 4.4's linear
+ * interpolation) that the prolongation tables store.
  * Returns 0 if consistent, otherwise the number of mismatches. */
 int hhg_lattice_selfcheck(int dim, int n);
 

@@ -779,6 +779,44 @@ int hhg_lattice_selfcheck(int dim, int n) {
       }
   for (int64_t g = 0; g < Nt; ++g)
     if (seen[g] != 1) ++bad;
+  // interpolation end points from the side-n/2 lattice (n even): both are coarse closure nodes, the
+  // fine node is their midpoint (fine coordinates = sum of the coarse ones), they are equal exactly
+  // for all-even fine coordinates, and otherwise they differ by one lattice direction
+  if (n % 2 == 0) {
+    const int nc = n / 2;
+    const int64_t Ntc = closure_size(dim, nc);
+    std::vector<int> cc(3 * Ntc, -1);
+    for (int k = 0; k <= (dim == 3 ? nc : 0); ++k)
+      for (int j = 0; j <= nc - k; ++j)
+        for (int i = 0; i <= nc - k - j; ++i) {
+          const int64_t g = packed_index(dim, nc, i, j, k);
+          cc[3 * g] = i, cc[3 * g + 1] = j, cc[3 * g + 2] = k;
+        }
+    for (int k = 0; k <= (dim == 3 ? n : 0); ++k)
+      for (int j = 0; j <= n - k; ++j)
+        for (int i = 0; i <= n - k - j; ++i) {
+          int64_t ia, ib;
+          interp_ends(dim, n, i, j, k, ia, ib);
+          if (ia < 0 || ia >= Ntc || ib < 0 || ib >= Ntc) {
+            ++bad;
+            continue;
+          }
+          const int* a = &cc[3 * ia];
+          const int* b = &cc[3 * ib];
+          if (a[0] + b[0] != i || a[1] + b[1] != j || a[2] + b[2] != k) ++bad;
+          const bool even = !((i | j | k) & 1);
+          if (even != (ia == ib)) ++bad;
+          if (!even) {
+            bool adjacent = false;
+            for (int d = 1; d < (dim == 2 ? 7 : 15); ++d) {
+              int di, dj, dk;
+              dir_vec(dim, d, di, dj, dk);
+              if (b[0] - a[0] == di && b[1] - a[1] == dj && b[2] - a[2] == dk) adjacent = true;
+            }
+            if (!adjacent) ++bad;
+          }
+        }
+  }
   return bad;
 }
 

@@ -217,4 +217,20 @@ HHG_HD int parity_dir_slot(int dim, int pi, int pj, int pk) {
   }
 }
 
+// Interpolation from the lattice of side n / 2 (n even) to the lattice of side n: the coarse packed
+// indices of the two end points of fine node (i, j, k).  A node with all-even coordinates is the
+// coarse node (i, j, k) / 2 (ia = ib); any other is the midpoint of the coarse edge along the
+// direction of its odd coordinates (checked against brute force by hhg_lattice_selfcheck).
+HHG_HD void interp_ends(int dim, int n, int i, int j, int k, int64_t& ia, int64_t& ib) {
+  const int nc = n / 2;
+  if (!((i | j | k) & 1)) {
+    ia = ib = packed_index(dim, nc, i >> 1, j >> 1, k >> 1);
+    return;
+  }
+  int di, dj, dk;
+  dir_vec(dim, parity_dir_slot(dim, i & 1, j & 1, k & 1), di, dj, dk);
+  ia = packed_index(dim, nc, (i - di) >> 1, (j - dj) >> 1, (k - dk) >> 1);
+  ib = packed_index(dim, nc, (i + di) >> 1, (j + dj) >> 1, (k + dk) >> 1);
+}
+
 }  // namespace hhg

@@ -749,20 +749,12 @@ hhg_status build_mesh(hhg_mesh_s* m, const double* coords, const int* cells, con
     if (l >= 1) {
       // interpolation from level l-1: a node with all-even lattice coordinates is a coarse node;
       // any other is the midpoint of the coarse edge in the direction of its odd coordinates
-      const int nc_ = Lv.n / 2;
       std::vector<int2> itab(Lv.Nt);
       for (int64_t q = 0; q < Lv.Nt; ++q) {
         const int i = ijk[q] & 1023, j = (ijk[q] >> 10) & 1023, k = ijk[q] >> 20;
         const int t = boundary_type(d, Lv.n, i, j, k);
         int64_t ia, ib;
-        if (!((i | j | k) & 1)) {
-          ia = ib = packed_index(d, nc_, i >> 1, j >> 1, k >> 1);
-        } else {
-          int di, dj, dk;
-          dir_vec(d, parity_dir_slot(d, i & 1, j & 1, k & 1), di, dj, dk);
-          ia = packed_index(d, nc_, (i - di) >> 1, (j - dj) >> 1, (k - dk) >> 1);
-          ib = packed_index(d, nc_, (i + di) >> 1, (j + dj) >> 1, (k + dk) >> 1);
-        }
+        interp_ends(d, Lv.n, i, j, k, ia, ib);
         itab[q] = make_int2((int)(ia | ((int64_t)t << 27)), (int)ib);
       }
       if ((st = upload(m, &Lv.d_itab, itab)) != HHG_OK) return st;
