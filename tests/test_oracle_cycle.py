@@ -181,7 +181,7 @@ def test_fmg_call_sequence_and_stored_iterates(monkeypatch, nu, pre, post, n_ext
 
 
 def _colour_stage_sweep(lev, u, rhs):
-    """The survey's first reading of the sweep: every stage (the three face colours included) Jacobi
+    """The colour-stage reading of the sweep: every stage (the three face colours included) Jacobi
     inside the stage, in the oracle's stage order, with current values of everything else."""
     for s in range(len(lev.stages)):
         idx = lev.stages[s]
