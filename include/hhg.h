@@ -170,7 +170,8 @@ hhg_status hhg_estimate_norm(hhg_mesh mesh, int j, int norm, const double* cell_
 /* Read an internal level vector of the last solve (Alg. 4) into `out` (host or device, N_l doubles):
  * which = 0: u_l after its FMG V-cycles (l = L: the solution, l < L: overwritten by later
  * corrections, so only l = L is meaningful after the solve), 1: w_l (l = 0..L-1, stored on
- * level l+1, N_{l+1} doubles), 2: b_l summed over interface copies (N_l). */
+ * level l+1, N_{l+1} doubles), 2: b_l summed over interface copies (N_l; after a mixed-precision
+ * solve only l = L is kept in binary64, the coarser right-hand sides live in binary32). */
 hhg_status hhg_get_vector(hhg_mesh mesh, int which, int level, double* out);
 
 /* Operator application for testing (the operators of Eq. 4.15 and Sec. 4.4, and the smoother of
